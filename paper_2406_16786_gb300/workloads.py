@@ -1,0 +1,433 @@
+"""Seeded synthetic inputs: channel and pipe geometries, particle lattices, velocity fields.
+
+This module only *describes problems*: where fluid and wall particles start, what each
+in-/outlet buffer box is (origin, frame, extent, boundary type) and the physical
+constants.  It performs no step of the open-boundary method and no SPH arithmetic, so both
+the CUDA library's tests/bench and the CPU oracle's tests can take their inputs from it.
+
+Conventions shared with the library header ``include/sphbuf.h``:
+
+* positions are global coordinates in metres; ``dim`` is 2 or 3 (2-D cases keep z = 0);
+* a buffer frame is a row-major 3x3 matrix ``R`` with ``X' = R (X - O')``; its first row is
+  the unit normal of the in-/outlet, pointing in the *inflow* direction for inflow and
+  bidirectional buffers and in the *outflow* direction for outflow buffers (Sec. 3.1, 3.2);
+* the cell-relative encoding of a position is the storage format of the library: integer
+  cell coordinates on a dense grid of cell size ``cs = 2 h`` anchored at ``lo`` plus an FP32
+  offset inside the cell (``encode_positions``).
+
+Lattices follow the paper's set-up: particles on a Cartesian lattice of spacing ``dp`` with
+three wall layers (Sec. 3, 5.1); a seeded uniform jitter of +-0.01 dp is added to fluid
+particles so that threshold ties are rare.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+# Boundary-type codes; identical numbering in include/sphbuf.h (sphbuf_bc_type).
+VELOCITY_INLET = 0
+PRESSURE_OUTLET = 1
+PRESSURE_INLET = 2
+VELOCITY_OUTLET = 3
+BIDIR_PRESSURE = 4
+BIDIR_VELOCITY = 5
+BC_NAMES = {
+    VELOCITY_INLET: "velocity_inlet",
+    PRESSURE_OUTLET: "pressure_outlet",
+    PRESSURE_INLET: "pressure_inlet",
+    VELOCITY_OUTLET: "velocity_outlet",
+    BIDIR_PRESSURE: "bidir_pressure",
+    BIDIR_VELOCITY: "bidir_velocity",
+}
+
+BASE_SEED = 20240616
+
+
+@dataclasses.dataclass
+class BufferSpec:
+    """One in-/outlet buffer box as the user states it (Sec. 3.1, Fig. of the buffer)."""
+
+    origin: np.ndarray  # (3,) box centre O'
+    rotation: np.ndarray  # (3, 3) row-major, X' = R (X - O')
+    extent: np.ndarray  # (3,) a (along X'), b (along Y'), c (along Z'; ignored in 2-D)
+    bc: int
+    umax: float = 0.0  # velocity BC: peak speed of the profile
+    half_width: float = 0.0  # velocity BC: R of the profile 1-(Y'/R)^2; 0 => plug
+    p_b: float = 0.0  # pressure BC: p_b(t) = p_b + p_amp sin(p_omega t + p_phase)
+    p_amp: float = 0.0
+    p_omega: float = 0.0
+    p_phase: float = 0.0
+
+
+@dataclasses.dataclass
+class Case:
+    """A complete synthetic problem: grid box, constants, particles, buffers."""
+
+    name: str
+    dim: int
+    lo: np.ndarray  # (3,)
+    hi: np.ndarray  # (3,)
+    dp: float
+    h_over_dp: float
+    rho0: float
+    c0: float
+    nu: float
+    dt: float
+    fluid_pos: np.ndarray  # (n, dim) float64
+    fluid_vel: np.ndarray  # (n, dim) float64
+    fluid_rho: np.ndarray  # (n,) float64
+    wall_pos: np.ndarray  # (nw, dim) float64
+    buffers: List[BufferSpec]
+    capacity: int
+    steps: int = 1
+
+    @property
+    def n(self) -> int:
+        return int(self.fluid_pos.shape[0])
+
+    @property
+    def cs(self) -> float:
+        # grid cell size = kernel support 2h, with h = h_over_dp * dp
+        return 2.0 * (self.h_over_dp * self.dp)
+
+    def grid_dims(self):
+        return grid_dims(self.lo, self.hi, self.cs, self.dim)
+
+
+def grid_dims(lo, hi, cs, dim):
+    n = [int(math.ceil((float(hi[a]) - float(lo[a])) / cs)) for a in range(3)]
+    if dim == 2:
+        n[2] = 1
+    return n
+
+
+def encode_positions(pos: np.ndarray, lo, cs: float, dims: Sequence[int]):
+    """Global FP64 positions -> (linear cell index int32, FP32 in-cell offset).
+
+    cell_a = floor((x_a - lo_a) / cs); frac_a = fl32((x_a - lo_a) - cell_a * cs), then folded
+    back into [0, cs32) with at most one FP32 add/sub of cs32.  Linear index
+    (cz * ny + cy) * nx + cx.  Positions outside the grid raise ValueError.
+    """
+    pos = np.asarray(pos, dtype=np.float64)
+    n, d = pos.shape
+    cs32 = np.float32(cs)
+    cells = np.zeros((n, 3), dtype=np.int64)
+    frac = np.zeros((n, d), dtype=np.float32)
+    for a in range(d):
+        t = pos[:, a] - float(lo[a])
+        c = np.floor(t / cs).astype(np.int64)
+        f = (t - c.astype(np.float64) * cs).astype(np.float32)
+        hi_m = f >= cs32
+        f[hi_m] = f[hi_m] - cs32
+        c[hi_m] += 1
+        lo_m = f < np.float32(0)
+        f[lo_m] = f[lo_m] + cs32
+        c[lo_m] -= 1
+        # a value that rounds up to cs32 after the add above is folded once more
+        hi_m = f >= cs32
+        f[hi_m] = np.float32(0)
+        c[hi_m] += 1
+        cells[:, a] = c
+        frac[:, a] = f
+    nx, ny, nz = dims
+    bad = (cells[:, 0] < 0) | (cells[:, 0] >= nx) | (cells[:, 1] < 0) | (cells[:, 1] >= ny)
+    if d == 3:
+        bad |= (cells[:, 2] < 0) | (cells[:, 2] >= nz)
+    if np.any(bad):
+        raise ValueError("%d positions lie outside the grid box" % int(bad.sum()))
+    lin = (cells[:, 2] * ny + cells[:, 1]) * nx + cells[:, 0]
+    return lin.astype(np.int32), frac
+
+
+def decode_positions(cell: np.ndarray, frac: np.ndarray, lo, cs: float, dims: Sequence[int]):
+    """Inverse of ``encode_positions`` in FP64: x_a = lo_a + cell_a * cs + frac_a."""
+    nx, ny, _ = dims
+    cell = np.asarray(cell, dtype=np.int64)
+    d = frac.shape[1]
+    cc = [cell % nx, (cell // nx) % ny, cell // (nx * ny)]
+    out = np.zeros((cell.shape[0], d), dtype=np.float64)
+    for a in range(d):
+        out[:, a] = float(lo[a]) + cc[a].astype(np.float64) * cs + frac[:, a].astype(np.float64)
+    return out
+
+
+# ----------------------------------------------------------------------------- frames
+def frame_2d(angle_rad: float) -> np.ndarray:
+    """Frame whose first row is the unit vector at ``angle_rad`` in the xy-plane."""
+    c, s = math.cos(angle_rad), math.sin(angle_rad)
+    return np.array([[c, s, 0.0], [-s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def frame_3d(normal, roll: float = 0.0) -> np.ndarray:
+    """An orthonormal right-handed frame with first row ``normal`` (Gram-Schmidt).
+
+    The second row is the component of the coordinate axis least aligned with the normal,
+    orthogonalised against it and turned by ``roll`` about the normal; the third row is
+    normal x second.  Any roll is a valid local frame: the buffer box only needs its X'
+    axis on the normal.
+    """
+    n = np.asarray(normal, dtype=np.float64)
+    n = n / np.linalg.norm(n)
+    k = int(np.argmin(np.abs(n)))
+    helper = np.zeros(3)
+    helper[k] = 1.0
+    e2 = helper - np.dot(helper, n) * n
+    e2 /= np.linalg.norm(e2)
+    e3 = np.cross(n, e2)
+    c, s = math.cos(roll), math.sin(roll)
+    e2r = c * e2 + s * e3
+    e3r = np.cross(n, e2r)
+    return np.stack([n, e2r, e3r])
+
+
+# --------------------------------------------------------------------------- lattices
+def _jitter(rng, shape, dp, amount=0.01):
+    return rng.uniform(-amount * dp, amount * dp, size=shape)
+
+
+def _grid_box(points_list, margin):
+    allp = np.concatenate([p for p in points_list if p.size], axis=0)
+    lo = np.zeros(3)
+    hi = np.zeros(3)
+    d = allp.shape[1]
+    lo[:d] = allp.min(axis=0) - margin
+    hi[:d] = allp.max(axis=0) + margin
+    if d == 2:
+        lo[2], hi[2] = 0.0, 1.0
+    return lo, hi
+
+
+def channel_2d_local(length, width, dp, wall_layers=3, wall_extend=3):
+    """Fluid and wall lattice points of a straight 2-D channel in its own frame (s, t)."""
+    ns = int(round(length / dp))
+    nt = int(round(width / dp))
+    s = (np.arange(ns) + 0.5) * dp
+    t = -0.5 * width + (np.arange(nt) + 0.5) * dp
+    S, T = np.meshgrid(s, t, indexing="ij")
+    fluid = np.stack([S.ravel(), T.ravel()], axis=1)
+    sw = (np.arange(-wall_extend, ns + wall_extend) + 0.5) * dp
+    tw = np.concatenate([0.5 * width + (np.arange(wall_layers) + 0.5) * dp,
+                         -0.5 * width - (np.arange(wall_layers) + 0.5) * dp])
+    SW, TW = np.meshgrid(sw, tw, indexing="ij")
+    wall = np.stack([SW.ravel(), TW.ravel()], axis=1)
+    return fluid, wall
+
+
+def pipe_3d_local(length, radius, dp, wall_layers=3, wall_extend=3):
+    """Fluid and wall lattice points of a straight circular pipe in its frame (s, y, z)."""
+    ns = int(round(length / dp))
+    m = int(math.ceil((radius + wall_layers * dp) / dp))
+    yz = (np.arange(-m, m) + 0.5) * dp
+    Y, Z = np.meshgrid(yz, yz, indexing="ij")
+    r = np.sqrt(Y * Y + Z * Z).ravel()
+    Y, Z = Y.ravel(), Z.ravel()
+    inner = r < radius
+    ring = (r >= radius) & (r < radius + wall_layers * dp)
+    s = (np.arange(ns) + 0.5) * dp
+    sw = (np.arange(-wall_extend, ns + wall_extend) + 0.5) * dp
+    fluid = np.stack([np.repeat(s, inner.sum()), np.tile(Y[inner], ns), np.tile(Z[inner], ns)], axis=1)
+    nsw = sw.shape[0]
+    wall = np.stack([np.repeat(sw, ring.sum()), np.tile(Y[ring], nsw), np.tile(Z[ring], nsw)], axis=1)
+    return fluid, wall
+
+
+def _to_global(local, frame, origin):
+    d = local.shape[1]
+    M = frame[:d, :d]
+    return origin[:d][None, :] + local @ M
+
+
+def straight_channel_case(
+    *,
+    name="channel2d",
+    length=10.0,
+    width=1.0,
+    dp=0.025,
+    angle_deg=0.0,
+    inlet_bc=VELOCITY_INLET,
+    outlet_bc=PRESSURE_OUTLET,
+    umax=1.0,
+    profile="plug",
+    p_in=0.0,
+    p_out=0.0,
+    p_amp=0.0,
+    p_omega=0.0,
+    rho0=1000.0,
+    c0=10.0,
+    nu=1e-2,
+    dt=None,
+    h_over_dp=1.3,
+    buffer_layers=4,
+    seed=BASE_SEED + 1,
+    init_velocity="bc",
+    capacity_factor=1.5,
+    steps=200,
+) -> Case:
+    """2-D straight channel of ``length`` x ``width`` along ``angle_deg`` (Sec. 5.1 set-up)."""
+    rng = np.random.default_rng(seed)
+    theta = math.radians(angle_deg)
+    fluid_l, wall_l = channel_2d_local(length, width, dp)
+    fluid_l = fluid_l + _jitter(rng, fluid_l.shape, dp)
+    frame = frame_2d(theta)
+    origin = np.zeros(3)
+    fluid = _to_global(fluid_l, frame, origin)
+    wall = _to_global(wall_l, frame, origin)
+    h = h_over_dp * dp
+    lo, hi = _grid_box([fluid, wall], margin=2.0 * (2.0 * h))
+    a = buffer_layers * dp
+    e_s = frame[0]
+    half = 0.5 * width
+    bufs = []
+    inlet_is_bidir = inlet_bc in (BIDIR_PRESSURE, BIDIR_VELOCITY)
+    outlet_is_bidir = outlet_bc in (BIDIR_PRESSURE, BIDIR_VELOCITY)
+    prof_hw = half if profile == "parabolic" else 0.0
+    # inlet box: centred a/2 inside the channel start, X' along +e_s (into the channel)
+    bufs.append(BufferSpec(origin=origin + 0.5 * a * e_s, rotation=frame.copy(),
+                           extent=np.array([a, width, 0.0]), bc=inlet_bc, umax=umax,
+                           half_width=prof_hw, p_b=p_in, p_amp=p_amp, p_omega=p_omega))
+    # outlet box: X' along +e_s for an outflow buffer, along -e_s (inflow direction) if bidirectional
+    out_frame = frame_2d(theta + math.pi) if outlet_is_bidir else frame.copy()
+    bufs.append(BufferSpec(origin=origin + (length - 0.5 * a) * e_s, rotation=out_frame,
+                           extent=np.array([a, width, 0.0]), bc=outlet_bc, umax=umax,
+                           half_width=prof_hw, p_b=p_out))
+    del inlet_is_bidir
+    vel = np.zeros_like(fluid)
+    if init_velocity == "bc":
+        # every particle starts at the inlet profile value along the channel axis
+        t_loc = fluid_l[:, 1]
+        if profile == "parabolic":
+            u = umax * np.clip(1.0 - (t_loc / half) ** 2, 0.0, None)
+        else:
+            u = np.full(fluid.shape[0], umax)
+        vel = u[:, None] * e_s[None, :2]
+    elif init_velocity == "inlet_only":
+        t_loc = fluid_l[:, 1]
+        in_box = fluid_l[:, 0] < a
+        if profile == "parabolic":
+            u = umax * np.clip(1.0 - (t_loc / half) ** 2, 0.0, None)
+        else:
+            u = np.full(fluid.shape[0], umax)
+        vel[in_box] = u[in_box, None] * e_s[None, :2]
+    if dt is None:
+        dt = min(0.25 * h / (c0 + umax), 0.125 * h * h / nu if nu > 0 else 1e30)
+    n = fluid.shape[0]
+    return Case(name=name, dim=2, lo=lo, hi=hi, dp=dp, h_over_dp=h_over_dp, rho0=rho0, c0=c0,
+                nu=nu, dt=dt, fluid_pos=fluid, fluid_vel=vel, fluid_rho=np.full(n, rho0),
+                wall_pos=wall, buffers=bufs, capacity=int(capacity_factor * n) + 1024, steps=steps)
+
+
+def pipe_case(
+    *,
+    name="pipe3d",
+    length=5.09,
+    radius=0.5,
+    dp=0.01,
+    axis=(1.0, 1.0, 1.0),
+    roll=None,
+    inlet_bc=BIDIR_PRESSURE,
+    outlet_bc=BIDIR_PRESSURE,
+    p_in=0.0,
+    p_amp=50.0,
+    p_omega=math.pi,
+    p_out=0.0,
+    umax=0.0,
+    rho0=1000.0,
+    c0=3.0,
+    nu=1e-2,
+    dt=None,
+    umax_est=0.03,
+    h_over_dp=1.3,
+    buffer_layers=4,
+    seed=BASE_SEED + 3,
+    init_velocity="rest",
+    capacity_factor=1.25,
+    steps=1000,
+) -> Case:
+    """3-D circular pipe along ``axis`` with a buffer box at each end (Sec. 6.1 set-up)."""
+    rng = np.random.default_rng(seed)
+    if roll is None:
+        roll = float(rng.uniform(0.0, 2.0 * math.pi))
+    frame = frame_3d(axis, roll)
+    fluid_l, wall_l = pipe_3d_local(length, radius, dp)
+    fluid_l = fluid_l + _jitter(rng, fluid_l.shape, dp)
+    origin = np.zeros(3)
+    fluid = _to_global(fluid_l, frame, origin)
+    wall = _to_global(wall_l, frame, origin)
+    h = h_over_dp * dp
+    lo, hi = _grid_box([fluid, wall], margin=2.0 * (2.0 * h))
+    a = buffer_layers * dp
+    e_s = frame[0]
+    flip = np.diag([-1.0, -1.0, 1.0]) @ frame  # first row -e_s, still right-handed
+    inlet_bidir = inlet_bc in (BIDIR_PRESSURE, BIDIR_VELOCITY)
+    outlet_bidir = outlet_bc in (BIDIR_PRESSURE, BIDIR_VELOCITY)
+    del inlet_bidir
+    bufs = [
+        BufferSpec(origin=origin + 0.5 * a * e_s, rotation=frame.copy(),
+                   extent=np.array([a, 2 * radius, 2 * radius]), bc=inlet_bc, umax=umax,
+                   half_width=radius, p_b=p_in, p_amp=p_amp, p_omega=p_omega),
+        BufferSpec(origin=origin + (length - 0.5 * a) * e_s,
+                   rotation=flip if outlet_bidir else frame.copy(),
+                   extent=np.array([a, 2 * radius, 2 * radius]), bc=outlet_bc, umax=umax,
+                   half_width=radius, p_b=p_out),
+    ]
+    vel = np.zeros_like(fluid)
+    if init_velocity == "profile" and umax > 0:
+        r2 = fluid_l[:, 1] ** 2 + fluid_l[:, 2] ** 2
+        u = umax * np.clip(1.0 - r2 / radius ** 2, 0.0, None)
+        vel = u[:, None] * e_s[None, :]
+    if dt is None:
+        dt = min(0.25 * h / (c0 + umax_est), 0.125 * h * h / nu if nu > 0 else 1e30)
+    n = fluid.shape[0]
+    return Case(name=name, dim=3, lo=lo, hi=hi, dp=dp, h_over_dp=h_over_dp, rho0=rho0, c0=c0,
+                nu=nu, dt=dt, fluid_pos=fluid, fluid_vel=vel, fluid_rho=np.full(n, rho0),
+                wall_pos=wall, buffers=bufs, capacity=int(capacity_factor * n) + 4096, steps=steps)
+
+
+def shear_velocity(case: Case, u0: float, lateral: float = 0.1, seed: int = 7) -> np.ndarray:
+    """A velocity field that crosses every buffer face in both directions.
+
+    Along each buffer's first frame row the speed is ``u0 * sin(2 pi Y'/b + phase)`` (half the
+    cross-section moves in, half out), plus seeded lateral noise of relative size ``lateral``.
+    Used by the kinematic (drift-only) lockstep tests.
+    """
+    rng = np.random.default_rng(seed)
+    d = case.dim
+    pos = case.fluid_pos
+    e = case.buffers[0].rotation
+    y = (pos - case.buffers[0].origin[None, :d]) @ e[1, :d]
+    b = case.buffers[0].extent[1]
+    u = u0 * np.sin(2.0 * math.pi * y / b + 0.3)
+    v = u[:, None] * e[0, :d][None, :]
+    v += lateral * u0 * rng.standard_normal(v.shape)
+    return v
+
+
+def perturbed_state(case: Case, dv: float, drho: float, seed: int = 11):
+    """Seeded small perturbations of velocity (absolute, m/s) and density (relative)."""
+    rng = np.random.default_rng(seed)
+    vel = case.fluid_vel + dv * rng.standard_normal(case.fluid_vel.shape)
+    rho = case.fluid_rho * (1.0 + drho * rng.standard_normal(case.fluid_rho.shape))
+    return vel, rho
+
+
+def config1() -> Case:
+    """10 x 1 m straight channel along x, dp 0.025: plug velocity inlet U = 1, pressure outlet p = 0."""
+    return straight_channel_case(name="cfg1_channel_10x1_dp0.025", length=10.0, width=1.0, dp=0.025,
+                                 angle_deg=0.0, inlet_bc=VELOCITY_INLET, outlet_bc=PRESSURE_OUTLET,
+                                 umax=1.0, profile="plug", c0=10.0, nu=1e-2,
+                                 seed=BASE_SEED + 1, init_velocity="inlet_only", steps=200)
+
+
+def config3(length=5.09, dp=0.01) -> Case:
+    """3-D pipe R 0.5 along (1,1,1)/sqrt3, random roll, two bidirectional pressure buffers.
+
+    Inlet pressure 50 sin(pi t) Pa (period 2 s), outlet 0 Pa, c0 = 3 m/s, nu = 1e-2.
+    ``length`` 5.09 m gives about 4.0 M fluid particles at dp = 0.01.
+    """
+    return pipe_case(name="cfg3_pipe_R0.5_L%.2f_dp%g" % (length, dp), length=length, radius=0.5,
+                     dp=dp, axis=(1.0, 1.0, 1.0), inlet_bc=BIDIR_PRESSURE, outlet_bc=BIDIR_PRESSURE,
+                     p_in=0.0, p_amp=50.0, p_omega=math.pi, p_out=0.0, c0=3.0, nu=1e-2,
+                     seed=BASE_SEED + 3, steps=1000)

@@ -1,0 +1,166 @@
+"""Pins of the oracle's WCSPH arithmetic (oracle.sph) against closed forms and invariants."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import kernel, sph
+
+
+def _lattice(dim, n, dp):
+    ax = (np.arange(n) + 0.5) * dp
+    g = np.meshgrid(*([ax] * dim), indexing="ij")
+    return np.stack([x.ravel() for x in g], axis=1)
+
+
+def _params(dim, dp=0.01, c0=10.0, nu=1e-3):
+    return sph.make_params(dim, dp, 1.3, 1000.0, c0, nu, 1e-4)
+
+
+def _lattice_moment(dim, dp, h):
+    """-sum_j V_j x_ji dW/dx_i on a full lattice: the discrete version of 1 (about 0.97-0.98)."""
+    ax = np.arange(-4, 5) * dp
+    g = np.meshgrid(*([ax] * dim), indexing="ij")
+    X = np.stack([x.ravel() for x in g], axis=1)
+    r = np.linalg.norm(X, axis=1)
+    k = (r > 0) & (r < 2 * h)
+    return float(np.sum(dp ** dim * X[k, 0] ** 2 / r[k] * -kernel.dW(r[k], h, dim)))
+
+
+def _interior(pos, lo, hi, margin):
+    return np.all((pos > lo + margin) & (pos < hi - margin), axis=1)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_pairs_match_brute_force(dim):
+    rng = np.random.default_rng(dim)
+    h = 0.013
+    f = rng.uniform(0, 0.08, (60, dim))
+    w = rng.uniform(0, 0.08, (30, dim))
+    ff, fw = sph.neighbor_pairs(f, w, h)
+    got = set(zip(ff.i.tolist(), ff.j.tolist()))
+    want = {(i, j) for i, j in itertools.permutations(range(60), 2) if 0 < np.linalg.norm(f[i] - f[j]) <= 2 * h}
+    assert got == want
+    gw = set(zip(fw.i.tolist(), fw.j.tolist()))
+    ww = {(i, j) for i in range(60) for j in range(30) if 0 < np.linalg.norm(f[i] - w[j]) <= 2 * h}
+    assert gw == ww
+    assert np.allclose(ff.rij, f[ff.i] - f[ff.j])
+    assert np.allclose(fw.r, np.linalg.norm(f[fw.i] - w[fw.j], axis=1))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_summation_density_of_an_unperturbed_lattice_is_rho0(dim):
+    P = _params(dim)
+    n = 16 if dim == 2 else 9
+    pos = _lattice(dim, n, P.dp)
+    ff, fw = sph.neighbor_pairs(pos, np.zeros((0, dim)), P.h)
+    rho = sph.density_summation(P, pos.shape[0], ff, fw)
+    inner = _interior(pos, 0, n * P.dp, 2 * P.h)
+    assert inner.sum() > 0
+    assert np.allclose(rho[inner], P.rho0, rtol=1e-12)
+    assert np.all(rho[~inner] <= P.rho0 * (1 + 1e-12))  # truncated support near the free edges
+    assert rho[0] < 0.7 * P.rho0  # corner particle
+
+
+def test_pair_forces_conserve_momentum():
+    dim = 2
+    P = _params(dim)
+    rng = np.random.default_rng(7)
+    pos = _lattice(dim, 14, P.dp) + rng.uniform(-0.2, 0.2, (196, 2)) * P.dp
+    vel = rng.standard_normal((196, 2)) * 0.5
+    rho = P.rho0 * (1 + 0.01 * rng.standard_normal(196))
+    ff, fw = sph.neighbor_pairs(pos, np.zeros((0, dim)), P.h)
+    acc = sph.acceleration(P, vel, rho, np.full(196, np.nan), ff, fw)
+    # equal masses: sum_i a_i = 0 (pairwise antisymmetry of Eq. (5) incl. the Riemann P*)
+    assert np.linalg.norm(acc.sum(axis=0)) < 1e-11 * np.abs(acc).sum()
+    assert np.abs(acc).sum() > 0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_linear_pressure_field_gives_minus_grad_p_over_rho(dim):
+    P = _params(dim, c0=10.0)
+    n = 16 if dim == 2 else 9
+    pos = _lattice(dim, n, P.dp)
+    G = 500.0  # Pa/m along x
+    rho = P.rho0 + G * pos[:, 0] / P.c0 ** 2
+    vel = np.zeros_like(pos)
+    ff, fw = sph.neighbor_pairs(pos, np.zeros((0, dim)), P.h)
+    acc = sph.acceleration(P, vel, rho, np.full(pos.shape[0], np.nan), ff, fw)
+    inner = _interior(pos, 0, n * P.dp, 2 * P.h)
+    ax = acc[inner, 0] * rho[inner] / (-G)
+    assert np.allclose(ax, 1.0, atol=0.04)
+    assert np.allclose(ax, _lattice_moment(dim, P.dp, P.h), atol=0.005)
+    assert np.allclose(acc[inner, 1:], 0.0, atol=0.02 * G / P.rho0)
+
+
+def test_viscous_term_is_nu_laplacian():
+    dim = 2
+    P = _params(dim, nu=2e-3)
+    pos = _lattice(dim, 20, P.dp)
+    A = 0.5  # v_x = A y^2  =>  nu lap v_x = 2 A nu
+    vel = np.zeros_like(pos)
+    vel[:, 0] = A * pos[:, 1] ** 2
+    rho = np.full(pos.shape[0], P.rho0)
+    ff, fw = sph.neighbor_pairs(pos, np.zeros((0, dim)), P.h)
+    acc = sph.acceleration(P, vel, rho, np.full(pos.shape[0], np.nan), ff, fw)
+    inner = _interior(pos, 0, 20 * P.dp, 2 * P.h)
+    assert np.allclose(acc[inner, 0] / (2 * A * P.nu), 1.0, atol=0.04)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_continuity_of_uniform_expansion(dim):
+    P = _params(dim)
+    n = 16 if dim == 2 else 9
+    pos = _lattice(dim, n, P.dp)
+    E = 0.3
+    vel = np.zeros_like(pos)
+    vel[:, 0] = E * pos[:, 0]  # div v = E
+    rho = np.full(pos.shape[0], P.rho0)
+    ff, fw = sph.neighbor_pairs(pos, np.zeros((0, dim)), P.h)
+    drho = sph.continuity_rate(P, vel, rho, ff, fw)
+    inner = _interior(pos, 0, n * P.dp, 2 * P.h)
+    assert np.allclose(drho[inner] / (-P.rho0 * E), 1.0, atol=0.04)
+    assert np.allclose(drho[inner] / (-P.rho0 * E), _lattice_moment(dim, P.dp, P.h), atol=0.005)
+
+
+def test_continuity_pressure_term_diffuses():
+    dim = 2
+    P = _params(dim)
+    pos = _lattice(dim, 16, P.dp)
+    x = pos[:, 0] - 8 * P.dp
+    rho = P.rho0 + 1e-3 * (x / P.dp) ** 2  # pressure minimum in the middle column
+    ff, fw = sph.neighbor_pairs(pos, np.zeros((0, dim)), P.h)
+    drho = sph.continuity_rate(P, np.zeros_like(pos), rho, ff, fw)
+    inner = _interior(pos, 0, 16 * P.dp, 2 * P.h)
+    # at rest only the Riemann pressure term acts: density rises where pressure is lowest
+    assert np.all(drho[inner & (np.abs(x) < 0.6 * P.dp)] > 0)
+
+
+def test_boundary_pressure_term_cancels_truncation():
+    # a lattice block at uniform pressure p_b: with Eq. (18) the edge particles feel no force
+    dim = 2
+    P = _params(dim)
+    pos = _lattice(dim, 12, P.dp)
+    pb = 37.0
+    rho = np.full(pos.shape[0], P.rho0 + pb / P.c0 ** 2)
+    ff, fw = sph.neighbor_pairs(pos, np.zeros((0, dim)), P.h)
+    vel = np.zeros_like(pos)
+    with_bc = sph.acceleration(P, vel, rho, np.full(pos.shape[0], pb), ff, fw)
+    without = sph.acceleration(P, vel, rho, np.full(pos.shape[0], np.nan), ff, fw)
+    assert np.abs(with_bc).max() < 1e-12 * np.abs(without).max()
+    edge = ~_interior(pos, 0, 12 * P.dp, 2 * P.h)
+    assert np.abs(without[edge]).max() > 0
+
+
+def test_wall_neighbours_stop_an_approaching_particle():
+    dim = 2
+    P = _params(dim)
+    wall = _lattice(dim, 8, P.dp) - np.array([0.0, 8 * P.dp])  # block below y = 0
+    pos = np.array([[4 * P.dp, 0.5 * P.dp]])
+    rho = np.array([P.rho0])
+    ff, fw = sph.neighbor_pairs(pos, wall, P.h)
+    down = sph.acceleration(P, np.array([[0.0, -0.5]]), rho, np.array([np.nan]), ff, fw)
+    rest = sph.acceleration(P, np.array([[0.0, 0.0]]), rho, np.array([np.nan]), ff, fw)
+    assert abs(rest[0, 1]) < 1e-12
+    assert down[0, 1] > 0  # pushed back up, away from the wall
+    assert kernel.W(0.0, P.h, 2) > 0

@@ -1,0 +1,313 @@
+"""Benchmark: full WCSPH + open-boundary-buffer steps on the 3-D pipe workload at 4.0 M particles.
+
+Workload (synthetic, seeded): circular pipe R = 0.5 m, L = 5.09 m along (1,1,1)/sqrt3 with a
+random roll, dp = 0.01 (about 4.0 M fluid + 0.48 M wall particles), two bidirectional
+pressure buffers (inlet p_b = 50 sin(pi t) Pa, outlet 0 Pa), c0 = 3, nu = 1e-2.
+
+One step = density, force + BC + drift, buffer decisions + apply (Algorithms 1-3), cell-list
+rebuild + relabel: the whole hot path.  ``value`` is particle-steps/s with the state resident
+in HBM (graph replays, CUDA events on the domain's stream); the particle state (~300 MB) is
+larger than L2, so no flush is needed between steps.  ``e2e`` runs the same step through the
+C ABI with host arrays (write_particles, step, read_particles) inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs an independent replica (the single-domain workload does not
+shard without a halo exchange); ``value`` sums all ranks.  ``--impl reference`` times the CPU
+oracle (the plain FP64 restatement of the method) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PIPE_LEN = 5.09
+WORKLOAD = "3-D pipe R0.5 L5.09 dp0.01 along (1,1,1)/sqrt3, 2 bidirectional pressure buffers"
+METRIC = "particle-steps/s at 4M (3-D pipe, 2 bidirectional pressure buffers); buffer-update us/step alongside"
+UNIT = "particle-steps/s"
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--length", type=float, default=PIPE_LEN)
+    ap.add_argument("--phase-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+def lattice_pairs(dim, h_over_dp):
+    """Neighbours within 2h of a lattice particle (self excluded) on the unperturbed lattice."""
+    m = int(math.ceil(2 * h_over_dp)) + 1
+    ax = np.arange(-m, m + 1)
+    g = np.meshgrid(*([ax] * dim), indexing="ij")
+    r = np.sqrt(sum(x.astype(float) ** 2 for x in g))
+    return int(np.sum((r > 0) & (r < 2 * h_over_dp)))
+
+
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[3 + q].lower().startswith("active")})
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def oracle_sample(target_particles):
+    """A pipe segment of the benchmark's cross-section and spacing with ~target_particles."""
+    from paper_2406_16786_gb300 import workloads as wl
+
+    area = math.pi * 0.25
+    length = max(0.09, target_particles * 1e-6 / area)
+    case = wl.pipe_case(name="oracle_sample", length=length, radius=0.5, dp=0.01, axis=(1.0, 1.0, 1.0),
+                        inlet_bc=wl.BIDIR_PRESSURE, outlet_bc=wl.BIDIR_PRESSURE, p_in=0.0, p_amp=50.0,
+                        p_omega=math.pi, p_out=0.0, c0=3.0, nu=1e-2, seed=wl.BASE_SEED + 3)
+    return case, length
+
+
+def time_oracle(steps, warmup, target_particles):
+    from oracle import buffer as OB
+
+    case, length = oracle_sample(target_particles)
+    sim = OB.OracleSim(case)
+    sim.commit()
+    for _ in range(warmup):
+        sim.step(1)
+    n_sum = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        n_sum += sim.n
+        sim.step(1)
+    dt = time.perf_counter() - t0
+    sample = ("oracle FP64 full step (density, force, BC, drift, Algorithms 1-3 over every particle and "
+              "buffer, rebuild, relabel) on a %.3f m segment of the same pipe (%d particles), %d steps"
+              % (length, case.n, steps))
+    return n_sum / dt, dt / steps, sample, case.n
+
+
+def oracle_rate_probe():
+    rate, _, _, _ = time_oracle(1, 0, 8000)
+    return rate
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+
+    from paper_2406_16786_gb300 import _ffi, workloads
+    from paper_2406_16786_gb300.domain import Domain
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    _ffi.load()
+
+    case = workloads.config3(length=args.length)
+    stream = torch.cuda.Stream()
+    dom = Domain.from_case(case, stream=stream)
+    dom.use_graph(True)
+    dom.step(args.warmup)
+    dom.sync()
+    n0 = dom.count()
+    l0 = dom.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    dom.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches = dom.launch_count() - l0
+    dom.sync()
+    n1 = dom.count()
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    n_mean = 0.5 * (n0 + n1)
+    value = world * n_mean * args.steps / (ms_max / 1e3)
+
+    # per-phase device time (events around each phase on the domain's stream; plain launches)
+    dom.use_graph(False)
+    dom.enable_phase_timing(True)
+    dom.step(args.phase_steps)
+    ph, nph = dom.phase_times()
+    dom.enable_phase_timing(False)
+    per = {k: v / nph for k, v in ph.items()}
+
+    # buffer-update roofline (decide + apply): algorithmic bytes per step
+    dim = 3
+    cand = [dom.candidate_count(k) for k in range(len(case.buffers))]
+    inj, dels = dom.last_decisions()
+    cells = sum(c for c, _ in cand)
+    parts = sum(p for _, p in cand)
+    state_bytes = 8 * dim + 13  # cell, frac, vel, rho, id, label
+    bu_bytes = (4 * cells + parts * (4 * dim + 5) + len(inj) * (2 * state_bytes + 4 * dim + 4) + len(dels))
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    bu_s = (per["decide"] + per["apply"]) / 1e3
+    bu_gbs = bu_bytes / bu_s / 1e9 if bu_s > 0 else None
+
+    # dominant kernel: the force pass, bound by FP32 arithmetic
+    pairs = lattice_pairs(dim, case.h_over_dp)
+    flops_pair = 58.0
+    force_flops = n_mean * pairs * flops_pair
+    force_tflops = force_flops / (per["force"] / 1e3) / 1e12
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
+    alu_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max / 1e12
+
+    # end to end through the C ABI with host arrays
+    st = dom.read()
+    nn = st["id"].shape[0]
+    e2e_steps = args.e2e_steps
+    pin = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in st.items()}
+    nid = dom.global_counters()["next_id"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dom.write_particles(pin["cell"], pin["frac"], pin["vel"], pin["rho"], ids=pin["id"], labels=pin["label"],
+                            next_id=nid)
+        dom.step(1)
+        back = dom.read()
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    bytes_io = nn * state_bytes
+    e2e_value = world * nn * e2e_steps / te
+    del back
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate = oracle_rate_probe()
+        target = int(min(200000, max(20000, rate * 15.0 / 3)))
+        r, per_step, sample, npart = time_oracle(3, 0, target)
+        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles": int(n_mean), "walls": int(case.wall_pos.shape[0]),
+                   "cells": int(dom.ncell), "buffers": len(case.buffers), "dt": case.dt,
+                   "l2": "state (~%d MB) larger than L2; no flush" % (n_mean * 2 * state_bytes / 1e6),
+                   "parallelism": "replicas%d" % world, "graph": True},
+        "buffer_update_us_per_step": (per["decide"] + per["apply"]) * 1e3,
+        "phase_ms_per_step": per,
+        "roofline": {"bound": "alu", "kernel": "k_force", "achieved": force_tflops, "peak": alu_peak,
+                     "unit": "TFLOP/s", "frac": force_tflops / alu_peak, "traffic": None,
+                     "peak_source": "FP32 lanes x 2 x max SM clock (derived; not measured)",
+                     "flops_per_pair": flops_pair, "pairs_per_particle": pairs},
+        "roofline_buffer_update": {"bound": "hbm", "kernel": "k_decide+k_apply", "achieved": bu_gbs, "peak": hbm,
+                                   "unit": "GB/s", "frac": (bu_gbs / hbm) if (bu_gbs and hbm) else None,
+                                   "traffic": None, "bytes_per_step": bu_bytes, "candidate_cells": cells,
+                                   "candidate_particles": parts, "injected": len(inj), "deleted": len(dels),
+                                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io,
+                "steps": e2e_steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    dom.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    rate = oracle_rate_probe()
+    budget = 120.0
+    target = int(max(3000, min(200000, rate * budget / max(1, args.steps + args.warmup))))
+    r, per_step, sample, npart = time_oracle(args.steps, args.warmup, target)
+    out = {"impl": "reference", "metric": METRIC, "value": r, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD + " (bounded oracle sample)", "particles": npart},
+           "cpu_baseline": {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": r, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)

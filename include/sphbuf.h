@@ -1,0 +1,226 @@
+/*
+ * sphbuf.h - C ABI of the GB300 (sm_103a) open-boundary SPH library.
+ *
+ * The library runs, on one GPU, the per-step hot path of the arbitrary-positioned
+ * in-/outflow buffer of Zhang, Fan, Ren, Qian & Hu, "Generalized and high-efficiency
+ * arbitrary-positioned buffer for smoothed particle hydrodynamics" (arXiv 2406.16786),
+ * inside a plain weakly-compressible SPH step:
+ *
+ *   1 density  - Eq. (9) summation for fluid particles, Eq. (4) continuity for buffer
+ *                particles (Sec. 4: no re-initialisation near the open boundary);
+ *   2 force    - Eq. (5) Riemann momentum with the Eq. (8) limiter; Eq. (18) for buffer
+ *                particles; kick, Eqs. (23)-(26) velocity BC or Eq. (19) projection; drift;
+ *   3 decide   - Algorithms 1-3: local-frame transform (Eqs. (11), (15)) of the particles in
+ *                the cells around each buffer and the normal-axis test X' > a/2 / X' < -a/2;
+ *   4 apply    - duplicate + recycle (Eqs. (16)-(17), density Eq. (22)), delete;
+ *   5 rebuild  - counting-sort cell-linked list, sorted by (cell, id);
+ *   6 relabel  - outflow / bidirectional buffers after the rebuild (Algorithms 2-3).
+ *
+ * Conventions
+ * -----------
+ * Grid: cell size cs = 2 h, h = h_over_dp * dp; nx = ceil((hi_x - lo_x) / cs) (same for y, z;
+ * nz = 1 in 2-D); linear cell index lin = (cz * ny + cy) * nx + cx.
+ * Particle positions are stored cell-relative: an int32 linear cell index plus an FP32
+ * offset f in [0, cs32) per axis (cs32 = FP32 rounding of cs).  Global x = lo + c cs + f.
+ * Particle arrays are structure-of-arrays on the host side of this ABI: frac and vel are
+ * n x dim row-major (x, y[, z] per particle).  Labels: 0 = fluid, k + 1 = particle of
+ * buffer k, 255 = never returned (deleted).
+ * Buffer frame: row-major R (3 x 3, FP64) with X' = R (X - O'); R's first row is the unit
+ * normal, pointing in the inflow direction for inlets and bidirectional buffers and in
+ * the outflow direction for outlets (Sec. 3.1-3.2).  In 2-D only the upper-left 2 x 2
+ * block and the first two components of origin are used.
+ *
+ * FP32 decision contract (bit-exact with an FP32 restatement of Algorithms 1-3):
+ *   cO = floor((O - lo) / cs) and fO = fl32((O - lo) - cO cs) per axis (FP64 host math);
+ *   D = fl(fl(fl(c - cO) * cs32) + fl(f - fO));  X'_r = ((R_r0 D0 + R_r1 D1) + R_r2 D2)
+ *   with every product and sum rounded to FP32 separately; thresholds fl32(a/2), fl32(b/2),
+ *   fl32(c/2); outflow candidates additionally need |X'| < fl32(a/2 + cs), |Y'| < fl32(b/2 + cs)
+ *   (|Z'| < fl32(c/2 + cs)).  Moves (drift fl(v * fl32(dt)), recycling fl32(-a R[0][x])) use
+ *   f = fl(f + delta) then at most 8 folds {f >= cs32: f -= cs32, c++; f < 0: f += cs32, c--}.
+ *   Injections are numbered in (buffer, parent id) order: new id = next_id + rank.
+ *
+ * Ownership: the library allocates and frees all device memory of a domain; host pointers
+ * passed in are only read (or written, for read_* calls) during the call.
+ * Errors: every call returns a status.  Asynchronous device-side errors (capacity overflow,
+ * NaN positions) are latched in the domain and returned by the next synchronising call
+ * (sphbuf_sync or any sphbuf_read_*); once latched, later steps do no work.  No call traps
+ * or aborts.  sphbuf_error_message gives a one-line text for the domain's last error.
+ */
+#ifndef SPHBUF_H
+#define SPHBUF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sphbuf_domain *sphbuf_domain_t; /* opaque, library-owned */
+
+typedef enum {
+  SPHBUF_OK = 0,
+  SPHBUF_ERR_INVALID_ARG = 1, /* bad pointer, size, dimension, non-orthonormal frame, ... */
+  SPHBUF_ERR_CAPACITY = 2,    /* particle capacity or per-step list capacity exceeded */
+  SPHBUF_ERR_OVERLAP = 3,     /* two buffers' candidate regions overlap */
+  SPHBUF_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  SPHBUF_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  SPHBUF_ERR_NAN = 6,         /* a non-finite position was met */
+  SPHBUF_ERR_STATE = 7        /* call not valid now (e.g. add_inout_buffer after the first step) */
+} sphbuf_status;
+
+typedef enum {
+  SPHBUF_VELOCITY_INLET = 0,  /* unidirectional inflow buffer (Algorithm 1), velocity BC */
+  SPHBUF_PRESSURE_OUTLET = 1, /* unidirectional outflow buffer (Algorithm 2), pressure BC */
+  SPHBUF_PRESSURE_INLET = 2,  /* Algorithm 1 with the pressure BC (PIVO inlet, Sec. 5.1) */
+  SPHBUF_VELOCITY_OUTLET = 3, /* Algorithm 2 with the velocity BC (PIVO outlet, Sec. 5.1) */
+  SPHBUF_BIDIR_PRESSURE = 4,  /* bidirectional buffer (Algorithm 3), pressure BC */
+  SPHBUF_BIDIR_VELOCITY = 5   /* bidirectional buffer (Algorithm 3), velocity BC */
+} sphbuf_bc_type;
+
+/* Phase masks for sphbuf_step_phases.  Exactly one of PHYSICS / KINEMATIC is required.
+ * The rebuild and relabel always close a step. */
+#define SPHBUF_PHASE_PHYSICS 1u     /* density, force, kick + BC velocity, drift */
+#define SPHBUF_PHASE_KINEMATIC 2u   /* drift only, with the stored velocity (no BC) */
+#define SPHBUF_PHASE_BUFFER 4u      /* decisions + apply (Algorithms 1-3) */
+#define SPHBUF_PHASE_FULL_CHECK 8u  /* decisions over all particles instead of the cells around
+                                       each buffer (same result; for timing comparisons) */
+#define SPHBUF_STEP_DEFAULT (SPHBUF_PHASE_PHYSICS | SPHBUF_PHASE_BUFFER)
+
+typedef struct {
+  int dim;                  /* 2 or 3 */
+  double lo[3], hi[3];      /* grid box, global coordinates (m); must contain every particle */
+  double dp;                /* initial particle spacing (m) */
+  double h_over_dp;         /* smoothing length / dp (1.3 in the paper, Sec. 3) */
+  double rho0, c0, nu, dt;  /* reference density, artificial sound speed, kinematic viscosity,
+                               fixed time step */
+  uint64_t capacity;        /* maximum number of fluid particles */
+} sphbuf_domain_desc;
+
+typedef struct {
+  double umax;       /* velocity BC: peak speed U of the profile (Eqs. (23)-(24)) */
+  double half_width; /* velocity BC: profile radius R in U (1 - (Y'^2 + Z'^2)/R^2); 0 = plug U */
+  double p_b;        /* pressure BC: p_b(t) = p_b + p_amp sin(p_omega t + p_phase) (Eq. (18)) */
+  double p_amp, p_omega, p_phase;
+} sphbuf_bc_params;
+
+const char *sphbuf_status_string(sphbuf_status s);
+
+/* Last error text of a domain ("" if none).  Valid until the next call on the domain. */
+const char *sphbuf_error_message(sphbuf_domain_t d);
+
+/* Creates an empty domain and allocates its device memory (capacity-sized) on the current
+ * CUDA device.  cuda_stream: a cudaStream_t on which every later call of this domain
+ * enqueues its work; NULL makes the domain create (and later destroy) a private
+ * non-blocking stream. */
+sphbuf_status sphbuf_create_domain(const sphbuf_domain_desc *desc, void *cuda_stream,
+                                   sphbuf_domain_t *out);
+sphbuf_status sphbuf_destroy(sphbuf_domain_t d);
+
+/* Fixed wall particles (3 layers, Sec. 3), FP64 global positions n x dim.  Replaces any
+ * previous walls.  Only before the first step. */
+sphbuf_status sphbuf_set_walls(sphbuf_domain_t d, const double *pos, uint64_t n);
+
+/* Fluid particles from FP64 global positions (n x dim), FP32 velocity (n x dim) and density
+ * (n); ids 0..n-1, labels 0; inflow buffer particles are identified at the first step
+ * (Algorithm 1).  Only before the first step. */
+sphbuf_status sphbuf_set_fluid(sphbuf_domain_t d, const double *pos, const float *vel,
+                               const float *rho, uint64_t n);
+
+/* Fluid particles in the native cell-relative encoding (see Conventions).  id NULL means
+ * 0..n-1.  label NULL means 0 everywhere and Algorithm 1's identification runs at the next
+ * step; a non-NULL label array is taken as is (restart).  next_id: first id for new
+ * particles (>= every id).  Allowed before the first step and between steps (restart). */
+sphbuf_status sphbuf_write_particles(sphbuf_domain_t d, const int32_t *cell, const float *frac,
+                                     const float *vel, const float *rho, const uint32_t *id,
+                                     const uint8_t *label, uint64_t n, uint32_t next_id);
+
+/* Adds one in-/outlet buffer: box centre O' (origin), frame R (rotation, see Conventions),
+ * extent = (a, b, c): width along X', length along Y', height along Z' (c unused in 2-D).
+ * R must be orthonormal with det +1 (tolerance 1e-9).  Candidate regions of two buffers
+ * (box dilated by 2 cs) must not overlap.  Only before the first step.  *out_id = k. */
+sphbuf_status sphbuf_add_inout_buffer(sphbuf_domain_t d, const double origin[3],
+                                      const double rotation[9], const double extent[3],
+                                      sphbuf_bc_type bc, const sphbuf_bc_params *params,
+                                      int *out_id);
+
+/* Rodrigues frame of Eqs. (12)-(14): R with R n = e_x (reading: I - S sin + S^2 (1 - cos),
+ * the transpose of the printed formula, so that X' = R (X - O') has X' along n), followed by
+ * a roll about X': R <- Rx(roll) R.  n need not be unit length. */
+sphbuf_status sphbuf_rotation_from_normal(const double normal[3], double roll, double out_R[9]);
+
+/* Runs nsteps full steps (SPHBUF_STEP_DEFAULT), asynchronously on the domain's stream. */
+sphbuf_status sphbuf_step(sphbuf_domain_t d, int nsteps);
+/* Runs nsteps steps of the given phases (SPHBUF_PHASE_* mask). */
+sphbuf_status sphbuf_step_phases(sphbuf_domain_t d, int nsteps, unsigned phases);
+
+/* Captures the launches of one step (for a phase mask) into a CUDA graph and replays it
+ * for later steps with that mask.  enable = 0 returns to plain launches. */
+sphbuf_status sphbuf_use_graph(sphbuf_domain_t d, int enable);
+
+/* Waits for the domain's stream and returns any latched device-side error. */
+sphbuf_status sphbuf_sync(sphbuf_domain_t d);
+
+/* Number of fluid particles after the last step (synchronises). */
+sphbuf_status sphbuf_count(sphbuf_domain_t d, uint64_t *n);
+
+/* Grid description. */
+sphbuf_status sphbuf_grid_info(sphbuf_domain_t d, int32_t dims[3], double *cs, uint64_t *ncell);
+
+/* Copies the sorted particle state to host arrays of capacity cap (synchronises).  Any
+ * pointer may be NULL.  Order: by (cell, id). */
+sphbuf_status sphbuf_read_particles(sphbuf_domain_t d, int32_t *cell, float *frac, float *vel,
+                                    float *rho, uint32_t *id, uint8_t *label, uint64_t cap,
+                                    uint64_t *n_out);
+/* FP64 global positions lo + c cs + f (n x dim), same order (synchronises). */
+sphbuf_status sphbuf_read_positions(sphbuf_domain_t d, double *pos, uint64_t cap, uint64_t *n_out);
+/* cell_start[ncell + 1] of the current cell-linked list (synchronises). */
+sphbuf_status sphbuf_read_cell_start(sphbuf_domain_t d, uint32_t *cell_start, uint64_t cap);
+
+/* Per-buffer counters since creation (synchronises): injected / deleted particle counts, the
+ * corresponding masses (count x rho0 dp^dim) and the volume flux through the buffer at the
+ * last step, Q_k = sum over its particles of (v . u) dp^dim / a (m^3/s in 3-D). */
+sphbuf_status sphbuf_read_counters(sphbuf_domain_t d, int buffer_id, uint64_t *injected,
+                                   uint64_t *deleted, double *mass_in, double *mass_out,
+                                   double *flux_q);
+/* Domain-wide counters (synchronises): escaped particles, completed steps, next new id. */
+sphbuf_status sphbuf_read_global(sphbuf_domain_t d, uint64_t *escaped, uint64_t *steps,
+                                 uint32_t *next_id);
+
+/* Decisions of the last step (synchronises): injections sorted by (buffer, parent id) with
+ * their new ids, and deletions (unordered).  Arrays of capacity cap; NULL allowed. */
+sphbuf_status sphbuf_last_decisions(sphbuf_domain_t d, uint32_t *inj_buffer, uint32_t *inj_parent,
+                                    uint32_t *inj_new, uint64_t *n_inj, uint32_t *del_buffer,
+                                    uint32_t *del_id, uint64_t *n_del, uint64_t cap);
+
+/* Phase timing: when enabled, every step records CUDA events around its phases on the
+ * domain's stream; sphbuf_read_phase_times returns the accumulated milliseconds per phase
+ * [density, force, decide, apply, rebuild] and resets them (synchronises). */
+sphbuf_status sphbuf_enable_phase_timing(sphbuf_domain_t d, int enable);
+sphbuf_status sphbuf_read_phase_times(sphbuf_domain_t d, double ms[5], uint64_t *steps);
+
+/* Candidate set of buffer k for the current cell-linked list (synchronises): the number of
+ * cells the decision visits and the particles listed in them (Sec. 3.1's local cells). */
+sphbuf_status sphbuf_candidate_count(sphbuf_domain_t d, int buffer_id, uint64_t *cells,
+                                     uint64_t *particles);
+
+/* Number of kernel launches this domain has issued (graph replays count every kernel
+ * node of the graph). */
+sphbuf_status sphbuf_read_launch_count(sphbuf_domain_t d, uint64_t *launches);
+
+/* Stand-alone counting-sort cell-linked list (the rebuild of step 5) on DEVICE arrays:
+ * cell[n] (linear cell index in [0, ncell)), id[n], optional label[n] (entries equal to 255
+ * are skipped; NULL = none skipped).  Writes cell_start[ncell + 1] (exclusive prefix sum of
+ * the per-cell counts) and order[n_kept]: order[p] = input index of the particle in sorted
+ * slot p, sorted by (cell, id).  Ids within one cell must be distinct.  Scratch memory is
+ * allocated and freed on the stream (cudaMallocAsync).  Returns INVALID_ARG for a cell index
+ * outside [0, ncell) (checked on the device, reported at the end of the call, which
+ * synchronises the stream). */
+sphbuf_status sphbuf_cell_list_build(const int32_t *cell, const uint32_t *id, const uint8_t *label,
+                                     uint64_t n, uint64_t ncell, uint32_t *cell_start,
+                                     uint32_t *order, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPHBUF_H */

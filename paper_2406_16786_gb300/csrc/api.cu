@@ -1,0 +1,990 @@
+// C ABI of the sphbuf library: domain set-up, buffer frames, step orchestration, read-back.
+// See include/sphbuf.h for the contract of every entry point.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "sphbuf.h"
+
+using namespace sphbuf;
+
+namespace {
+
+constexpr int kPhases = 5;
+
+struct BufHost {
+  double origin[3], R[9], extent[3];
+  int bc;
+  sphbuf_bc_params prm;
+};
+
+}  // namespace
+
+struct sphbuf_domain {
+  sphbuf_domain_desc desc{};
+  DomainDev dev{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  double cs = 0;
+  float cs32 = 0;
+  int dims[3] = {1, 1, 1};
+  long long ncell = 0;
+  double mass_d = 0;
+  std::vector<BufHost> bufs;
+  std::vector<BufDev> bufs_dev;
+  std::vector<void*> allocs;
+  void* seg_mem = nullptr;
+  std::vector<int> seg_host, segbuf_host;
+  void* wall_mem = nullptr;
+  uint64_t launches = 0;
+  uint64_t graph_launches = 0;  // kernels in the instantiated graph
+  bool committed = false;
+  bool need_rebuild = false;
+  bool labels_given = false;
+  bool stepped = false;
+  bool timing = false;
+  cudaEvent_t ev[kPhases + 1] = {};
+  double acc_ms[kPhases] = {};
+  uint64_t timed_steps = 0;
+  bool use_graph = false;
+  cudaGraphExec_t graph = nullptr;
+  unsigned graph_phases = 0;
+  std::string err;
+};
+
+namespace {
+
+sphbuf_status fail(sphbuf_domain* d, sphbuf_status s, const std::string& msg) {
+  if (d) d->err = msg;
+  return s;
+}
+
+sphbuf_status cuda_fail(sphbuf_domain* d, cudaError_t e, const char* what) {
+  return fail(d, SPHBUF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(d, e_, #call);    \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(sphbuf_domain* d, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  if (e == cudaSuccess) {
+    d->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+  }
+  return e;
+}
+
+double wendland_alpha(int dim, double h) {
+  return dim == 2 ? 7.0 / (4.0 * M_PI * h * h) : 21.0 / (16.0 * M_PI * h * h * h);
+}
+
+double wendland_w(double r, double h, int dim) {
+  const double q = r / h;
+  const double t = std::max(1.0 - 0.5 * q, 0.0);
+  return wendland_alpha(dim, h) * t * t * t * t * (2.0 * q + 1.0);
+}
+
+// Reference sum of Eq. (9): W over the full-support lattice of spacing dp, self included.
+double lattice_sum_w0(int dim, double dp, double h) {
+  const int m = (int)std::ceil(2.0 * h / dp) + 1;
+  double s = 0;
+  for (int i = -m; i <= m; ++i)
+    for (int j = -m; j <= m; ++j)
+      for (int k = (dim == 3 ? -m : 0); k <= (dim == 3 ? m : 0); ++k) {
+        const double r = std::sqrt((double)(i * i + j * j + k * k)) * dp;
+        if (r < 2.0 * h) s += wendland_w(r, h, dim);
+      }
+  return s;
+}
+
+// Host encoding of a global FP64 position into (cell coordinate, FP32 offset) per axis.
+bool encode_axis(double x, double lo, double cs, float cs32, int n, int* c_out, float* f_out) {
+  const double t = x - lo;
+  double c = std::floor(t / cs);
+  float f = (float)(t - c * cs);
+  if (f >= cs32) {
+    f = f - cs32;
+    c += 1;
+  }
+  if (f < 0.f) {
+    f = f + cs32;
+    c -= 1;
+  }
+  if (f >= cs32) {
+    f = 0.f;
+    c += 1;
+  }
+  if (!(c >= 0 && c < n)) return false;
+  *c_out = (int)c;
+  *f_out = f;
+  return true;
+}
+
+void mat_T_vec(const double R[9], const double v[3], double out[3]) {
+  for (int x = 0; x < 3; ++x) out[x] = R[0 * 3 + x] * v[0] + R[1 * 3 + x] * v[1] + R[2 * 3 + x] * v[2];
+}
+
+// Separating-axis test of two oriented boxes (centre, frame rows, half extents); 2-D uses
+// the in-plane axes only.
+bool obb_overlap(int dim, const double c1[3], const double R1[9], const double h1[3], const double c2[3],
+                 const double R2[9], const double h2[3]) {
+  std::vector<std::array<double, 3>> axes;
+  auto row = [](const double R[9], int r) { return std::array<double, 3>{R[3 * r], R[3 * r + 1], R[3 * r + 2]}; };
+  const int nr = dim;
+  for (int r = 0; r < nr; ++r) axes.push_back(row(R1, r));
+  for (int r = 0; r < nr; ++r) axes.push_back(row(R2, r));
+  if (dim == 3)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        auto u = row(R1, a), v = row(R2, b);
+        std::array<double, 3> w{u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+        const double nn = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        if (nn > 1e-9) axes.push_back({w[0] / nn, w[1] / nn, w[2] / nn});
+      }
+  for (auto& ax : axes) {
+    if (dim == 2) ax[2] = 0;
+    auto proj = [&](const double R[9], const double h[3]) {
+      double s = 0;
+      for (int r = 0; r < nr; ++r) s += h[r] * std::fabs(R[3 * r] * ax[0] + R[3 * r + 1] * ax[1] + R[3 * r + 2] * ax[2]);
+      return s;
+    };
+    const double dist = std::fabs((c2[0] - c1[0]) * ax[0] + (c2[1] - c1[1]) * ax[1] + (c2[2] - c1[2]) * ax[2]);
+    if (dist > proj(R1, h1) + proj(R2, h2)) return false;
+  }
+  return true;
+}
+
+sphbuf_status upload_buffers(sphbuf_domain* d) {
+  CK(cudaMemcpy(const_cast<BufDev*>(d->dev.bufs), d->bufs_dev.data(), d->bufs_dev.size() * sizeof(BufDev),
+                cudaMemcpyHostToDevice));
+  std::vector<int> rel;
+  for (size_t k = 0; k < d->bufs_dev.size(); ++k)
+    if (d->bufs_dev[k].kind != KIND_INFLOW) rel.push_back((int)k);
+  if (!rel.empty())
+    CK(cudaMemcpy(const_cast<int*>(d->dev.relabel_ids), rel.data(), rel.size() * sizeof(int), cudaMemcpyHostToDevice));
+  d->dev.nbuf = (int)d->bufs_dev.size();
+  d->dev.nrelabel = (int)rel.size();
+  return SPHBUF_OK;
+}
+
+// Candidate cells of every buffer (Sec. 3.1: the local cell-linked lists around the box):
+// cells that can hold, before this step's drift, a particle the decision has to see.
+// Inflow/bidirectional: box dilated by one cell (movement within a step); outflow: box
+// dilated by the candidate margin cs plus one cell.  A cell is kept when its centre passes
+// the separating-axis test on the box axes against the dilated box (a superset of the cells
+// the region touches).  Consecutive x-cells are merged into [lin0, lin1) segments.
+sphbuf_status build_segments(sphbuf_domain* d) {
+  const int D = d->desc.dim;
+  const double cs = d->cs;
+  std::vector<int> seg;
+  std::vector<int> segbuf;
+  for (size_t k = 0; k < d->bufs.size(); ++k) {
+    const BufHost& b = d->bufs[k];
+    const double dil = (d->bufs_dev[k].kind == KIND_OUTFLOW) ? 2.0 * cs : cs;
+    double half[3] = {0.5 * b.extent[0] + dil, 0.5 * b.extent[1] + dil, D == 3 ? 0.5 * b.extent[2] + dil : 0.0};
+    // AABB of the dilated box in cell coordinates
+    int lo_c[3] = {0, 0, 0}, hi_c[3] = {0, 0, 0};
+    for (int x = 0; x < D; ++x) {
+      double ext = 0;
+      for (int r = 0; r < D; ++r) ext += half[r] * std::fabs(b.R[3 * r + x]);
+      ext += cs;
+      lo_c[x] = std::max(0, (int)std::floor((b.origin[x] - ext - d->desc.lo[x]) / cs));
+      hi_c[x] = std::min(d->dims[x] - 1, (int)std::floor((b.origin[x] + ext - d->desc.lo[x]) / cs));
+    }
+    double rad[3] = {0, 0, 0};
+    for (int r = 0; r < D; ++r)
+      for (int x = 0; x < D; ++x) rad[r] += 0.5 * cs * std::fabs(b.R[3 * r + x]);
+    for (int cz = lo_c[2]; cz <= hi_c[2]; ++cz)
+      for (int cy = lo_c[1]; cy <= hi_c[1]; ++cy) {
+        int run0 = -1;
+        for (int cx = lo_c[0]; cx <= hi_c[0] + 1; ++cx) {
+          bool keep = false;
+          if (cx <= hi_c[0]) {
+            const int cc[3] = {cx, cy, cz};
+            double ctr[3] = {0, 0, 0};
+            for (int x = 0; x < D; ++x) ctr[x] = d->desc.lo[x] + (cc[x] + 0.5) * cs - b.origin[x];
+            keep = true;
+            for (int r = 0; r < D; ++r) {
+              double X = 0;
+              for (int x = 0; x < D; ++x) X += b.R[3 * r + x] * ctr[x];
+              if (std::fabs(X) > half[r] + rad[r]) keep = false;
+            }
+          }
+          const int lin = (cz * d->dims[1] + cy) * d->dims[0] + cx;
+          if (keep && run0 < 0) run0 = lin;
+          if (!keep && run0 >= 0) {
+            seg.push_back(run0);
+            seg.push_back(lin);
+            segbuf.push_back((int)k);
+            run0 = -1;
+          }
+        }
+      }
+  }
+  if (d->seg_mem) {
+    cudaFree(d->seg_mem);
+    d->seg_mem = nullptr;
+  }
+  const size_t nseg = segbuf.size();
+  const size_t bytes = (2 * nseg + nseg) * sizeof(int);
+  CK(cudaMalloc(&d->seg_mem, std::max<size_t>(bytes, 16)));
+  int* p = static_cast<int*>(d->seg_mem);
+  if (nseg) {
+    CK(cudaMemcpy(p, seg.data(), 2 * nseg * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p + 2 * nseg, segbuf.data(), nseg * sizeof(int), cudaMemcpyHostToDevice));
+  }
+  d->dev.seg_lin = p;
+  d->dev.seg_buf = p + 2 * nseg;
+  d->dev.nseg = (int)nseg;
+  d->seg_host = seg;
+  d->segbuf_host = segbuf;
+  return SPHBUF_OK;
+}
+
+template <typename T>
+sphbuf_status set_state_field(sphbuf_domain* d, size_t offset, T value) {
+  CK(cudaMemcpyAsync(reinterpret_cast<char*>(d->dev.st) + offset, &value, sizeof(T), cudaMemcpyHostToDevice,
+                     d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  return SPHBUF_OK;
+}
+
+sphbuf_status read_state(sphbuf_domain* d, StepState* out) {
+  CK(cudaStreamSynchronize(d->stream));
+  CK(cudaMemcpy(out, d->dev.st, sizeof(StepState), cudaMemcpyDeviceToHost));
+  if (out->status) {
+    const char* what = out->status == SPHBUF_ERR_CAPACITY ? "particle or decision-list capacity exceeded"
+                       : out->status == SPHBUF_ERR_NAN    ? "non-finite particle position"
+                                                          : "device-side error";
+    return fail(d, (sphbuf_status)out->status, what);
+  }
+  return SPHBUF_OK;
+}
+
+sphbuf_status commit(sphbuf_domain* d) {
+  sphbuf_status s;
+  if (!d->committed) {
+    if ((s = upload_buffers(d)) != SPHBUF_OK) return s;
+    if ((s = build_segments(d)) != SPHBUF_OK) return s;
+    if (!d->dev.W.start) {
+      // no walls: an empty wall list
+      unsigned* ws = nullptr;
+      CK(dalloc(d, &ws, (size_t)d->ncell + 1));
+      CK(cudaMemset(ws, 0, ((size_t)d->ncell + 1) * sizeof(unsigned)));
+      d->dev.W.start = ws;
+    }
+    d->committed = true;
+  }
+  if (d->need_rebuild) {
+    if (!d->labels_given) d->launches += launch_identify(d->dev, d->stream);
+    d->launches += launch_rebuild(d->dev, false, d->stream);
+    CK(cudaGetLastError());
+    d->need_rebuild = false;
+  }
+  return SPHBUF_OK;
+}
+
+// Enqueues the kernels of one step; returns the number of kernels launched.
+int enqueue_step(sphbuf_domain* d, unsigned phases, bool timed) {
+  const DomainDev& v = d->dev;
+  cudaStream_t s = d->stream;
+  int k = 0;
+  if (timed) cudaEventRecord(d->ev[0], s);
+  if (phases & SPHBUF_PHASE_PHYSICS) {
+    k += launch_density(v, s);
+    if (timed) cudaEventRecord(d->ev[1], s);
+    k += launch_force(v, s);
+  } else {
+    k += launch_drift(v, s);
+    if (timed) cudaEventRecord(d->ev[1], s);
+  }
+  if (timed) cudaEventRecord(d->ev[2], s);
+  if (phases & SPHBUF_PHASE_BUFFER) {
+    k += launch_decide(v, (phases & SPHBUF_PHASE_FULL_CHECK) != 0, s);
+    if (timed) cudaEventRecord(d->ev[3], s);
+    k += launch_apply(v, s);
+  } else if (timed) {
+    cudaEventRecord(d->ev[3], s);
+  }
+  if (timed) cudaEventRecord(d->ev[4], s);
+  k += launch_rebuild(v, true, s);
+  if (timed) cudaEventRecord(d->ev[5], s);
+  return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sphbuf_status_string(sphbuf_status s) {
+  switch (s) {
+    case SPHBUF_OK: return "ok";
+    case SPHBUF_ERR_INVALID_ARG: return "invalid argument";
+    case SPHBUF_ERR_CAPACITY: return "capacity exceeded";
+    case SPHBUF_ERR_OVERLAP: return "buffer regions overlap";
+    case SPHBUF_ERR_CUDA: return "CUDA error";
+    case SPHBUF_ERR_TIMEOUT: return "device wait timed out";
+    case SPHBUF_ERR_NAN: return "non-finite value";
+    case SPHBUF_ERR_STATE: return "call not valid in the current state";
+  }
+  return "unknown status";
+}
+
+const char* sphbuf_error_message(sphbuf_domain_t d) { return d ? d->err.c_str() : ""; }
+
+sphbuf_status sphbuf_create_domain(const sphbuf_domain_desc* desc, void* cuda_stream, sphbuf_domain_t* out) {
+  if (!desc || !out) return SPHBUF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (desc->dim != 2 && desc->dim != 3) return SPHBUF_ERR_INVALID_ARG;
+  if (!(desc->dp > 0) || !(desc->h_over_dp > 0) || !(desc->rho0 > 0) || !(desc->c0 > 0) || !(desc->dt > 0) ||
+      !(desc->nu >= 0) || desc->capacity == 0 || desc->capacity >= 0xF0000000ull)
+    return SPHBUF_ERR_INVALID_ARG;
+  auto* d = new sphbuf_domain();
+  d->desc = *desc;
+  const int D = desc->dim;
+  d->cs = 2.0 * (desc->h_over_dp * desc->dp);
+  d->cs32 = (float)d->cs;
+  for (int x = 0; x < 3; ++x) {
+    if (x < D) {
+      if (!(desc->hi[x] > desc->lo[x])) {
+        delete d;
+        return SPHBUF_ERR_INVALID_ARG;
+      }
+      d->dims[x] = (int)std::ceil((desc->hi[x] - desc->lo[x]) / d->cs);
+    } else {
+      d->dims[x] = 1;
+    }
+  }
+  d->ncell = (long long)d->dims[0] * d->dims[1] * d->dims[2];
+  if (d->ncell >= (1ll << 31) - kScanTile) {
+    delete d;
+    return SPHBUF_ERR_INVALID_ARG;
+  }
+  cudaGetDevice(&d->device);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d->device);
+  if (cuda_stream) {
+    d->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&d->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete d;
+      return SPHBUF_ERR_CUDA;
+    }
+    d->own_stream = true;
+  }
+  DomainDev& v = d->dev;
+  v.sm_count = sms > 0 ? sms : 1;
+  v.g.dim = D;
+  v.g.nx = d->dims[0];
+  v.g.ny = d->dims[1];
+  v.g.nz = d->dims[2];
+  v.g.ncell = d->ncell;
+  v.g.cs = d->cs32;
+  const double h = desc->h_over_dp * desc->dp;
+  Phys& P = v.P;
+  P.h = (float)h;
+  P.inv_h = (float)(1.0 / h);
+  P.two_h_sq = (float)(4.0 * h * h);
+  P.alpha = (float)wendland_alpha(D, h);
+  P.rho0 = (float)desc->rho0;
+  P.c0 = (float)desc->c0;
+  P.c0sq = (float)(desc->c0 * desc->c0);
+  P.eta = (float)(desc->rho0 * desc->nu);
+  d->mass_d = desc->rho0 * std::pow(desc->dp, D);
+  P.mass = (float)d->mass_d;
+  P.dt = (float)desc->dt;
+  P.inv_sum_w0 = (float)(1.0 / lattice_sum_w0(D, desc->dp, h));
+  P.w_self = (float)wendland_w(0.0, h, D);
+  P.rho0_d = desc->rho0;
+  P.c0sq_d = desc->c0 * desc->c0;
+  P.dt_d = desc->dt;
+  P.capacity = (unsigned)desc->capacity;
+  P.list_cap = (unsigned)std::max<uint64_t>(1024, std::min<uint64_t>(desc->capacity, 1ull << 22));
+  const size_t C = desc->capacity;
+  v.ncell_pad = (d->ncell + 1 + kScanTile - 1) / kScanTile * kScanTile;
+  v.scan_tiles = (int)(v.ncell_pad / kScanTile);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  for (Particles* p : {&v.A, &v.B}) {
+    A(dalloc(d, &p->cell, C));
+    for (int x = 0; x < 3; ++x) {
+      p->f[x] = nullptr;
+      p->v[x] = nullptr;
+      if (x < D) {
+        A(dalloc(d, &p->f[x], C));
+        A(dalloc(d, &p->v[x], C));
+      }
+    }
+    A(dalloc(d, &p->rho, C));
+    A(dalloc(d, &p->id, C));
+    A(dalloc(d, &p->label, C));
+  }
+  A(dalloc(d, &v.rho_new, C));
+  A(dalloc(d, &v.slot, C));
+  A(dalloc(d, &v.tmp_id, C));
+  A(dalloc(d, &v.cell_start, (size_t)v.ncell_pad + 1));
+  A(dalloc(d, &v.cnt, (size_t)v.ncell_pad));
+  A(dalloc(d, &v.scan_part, (size_t)v.scan_tiles));
+  A(dalloc(d, &v.inj, P.list_cap));
+  A(dalloc(d, &v.del, P.list_cap));
+  A(dalloc(d, &v.inj_sorted, P.list_cap));
+  BufDev* bd = nullptr;
+  A(dalloc(d, &bd, kMaxBuffers));
+  v.bufs = bd;
+  int* rel = nullptr;
+  A(dalloc(d, &rel, kMaxBuffers));
+  v.relabel_ids = rel;
+  A(dalloc(d, &v.st, 1));
+  if (e == cudaSuccess) {
+    A(cudaMemset(v.cnt, 0, (size_t)v.ncell_pad * sizeof(unsigned)));
+    A(cudaMemset(v.cell_start, 0, ((size_t)v.ncell_pad + 1) * sizeof(unsigned)));
+    A(cudaMemset(v.st, 0, sizeof(StepState)));
+  }
+  for (int q = 0; q <= kPhases && e == cudaSuccess; ++q) A(cudaEventCreate(&d->ev[q]));
+  if (e != cudaSuccess) {
+    sphbuf_destroy(d);
+    return SPHBUF_ERR_CUDA;
+  }
+  *out = d;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_destroy(sphbuf_domain_t d) {
+  if (!d) return SPHBUF_ERR_INVALID_ARG;
+  if (d->stream) cudaStreamSynchronize(d->stream);
+  if (d->graph) cudaGraphExecDestroy(d->graph);
+  for (void* p : d->allocs) cudaFree(p);
+  if (d->seg_mem) cudaFree(d->seg_mem);
+  for (int q = 0; q <= kPhases; ++q)
+    if (d->ev[q]) cudaEventDestroy(d->ev[q]);
+  if (d->own_stream) cudaStreamDestroy(d->stream);
+  delete d;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_set_walls(sphbuf_domain_t d, const double* pos, uint64_t n) {
+  if (!d || (!pos && n)) return SPHBUF_ERR_INVALID_ARG;
+  if (d->stepped) return fail(d, SPHBUF_ERR_STATE, "walls must be set before the first step");
+  const int D = d->desc.dim;
+  std::vector<int> cell(n);
+  std::vector<float> f((size_t)n * 3, 0.f);
+  for (uint64_t i = 0; i < n; ++i) {
+    int c[3] = {0, 0, 0};
+    for (int x = 0; x < D; ++x)
+      if (!encode_axis(pos[i * D + x], d->desc.lo[x], d->cs, d->cs32, d->dims[x], &c[x], &f[i * 3 + x]))
+        return fail(d, SPHBUF_ERR_INVALID_ARG, "wall particle outside the grid box");
+    cell[i] = (c[2] * d->dims[1] + c[1]) * d->dims[0] + c[0];
+  }
+  std::vector<uint64_t> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](uint64_t a, uint64_t b) { return cell[a] < cell[b]; });
+  std::vector<unsigned> start((size_t)d->ncell + 1, 0);
+  for (uint64_t i = 0; i < n; ++i) start[cell[i] + 1]++;
+  for (long long c = 0; c < d->ncell; ++c) start[c + 1] += start[c];
+  std::vector<int> sc(n);
+  std::vector<float> sf[3];
+  for (int x = 0; x < D; ++x) sf[x].resize(n);
+  for (uint64_t p = 0; p < n; ++p) {
+    sc[p] = cell[order[p]];
+    for (int x = 0; x < D; ++x) sf[x][p] = f[order[p] * 3 + x];
+  }
+  if (d->wall_mem) {
+    cudaFree(d->wall_mem);
+    d->wall_mem = nullptr;
+  }
+  const size_t nn = std::max<uint64_t>(n, 1);
+  const size_t bytes = nn * sizeof(int) + 3 * nn * sizeof(float) + ((size_t)d->ncell + 1) * sizeof(unsigned) + 64;
+  CK(cudaMalloc(&d->wall_mem, bytes));
+  char* p = static_cast<char*>(d->wall_mem);
+  int* wc = reinterpret_cast<int*>(p);
+  float* wf = reinterpret_cast<float*>(p + nn * sizeof(int));
+  unsigned* ws = reinterpret_cast<unsigned*>(p + nn * sizeof(int) + 3 * nn * sizeof(float));
+  if (n) CK(cudaMemcpy(wc, sc.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+  for (int x = 0; x < D; ++x)
+    if (n) CK(cudaMemcpy(wf + x * nn, sf[x].data(), n * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ws, start.data(), start.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
+  d->dev.W.cell = wc;
+  for (int x = 0; x < 3; ++x) d->dev.W.f[x] = x < D ? wf + x * nn : nullptr;
+  d->dev.W.start = ws;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_write_particles(sphbuf_domain_t d, const int32_t* cell, const float* frac, const float* vel,
+                                     const float* rho, const uint32_t* id, const uint8_t* label, uint64_t n,
+                                     uint32_t next_id) {
+  if (!d || (n && (!cell || !frac || !vel || !rho))) return SPHBUF_ERR_INVALID_ARG;
+  if (n > d->desc.capacity) return fail(d, SPHBUF_ERR_CAPACITY, "more particles than the domain capacity");
+  const int D = d->desc.dim;
+  std::vector<float> tf[3], tv[3];
+  for (int x = 0; x < D; ++x) {
+    tf[x].resize(n);
+    tv[x].resize(n);
+  }
+  uint32_t max_id = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    if (cell[i] < 0 || (long long)cell[i] >= d->ncell)
+      return fail(d, SPHBUF_ERR_INVALID_ARG, "cell index outside the grid");
+    for (int x = 0; x < D; ++x) {
+      const float f = frac[i * D + x];
+      if (!(f >= 0.f && f < d->cs32)) return fail(d, SPHBUF_ERR_INVALID_ARG, "in-cell offset outside [0, cs)");
+      tf[x][i] = f;
+      tv[x][i] = vel[i * D + x];
+    }
+    if (label && label[i] != 0 && (label[i] == kDead || (size_t)label[i] > d->bufs.size()))
+      return fail(d, SPHBUF_ERR_INVALID_ARG, "label names no buffer");
+    max_id = std::max(max_id, id ? id[i] : (uint32_t)i);
+  }
+  if (n && next_id <= max_id) return fail(d, SPHBUF_ERR_INVALID_ARG, "next_id must exceed every id");
+  CK(cudaStreamSynchronize(d->stream));
+  Particles& B = d->dev.B;
+  if (n) {
+    CK(cudaMemcpy(B.cell, cell, n * sizeof(int), cudaMemcpyHostToDevice));
+    for (int x = 0; x < D; ++x) {
+      CK(cudaMemcpy(B.f[x], tf[x].data(), n * sizeof(float), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(B.v[x], tv[x].data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(B.rho, rho, n * sizeof(float), cudaMemcpyHostToDevice));
+    if (id) {
+      CK(cudaMemcpy(B.id, id, n * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    } else {
+      std::vector<uint32_t> ids(n);
+      std::iota(ids.begin(), ids.end(), 0u);
+      CK(cudaMemcpy(B.id, ids.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    }
+    if (label)
+      CK(cudaMemcpy(B.label, label, n, cudaMemcpyHostToDevice));
+    else
+      CK(cudaMemset(B.label, 0, n));
+  }
+  StepState st;
+  CK(cudaMemcpy(&st, d->dev.st, sizeof(StepState), cudaMemcpyDeviceToHost));
+  st.n = (unsigned)n;
+  st.n_inj = 0;
+  st.n_del = 0;
+  st.next_id = next_id;
+  st.status = 0;
+  CK(cudaMemcpy(d->dev.st, &st, sizeof(StepState), cudaMemcpyHostToDevice));
+  d->labels_given = label != nullptr;
+  d->need_rebuild = true;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_set_fluid(sphbuf_domain_t d, const double* pos, const float* vel, const float* rho, uint64_t n) {
+  if (!d || (n && (!pos || !vel || !rho))) return SPHBUF_ERR_INVALID_ARG;
+  if (d->stepped) return fail(d, SPHBUF_ERR_STATE, "set_fluid is only valid before the first step");
+  const int D = d->desc.dim;
+  std::vector<int32_t> cell(n);
+  std::vector<float> f((size_t)n * D);
+  for (uint64_t i = 0; i < n; ++i) {
+    int c[3] = {0, 0, 0};
+    for (int x = 0; x < D; ++x)
+      if (!encode_axis(pos[i * D + x], d->desc.lo[x], d->cs, d->cs32, d->dims[x], &c[x], &f[i * D + x]))
+        return fail(d, SPHBUF_ERR_INVALID_ARG, "fluid particle outside the grid box");
+    cell[i] = (c[2] * d->dims[1] + c[1]) * d->dims[0] + c[0];
+  }
+  return sphbuf_write_particles(d, cell.data(), f.data(), vel, rho, nullptr, nullptr, n, (uint32_t)n);
+}
+
+sphbuf_status sphbuf_rotation_from_normal(const double normal[3], double roll, double out_R[9]) {
+  if (!normal || !out_R) return SPHBUF_ERR_INVALID_ARG;
+  const double nn = std::sqrt(normal[0] * normal[0] + normal[1] * normal[1] + normal[2] * normal[2]);
+  if (!(nn > 0) || !std::isfinite(nn)) return SPHBUF_ERR_INVALID_ARG;
+  const double dvec[3] = {normal[0] / nn, normal[1] / nn, normal[2] / nn};
+  // Eq. (12): n = e_x x d / |e_x x d| = (0, -d_z, d_y) / |.|
+  const double ax[3] = {0.0, -dvec[2], dvec[1]};
+  const double an = std::sqrt(ax[1] * ax[1] + ax[2] * ax[2]);
+  double R[9];
+  if (an < 1e-12) {
+    for (int q = 0; q < 9; ++q) R[q] = 0;
+    if (dvec[0] > 0) {
+      R[0] = R[4] = R[8] = 1.0;
+    } else {
+      R[0] = -1.0;
+      R[4] = -1.0;
+      R[8] = 1.0;
+    }
+  } else {
+    const double n0 = ax[0] / an, n1 = ax[1] / an, n2 = ax[2] / an;
+    // Eq. (13)
+    const double S[9] = {0, -n2, n1, n2, 0, -n0, -n1, n0, 0};
+    double S2[9];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) S2[3 * r + c] = S[3 * r] * S[c] + S[3 * r + 1] * S[3 + c] + S[3 * r + 2] * S[6 + c];
+    const double th = std::acos(std::max(-1.0, std::min(1.0, dvec[0])));
+    const double sn = std::sin(th), cm = 1.0 - std::cos(th);
+    // Eq. (14) with the sign reading: R = I - S sin + S^2 (1 - cos), so that R d = e_x
+    for (int q = 0; q < 9; ++q) R[q] = ((q % 4) == 0 ? 1.0 : 0.0) - S[q] * sn + S2[q] * cm;
+  }
+  const double c = std::cos(roll), s = std::sin(roll);
+  const double Rx[9] = {1, 0, 0, 0, c, s, 0, -s, c};
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < 3; ++q) out_R[3 * r + q] = Rx[3 * r] * R[q] + Rx[3 * r + 1] * R[3 + q] + Rx[3 * r + 2] * R[6 + q];
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_add_inout_buffer(sphbuf_domain_t d, const double origin[3], const double rotation[9],
+                                      const double extent[3], sphbuf_bc_type bc, const sphbuf_bc_params* params,
+                                      int* out_id) {
+  if (!d || !origin || !rotation || !extent) return SPHBUF_ERR_INVALID_ARG;
+  if (d->stepped || d->committed) return fail(d, SPHBUF_ERR_STATE, "buffers must be added before the first step");
+  if ((int)bc < 0 || (int)bc > 5) return fail(d, SPHBUF_ERR_INVALID_ARG, "unknown boundary type");
+  if (d->bufs.size() >= (size_t)kMaxBuffers) return fail(d, SPHBUF_ERR_CAPACITY, "too many buffers");
+  const int D = d->desc.dim;
+  BufHost b{};
+  std::memcpy(b.origin, origin, sizeof(b.origin));
+  std::memcpy(b.R, rotation, sizeof(b.R));
+  std::memcpy(b.extent, extent, sizeof(b.extent));
+  if (D == 2) {
+    b.origin[2] = 0;
+    b.extent[2] = 0;
+    b.R[2] = b.R[5] = b.R[6] = b.R[7] = 0;
+    b.R[8] = 1;
+  }
+  b.bc = (int)bc;
+  if (params) b.prm = *params;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double dot = 0;
+      for (int x = 0; x < 3; ++x) dot += b.R[3 * r + x] * b.R[3 * c + x];
+      if (std::fabs(dot - (r == c ? 1.0 : 0.0)) > 1e-9) return fail(d, SPHBUF_ERR_INVALID_ARG, "frame not orthonormal");
+    }
+  const double det = b.R[0] * (b.R[4] * b.R[8] - b.R[5] * b.R[7]) - b.R[1] * (b.R[3] * b.R[8] - b.R[5] * b.R[6]) +
+                     b.R[2] * (b.R[3] * b.R[7] - b.R[4] * b.R[6]);
+  if (det < 0) return fail(d, SPHBUF_ERR_INVALID_ARG, "frame is not a rotation (det < 0)");
+  for (int x = 0; x < D; ++x)
+    if (!(b.extent[x] > 0)) return fail(d, SPHBUF_ERR_INVALID_ARG, "extent must be positive");
+  // candidate regions (box dilated by 2 cs) must not overlap
+  const double dil = 2.0 * d->cs;
+  const double h1[3] = {0.5 * b.extent[0] + dil, 0.5 * b.extent[1] + dil, D == 3 ? 0.5 * b.extent[2] + dil : 0};
+  for (const BufHost& o : d->bufs) {
+    const double h2[3] = {0.5 * o.extent[0] + dil, 0.5 * o.extent[1] + dil, D == 3 ? 0.5 * o.extent[2] + dil : 0};
+    if (obb_overlap(D, b.origin, b.R, h1, o.origin, o.R, h2))
+      return fail(d, SPHBUF_ERR_OVERLAP, "candidate regions of two buffers overlap");
+  }
+  const int k = (int)d->bufs.size();
+  BufDev v{};
+  v.kind = (bc == SPHBUF_VELOCITY_INLET || bc == SPHBUF_PRESSURE_INLET) ? KIND_INFLOW
+           : (bc == SPHBUF_PRESSURE_OUTLET || bc == SPHBUF_VELOCITY_OUTLET) ? KIND_OUTFLOW
+                                                                              : KIND_BIDIR;
+  v.vel_bc = (bc == SPHBUF_VELOCITY_INLET || bc == SPHBUF_VELOCITY_OUTLET || bc == SPHBUF_BIDIR_VELOCITY) ? 1 : 0;
+  v.label = k + 1;
+  const double cs = d->cs;
+  for (int x = 0; x < 3; ++x) {
+    v.cO[x] = 0;
+    v.fO[x] = 0.f;
+    if (x < D) {
+      const double t = b.origin[x] - d->desc.lo[x];
+      const double c = std::floor(t / cs);
+      v.cO[x] = (int)c;
+      v.fO[x] = (float)(t - c * cs);
+    }
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) v.R[r][c] = (float)b.R[3 * r + c];
+  const double a = b.extent[0];
+  v.ha = (float)(0.5 * a);
+  v.hb = (float)(0.5 * b.extent[1]);
+  v.hc = (float)(0.5 * b.extent[2]);
+  v.da = (float)(0.5 * a + cs);
+  v.db = (float)(0.5 * b.extent[1] + cs);
+  v.dc = (float)(0.5 * b.extent[2] + cs);
+  for (int x = 0; x < 3; ++x) {
+    v.shift[x] = x < D ? (float)(-a * b.R[x]) : 0.f;
+    v.u[x] = x < D ? (float)b.R[x] : 0.f;
+  }
+  v.umax = (float)b.prm.umax;
+  v.inv_hw2 = b.prm.half_width > 0 ? (float)(1.0 / (b.prm.half_width * b.prm.half_width)) : 0.f;
+  v.flux_scale = (float)(std::pow(d->desc.dp, D) / a);
+  // cell bounds that contain the box (with one cell of margin): relabel prefilter
+  for (int x = 0; x < 3; ++x) {
+    if (x >= D) {
+      v.box_lo[x] = 0;
+      v.box_hi[x] = 0;
+      continue;
+    }
+    double ext = 0;
+    for (int r = 0; r < D; ++r) ext += 0.5 * b.extent[r] * std::fabs(b.R[3 * r + x]);
+    v.box_lo[x] = (int)std::floor((b.origin[x] - ext - d->desc.lo[x]) / cs) - 1;
+    v.box_hi[x] = (int)std::floor((b.origin[x] + ext - d->desc.lo[x]) / cs) + 1;
+  }
+  v.p_b0 = b.prm.p_b;
+  v.p_amp = b.prm.p_amp;
+  v.p_omega = b.prm.p_omega;
+  v.p_phase = b.prm.p_phase;
+  d->bufs.push_back(b);
+  d->bufs_dev.push_back(v);
+  if (out_id) *out_id = k;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_step_phases(sphbuf_domain_t d, int nsteps, unsigned phases) {
+  if (!d || nsteps < 0) return SPHBUF_ERR_INVALID_ARG;
+  const bool phys = phases & SPHBUF_PHASE_PHYSICS, kin = phases & SPHBUF_PHASE_KINEMATIC;
+  if (phys == kin) return fail(d, SPHBUF_ERR_INVALID_ARG, "exactly one of PHYSICS or KINEMATIC is required");
+  if (phases & ~15u) return fail(d, SPHBUF_ERR_INVALID_ARG, "unknown phase bits");
+  if (!d->committed && !d->need_rebuild) return fail(d, SPHBUF_ERR_STATE, "no particles written");
+  sphbuf_status s = commit(d);
+  if (s != SPHBUF_OK) return s;
+  d->stepped = true;
+  for (int q = 0; q < nsteps; ++q) {
+    if (d->timing) {
+      d->launches += enqueue_step(d, phases, true);
+      CK(cudaEventSynchronize(d->ev[kPhases]));
+      for (int p = 0; p < kPhases; ++p) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, d->ev[p], d->ev[p + 1]));
+        d->acc_ms[p] += ms;
+      }
+      d->timed_steps++;
+    } else if (d->use_graph) {
+      if (!d->graph || d->graph_phases != phases) {
+        if (d->graph) {
+          cudaGraphExecDestroy(d->graph);
+          d->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal));
+        const int nk = enqueue_step(d, phases, false);
+        CK(cudaStreamEndCapture(d->stream, &g));
+        CK(cudaGraphInstantiate(&d->graph, g, 0));
+        cudaGraphDestroy(g);
+        d->graph_phases = phases;
+        d->graph_launches = (uint64_t)nk;
+      }
+      CK(cudaGraphLaunch(d->graph, d->stream));
+      d->launches += d->graph_launches;
+    } else {
+      d->launches += enqueue_step(d, phases, false);
+    }
+  }
+  CK(cudaGetLastError());
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_step(sphbuf_domain_t d, int nsteps) { return sphbuf_step_phases(d, nsteps, SPHBUF_STEP_DEFAULT); }
+
+sphbuf_status sphbuf_use_graph(sphbuf_domain_t d, int enable) {
+  if (!d) return SPHBUF_ERR_INVALID_ARG;
+  d->use_graph = enable != 0;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_sync(sphbuf_domain_t d) {
+  if (!d) return SPHBUF_ERR_INVALID_ARG;
+  if (!d->committed) {
+    CK(cudaStreamSynchronize(d->stream));
+    return SPHBUF_OK;
+  }
+  StepState st;
+  return read_state(d, &st);
+}
+
+sphbuf_status sphbuf_count(sphbuf_domain_t d, uint64_t* n) {
+  if (!d || !n) return SPHBUF_ERR_INVALID_ARG;
+  StepState st;
+  sphbuf_status s = read_state(d, &st);
+  *n = st.n;
+  return s;
+}
+
+sphbuf_status sphbuf_grid_info(sphbuf_domain_t d, int32_t dims[3], double* cs, uint64_t* ncell) {
+  if (!d) return SPHBUF_ERR_INVALID_ARG;
+  if (dims)
+    for (int x = 0; x < 3; ++x) dims[x] = d->dims[x];
+  if (cs) *cs = d->cs;
+  if (ncell) *ncell = (uint64_t)d->ncell;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_read_particles(sphbuf_domain_t d, int32_t* cell, float* frac, float* vel, float* rho,
+                                    uint32_t* id, uint8_t* label, uint64_t cap, uint64_t* n_out) {
+  if (!d) return SPHBUF_ERR_INVALID_ARG;
+  if (d->need_rebuild) {
+    sphbuf_status s = commit(d);
+    if (s != SPHBUF_OK) return s;
+  }
+  StepState st;
+  sphbuf_status s = read_state(d, &st);
+  if (s != SPHBUF_OK) return s;
+  const uint64_t n = st.n;
+  if (n_out) *n_out = n;
+  if (n > cap && (cell || frac || vel || rho || id || label))
+    return fail(d, SPHBUF_ERR_CAPACITY, "host arrays smaller than the particle count");
+  const int D = d->desc.dim;
+  const Particles& A = d->dev.A;
+  if (!n) return SPHBUF_OK;
+  if (cell) CK(cudaMemcpy(cell, A.cell, n * sizeof(int), cudaMemcpyDeviceToHost));
+  std::vector<float> tmp(n);
+  for (int x = 0; x < D; ++x) {
+    if (frac) {
+      CK(cudaMemcpy(tmp.data(), A.f[x], n * sizeof(float), cudaMemcpyDeviceToHost));
+      for (uint64_t i = 0; i < n; ++i) frac[i * D + x] = tmp[i];
+    }
+    if (vel) {
+      CK(cudaMemcpy(tmp.data(), A.v[x], n * sizeof(float), cudaMemcpyDeviceToHost));
+      for (uint64_t i = 0; i < n; ++i) vel[i * D + x] = tmp[i];
+    }
+  }
+  if (rho) CK(cudaMemcpy(rho, A.rho, n * sizeof(float), cudaMemcpyDeviceToHost));
+  if (id) CK(cudaMemcpy(id, A.id, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (label) CK(cudaMemcpy(label, A.label, n, cudaMemcpyDeviceToHost));
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_read_positions(sphbuf_domain_t d, double* pos, uint64_t cap, uint64_t* n_out) {
+  if (!d) return SPHBUF_ERR_INVALID_ARG;
+  StepState st;
+  sphbuf_status s = read_state(d, &st);
+  if (s != SPHBUF_OK) return s;
+  const uint64_t n = st.n;
+  if (n_out) *n_out = n;
+  if (!pos || !n) return SPHBUF_OK;
+  if (n > cap) return fail(d, SPHBUF_ERR_CAPACITY, "host array smaller than the particle count");
+  double* tmp = nullptr;
+  CK(cudaMalloc(&tmp, n * d->desc.dim * sizeof(double)));
+  launch_decode_positions(d->dev, tmp, d->desc.lo, d->cs, d->stream);
+  cudaError_t e = cudaStreamSynchronize(d->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(pos, tmp, n * d->desc.dim * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(d, e, "read_positions");
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_read_cell_start(sphbuf_domain_t d, uint32_t* cell_start, uint64_t cap) {
+  if (!d || !cell_start) return SPHBUF_ERR_INVALID_ARG;
+  if (cap < (uint64_t)d->ncell + 1) return fail(d, SPHBUF_ERR_CAPACITY, "cell_start needs ncell + 1 entries");
+  StepState st;
+  sphbuf_status s = read_state(d, &st);
+  if (s != SPHBUF_OK) return s;
+  CK(cudaMemcpy(cell_start, d->dev.cell_start, ((size_t)d->ncell + 1) * sizeof(unsigned), cudaMemcpyDeviceToHost));
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_read_counters(sphbuf_domain_t d, int k, uint64_t* injected, uint64_t* deleted, double* mass_in,
+                                   double* mass_out, double* flux_q) {
+  if (!d || k < 0 || (size_t)k >= d->bufs.size()) return SPHBUF_ERR_INVALID_ARG;
+  StepState st;
+  sphbuf_status s = read_state(d, &st);
+  if (s != SPHBUF_OK) return s;
+  if (injected) *injected = st.injected[k];
+  if (deleted) *deleted = st.deleted[k];
+  if (mass_in) *mass_in = (double)st.injected[k] * d->mass_d;
+  if (mass_out) *mass_out = (double)st.deleted[k] * d->mass_d;
+  if (flux_q) *flux_q = st.flux[k];
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_read_global(sphbuf_domain_t d, uint64_t* escaped, uint64_t* steps, uint32_t* next_id) {
+  if (!d) return SPHBUF_ERR_INVALID_ARG;
+  StepState st;
+  sphbuf_status s = read_state(d, &st);
+  if (escaped) *escaped = st.escaped_total;
+  if (steps) *steps = st.step;
+  if (next_id) *next_id = st.next_id;
+  return s;
+}
+
+sphbuf_status sphbuf_last_decisions(sphbuf_domain_t d, uint32_t* inj_buffer, uint32_t* inj_parent, uint32_t* inj_new,
+                                    uint64_t* n_inj, uint32_t* del_buffer, uint32_t* del_id, uint64_t* n_del,
+                                    uint64_t cap) {
+  if (!d) return SPHBUF_ERR_INVALID_ARG;
+  StepState st;
+  sphbuf_status s = read_state(d, &st);
+  if (s != SPHBUF_OK) return s;
+  const uint64_t ni = std::min(st.n_inj, d->dev.P.list_cap), nd = std::min(st.n_del, d->dev.P.list_cap);
+  if (n_inj) *n_inj = ni;
+  if (n_del) *n_del = nd;
+  if ((ni > cap && (inj_buffer || inj_parent || inj_new)) || (nd > cap && (del_buffer || del_id)))
+    return fail(d, SPHBUF_ERR_CAPACITY, "host arrays smaller than the decision lists");
+  if (ni && (inj_buffer || inj_parent || inj_new)) {
+    std::vector<InjRecord> r(ni);
+    CK(cudaMemcpy(r.data(), d->dev.inj_sorted, ni * sizeof(InjRecord), cudaMemcpyDeviceToHost));
+    for (uint64_t q = 0; q < ni; ++q) {
+      if (inj_buffer) inj_buffer[q] = r[q].k;
+      if (inj_parent) inj_parent[q] = r[q].parent;
+      if (inj_new) inj_new[q] = r[q].child;
+    }
+  }
+  if (nd && (del_buffer || del_id)) {
+    std::vector<Decision> r(nd);
+    CK(cudaMemcpy(r.data(), d->dev.del, nd * sizeof(Decision), cudaMemcpyDeviceToHost));
+    for (uint64_t q = 0; q < nd; ++q) {
+      if (del_buffer) del_buffer[q] = r[q].k;
+      if (del_id) del_id[q] = r[q].id;
+    }
+  }
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_enable_phase_timing(sphbuf_domain_t d, int enable) {
+  if (!d) return SPHBUF_ERR_INVALID_ARG;
+  d->timing = enable != 0;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_read_phase_times(sphbuf_domain_t d, double ms[5], uint64_t* steps) {
+  if (!d || !ms) return SPHBUF_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(d->stream));
+  for (int p = 0; p < kPhases; ++p) {
+    ms[p] = d->acc_ms[p];
+    d->acc_ms[p] = 0;
+  }
+  if (steps) *steps = d->timed_steps;
+  d->timed_steps = 0;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_candidate_count(sphbuf_domain_t d, int k, uint64_t* cells, uint64_t* particles) {
+  if (!d || k < 0 || (size_t)k >= d->bufs.size()) return SPHBUF_ERR_INVALID_ARG;
+  if (!d->committed) return fail(d, SPHBUF_ERR_STATE, "no cell-linked list yet");
+  StepState st;
+  sphbuf_status s = read_state(d, &st);
+  if (s != SPHBUF_OK) return s;
+  std::vector<unsigned> start((size_t)d->ncell + 1);
+  CK(cudaMemcpy(start.data(), d->dev.cell_start, start.size() * sizeof(unsigned), cudaMemcpyDeviceToHost));
+  uint64_t nc = 0, np = 0;
+  for (size_t q = 0; q < d->segbuf_host.size(); ++q) {
+    if (d->segbuf_host[q] != k) continue;
+    const int l0 = d->seg_host[2 * q], l1 = d->seg_host[2 * q + 1];
+    nc += (uint64_t)(l1 - l0);
+    np += start[l1] - start[l0];
+  }
+  if (cells) *cells = nc;
+  if (particles) *particles = np;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_read_launch_count(sphbuf_domain_t d, uint64_t* launches) {
+  if (!d || !launches) return SPHBUF_ERR_INVALID_ARG;
+  *launches = d->launches;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_cell_list_build(const int32_t* cell, const uint32_t* id, const uint8_t* label, uint64_t n,
+                                     uint64_t ncell, uint32_t* cell_start, uint32_t* order, void* cuda_stream) {
+  if ((n && (!cell || !id || !order)) || !cell_start || ncell == 0 || n >= 0xF0000000ull ||
+      ncell >= (1ull << 31) - kScanTile)
+    return SPHBUF_ERR_INVALID_ARG;
+  int bad = 0;
+  cudaError_t e = sphbuf::cell_list_build(cell, id, label, n, ncell, cell_start, order,
+                                          static_cast<cudaStream_t>(cuda_stream), &bad);
+  if (e != cudaSuccess) return SPHBUF_ERR_CUDA;
+  return bad ? SPHBUF_ERR_INVALID_ARG : SPHBUF_OK;
+}
+
+}  // extern "C"

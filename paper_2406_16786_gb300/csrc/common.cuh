@@ -1,0 +1,169 @@
+// Shared device-side definitions of the sphbuf library (GB300, sm_103a).
+//
+// Data layout in HBM (structure of arrays, one array per field, capacity-sized):
+//   cell  int32   linear cell index (cz * ny + cy) * nx + cx, cell size cs = 2h
+//   f[d]  float   offset inside the cell, [0, cs32)
+//   v[d]  float   velocity
+//   rho   float   density
+//   id    uint32  particle id
+//   label uint8   0 fluid, k + 1 buffer k, 255 dead (dropped by the next rebuild)
+// Two copies exist: A (sorted by (cell, id), read by the neighbour passes) and B (written
+// by the force/drift pass in A's order; new particles are appended; the rebuild sorts B
+// back into A).  Walls are a third, static, sorted set with their own cell_start.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sphbuf {
+
+constexpr int kMaxBuffers = 32;
+constexpr uint8_t kDead = 255;
+constexpr unsigned kNoSlot = 0xFFFFFFFFu;
+constexpr int kScanItems = 16;      // cells per thread in the scan kernels
+constexpr int kScanThreads = 256;
+constexpr int kScanTile = kScanItems * kScanThreads;
+
+enum Kind : int { KIND_INFLOW = 0, KIND_OUTFLOW = 1, KIND_BIDIR = 2 };
+
+// Per-buffer constants (FP32 copies follow the header's FP32 decision contract).
+struct BufDev {
+  int kind;
+  int vel_bc;          // 1 velocity BC, 0 pressure BC
+  int label;           // k + 1
+  int cO[3];
+  float fO[3];
+  float R[3][3];
+  float ha, hb, hc;    // a/2, b/2, c/2
+  float da, db, dc;    // a/2 + cs, b/2 + cs, c/2 + cs (outflow candidate region)
+  float shift[3];      // fl32(-a R[0][x]): recycling move
+  float u[3];          // FP32 boundary normal R^T e_x
+  float umax, inv_hw2; // velocity profile; inv_hw2 = 1/R^2, 0 = plug
+  float flux_scale;    // dp^d / a
+  int box_lo[3], box_hi[3];  // cell-coordinate bounds containing the box (relabel prefilter)
+  double p_b0, p_amp, p_omega, p_phase;
+};
+
+struct Grid {
+  int dim;
+  int nx, ny, nz;
+  long long ncell;
+  float cs;  // cs32
+};
+
+struct Phys {
+  float h, inv_h, two_h_sq, alpha, rho0, c0, c0sq, eta, mass, dt, inv_sum_w0, w_self;
+  double rho0_d, c0sq_d, dt_d;
+  unsigned capacity;
+  unsigned list_cap;
+};
+
+// Device-resident step bookkeeping (one per domain).
+struct StepState {
+  unsigned n;          // particles in the sorted arrays (A)
+  unsigned n_inj;      // injections of the current step
+  unsigned n_del;      // deletions of the current step
+  unsigned next_id;
+  unsigned long long step;
+  int status;          // latched error code (sphbuf_status), 0 = OK
+  unsigned long long escaped_total;
+  unsigned long long injected[kMaxBuffers];
+  unsigned long long deleted[kMaxBuffers];
+  float pb[kMaxBuffers];      // p_b(t_n)
+  float rho_pb[kMaxBuffers];  // fl32(rho0 + p_b(t_n) / c0^2)
+  double flux[kMaxBuffers];   // volume flux of the last step
+};
+
+struct Particles {
+  int* cell;
+  float* f[3];
+  float* v[3];
+  float* rho;
+  unsigned* id;
+  uint8_t* label;
+};
+
+struct Walls {
+  const int* cell;
+  const float* f[3];
+  const unsigned* start;  // wall cell_start[ncell + 1]
+};
+
+// Decision list entry: buffer k, particle index in B, particle id.
+struct Decision {
+  unsigned k;
+  unsigned idx;
+  unsigned id;
+};
+
+struct InjRecord {
+  unsigned k;
+  unsigned parent;
+  unsigned child;
+};
+
+__device__ __forceinline__ void latch(StepState* st, int code) { atomicCAS(&st->status, 0, code); }
+
+__device__ __forceinline__ void cell_coords(int lin, const Grid& g, int c[3]) {
+  c[0] = lin % g.nx;
+  int t = lin / g.nx;
+  c[1] = t % g.ny;
+  c[2] = t / g.ny;
+}
+
+// FP32 move + fold of the decision contract: f <- fl(f + delta), then at most 8 folds.
+// Returns false for a non-finite result.
+__device__ __forceinline__ bool move_fold(float& f, int& c, float delta, float cs) {
+  f = __fadd_rn(f, delta);
+#pragma unroll 1
+  for (int it = 0; it < 8; ++it) {
+    if (f >= cs) {
+      f = __fadd_rn(f, -cs);
+      c += 1;
+    } else if (f < 0.f) {
+      f = __fadd_rn(f, cs);
+      c -= 1;
+    } else {
+      break;
+    }
+  }
+  return isfinite(f);
+}
+
+// Local coordinates X' = R (X - O') in the contract's FP32 order, rows [0, nrow).
+template <int D>
+__device__ __forceinline__ void local_coords(const BufDev& b, const int c[3], const float f[3],
+                                             float cs, float X[3], int nrow) {
+  float Dl[3];
+#pragma unroll
+  for (int x = 0; x < D; ++x)
+    Dl[x] = __fadd_rn(__fmul_rn(__int2float_rn(c[x] - b.cO[x]), cs), __fadd_rn(f[x], -b.fO[x]));
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    if (r >= D || r >= nrow) break;
+    float acc = __fmul_rn(b.R[r][0], Dl[0]);
+    acc = __fadd_rn(acc, __fmul_rn(b.R[r][1], Dl[1]));
+    if (D == 3) acc = __fadd_rn(acc, __fmul_rn(b.R[r][2], Dl[2]));
+    X[r] = acc;
+  }
+}
+
+template <int D>
+__device__ __forceinline__ bool in_box(const BufDev& b, const float X[3]) {
+  bool in = fabsf(X[0]) < b.ha && fabsf(X[1]) < b.hb;
+  if (D == 3) in = in && fabsf(X[2]) < b.hc;
+  return in;
+}
+
+// Wendland C2: W = alpha (1 - q/2)^4 (2q + 1); dW/dr = -(5 alpha / h) q (1 - q/2)^3.
+__device__ __forceinline__ float kernel_w(float q, const Phys& P) {
+  float t = fmaxf(1.f - 0.5f * q, 0.f);
+  float t2 = t * t;
+  return P.alpha * t2 * t2 * (2.f * q + 1.f);
+}
+__device__ __forceinline__ float kernel_dw(float q, const Phys& P) {
+  float t = fmaxf(1.f - 0.5f * q, 0.f);
+  return -5.f * P.alpha * P.inv_h * q * t * t * t;
+}
+
+}  // namespace sphbuf

@@ -1,0 +1,321 @@
+// Cell-linked list rebuild (the end of each step, Sec. 3.1) as a counting sort, fused with the
+// relabelling of outflow and bidirectional buffers (Algorithms 2-3, after the rebuild).
+//
+//   hist    slot_i = atomicAdd(count[cell_i], 1) for every live particle of B
+//   scan    cell_start = exclusive prefix sum of count (3 passes over tiles of 4096 cells;
+//           count is re-zeroed on the way)
+//   keys    tmp_id[cell_start[cell_i] + slot_i] = id_i  (the cell's ids, in arbitrary order)
+//   scatter rank_i = #{ids of the same cell smaller than id_i}; A[cell_start + rank] = B[i]
+//           with the relabel test applied on the way
+// The result is sorted by (cell, id) whatever order the atomics took, so it is
+// deterministic and identical to a plain sort.
+#include "kernels.cuh"
+
+namespace sphbuf {
+
+namespace {
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const unsigned* __restrict__ cnt,
+                                                              unsigned* __restrict__ part,
+                                                              const int* status) {
+  if (status && *status) return;
+  const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
+  const uint4* p = reinterpret_cast<const uint4*>(cnt + base);
+  unsigned s = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems / 4; ++q) {
+    const uint4 v = p[q];
+    s += v.x + v.y + v.z + v.w;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  __shared__ unsigned ws[kScanThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) t += ws[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of the per-tile sums, one block.
+__global__ void __launch_bounds__(1024) k_scan_top(unsigned* part, int ntiles, const int* status) {
+  if (status && *status) return;
+  __shared__ unsigned ws[32];
+  __shared__ unsigned carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < ntiles; b0 += 1024) {
+    const int t = b0 + threadIdx.x;
+    const unsigned v = t < ntiles ? part[t] : 0u;
+    unsigned x = v;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      unsigned s = ws[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+        if (lane >= o) s += y;
+      }
+      ws[lane] = s;
+    }
+    __syncthreads();
+    const unsigned incl = x + (w > 0 ? ws[w - 1] : 0u);
+    if (t < ntiles) part[t] = carry + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += incl;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(unsigned* __restrict__ cnt,
+                                                            const unsigned* __restrict__ part,
+                                                            unsigned* __restrict__ start,
+                                                            const int* status) {
+  if (status && *status) return;
+  const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
+  uint4* p = reinterpret_cast<uint4*>(cnt + base);
+  unsigned v[kScanItems];
+#pragma unroll
+  for (int q = 0; q < kScanItems / 4; ++q) {
+    const uint4 t = p[q];
+    v[4 * q] = t.x;
+    v[4 * q + 1] = t.y;
+    v[4 * q + 2] = t.z;
+    v[4 * q + 3] = t.w;
+    p[q] = make_uint4(0, 0, 0, 0);
+  }
+  unsigned s = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) s += v[q];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  __shared__ unsigned ws[kScanThreads / 32];
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  unsigned wpre = 0;
+  for (int q = 0; q < w; ++q) wpre += ws[q];
+  unsigned run = part[blockIdx.x] + wpre + x - s;
+  uint4* o = reinterpret_cast<uint4*>(start + base);
+#pragma unroll
+  for (int q = 0; q < kScanItems / 4; ++q) {
+    uint4 t;
+    t.x = run;
+    run += v[4 * q];
+    t.y = run;
+    run += v[4 * q + 1];
+    t.z = run;
+    run += v[4 * q + 2];
+    t.w = run;
+    run += v[4 * q + 3];
+    o[q] = t;
+  }
+}
+
+void scan_cells(unsigned* cnt, unsigned* part, unsigned* start, int tiles, const int* status,
+                cudaStream_t s) {
+  k_scan_reduce<<<tiles, kScanThreads, 0, s>>>(cnt, part, status);
+  k_scan_top<<<1, 1024, 0, s>>>(part, tiles, status);
+  k_scan_down<<<tiles, kScanThreads, 0, s>>>(cnt, part, start, status);
+}
+
+__global__ void __launch_bounds__(256) k_hist(DomainDev d) {
+  if (d.st->status) return;
+  const unsigned n = d.st->n + d.st->n_inj;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (d.B.label[i] == kDead)
+      d.slot[i] = kNoSlot;
+    else
+      d.slot[i] = atomicAdd(d.cnt + d.B.cell[i], 1u);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_keys(DomainDev d) {
+  if (d.st->status) return;
+  const unsigned n = d.st->n + d.st->n_inj;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned sl = d.slot[i];
+    if (sl != kNoSlot) d.tmp_id[d.cell_start[d.B.cell[i]] + sl] = d.B.id[i];
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_scatter(DomainDev d) {
+  if (d.st->status) return;
+  const unsigned n = d.st->n + d.st->n_inj;
+  const Grid& g = d.g;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (d.slot[i] == kNoSlot) continue;
+    const int lin = d.B.cell[i];
+    const unsigned s0 = d.cell_start[lin], s1 = d.cell_start[lin + 1];
+    const unsigned my = d.B.id[i];
+    unsigned rank = 0;
+    for (unsigned p = s0; p < s1; ++p) rank += __ldg(d.tmp_id + p) < my;
+    const unsigned dst = s0 + rank;
+    float f[3];
+    d.A.cell[dst] = lin;
+#pragma unroll
+    for (int x = 0; x < D; ++x) {
+      f[x] = d.B.f[x][i];
+      d.A.f[x][dst] = f[x];
+      d.A.v[x][dst] = d.B.v[x][i];
+    }
+    d.A.rho[dst] = d.B.rho[i];
+    d.A.id[dst] = my;
+    // Algorithms 2-3, after the rebuild: in-box particles join the buffer, others leave it
+    uint8_t lab = d.B.label[i];
+    if (d.nrelabel) {
+      int c[3];
+      cell_coords(lin, g, c);
+      for (int q = 0; q < d.nrelabel; ++q) {
+        const BufDev& b = d.bufs[d.relabel_ids[q]];
+        const bool near = c[0] >= b.box_lo[0] && c[0] <= b.box_hi[0] && c[1] >= b.box_lo[1] &&
+                          c[1] <= b.box_hi[1] && c[2] >= b.box_lo[2] && c[2] <= b.box_hi[2];
+        if (!near && lab != (uint8_t)b.label) continue;
+        float X[3];
+        local_coords<D>(b, c, f, g.cs, X, D);
+        if (in_box<D>(b, X))
+          lab = (uint8_t)b.label;
+        else if (lab == (uint8_t)b.label)
+          lab = 0;
+      }
+    }
+    d.A.label[dst] = lab;
+  }
+}
+
+__global__ void k_finalize(DomainDev d, int count_step) {
+  StepState* st = d.st;
+  if (st->status) return;
+  st->n = d.cell_start[d.g.ncell];
+  st->next_id += min(st->n_inj, d.P.list_cap);
+  if (count_step) st->step += 1;
+}
+
+__global__ void k_decode(DomainDev d, double* out, double lo0, double lo1, double lo2, double cs) {
+  const unsigned n = d.st->n;
+  const int D = d.g.dim;
+  const double lo[3] = {lo0, lo1, lo2};
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int c[3];
+    cell_coords(d.A.cell[i], d.g, c);
+    for (int x = 0; x < D; ++x) out[(size_t)i * D + x] = lo[x] + (double)c[x] * cs + (double)d.A.f[x][i];
+  }
+}
+
+// ---- stand-alone cell-linked list on caller-provided device arrays
+__global__ void k_hist_raw(const int32_t* cell, const uint8_t* label, unsigned n, long long ncell,
+                           unsigned* cnt, unsigned* slot, int* bad) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int c = cell[i];
+    if (label && label[i] == kDead) {
+      slot[i] = kNoSlot;
+    } else if (c < 0 || (long long)c >= ncell) {
+      slot[i] = kNoSlot;
+      atomicExch(bad, 1);
+    } else {
+      slot[i] = atomicAdd(cnt + c, 1u);
+    }
+  }
+}
+
+__global__ void k_keys_raw(const int32_t* cell, const uint32_t* id, unsigned n, const unsigned* slot,
+                           const unsigned* start, unsigned* tmp) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned sl = slot[i];
+    if (sl != kNoSlot) tmp[start[cell[i]] + sl] = id[i];
+  }
+}
+
+__global__ void k_order_raw(const int32_t* cell, const uint32_t* id, unsigned n, const unsigned* slot,
+                            const unsigned* start, const unsigned* tmp, uint32_t* order) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (slot[i] == kNoSlot) continue;
+    const int c = cell[i];
+    const unsigned s0 = start[c], s1 = start[c + 1], my = id[i];
+    unsigned rank = 0;
+    for (unsigned p = s0; p < s1; ++p) rank += tmp[p] < my;
+    order[s0 + rank] = i;
+  }
+}
+
+}  // namespace
+
+int launch_rebuild(const DomainDev& d, bool count_step, cudaStream_t s) {
+  const int blocks = d.sm_count * 8;
+  k_hist<<<blocks, 256, 0, s>>>(d);
+  scan_cells(d.cnt, d.scan_part, d.cell_start, d.scan_tiles, &d.st->status, s);
+  k_keys<<<blocks, 256, 0, s>>>(d);
+  if (d.g.dim == 2)
+    k_scatter<2><<<blocks, 256, 0, s>>>(d);
+  else
+    k_scatter<3><<<blocks, 256, 0, s>>>(d);
+  k_finalize<<<1, 1, 0, s>>>(d, count_step ? 1 : 0);
+  return 7;
+}
+
+void launch_decode_positions(const DomainDev& d, double* pos_out, const double lo[3], double cs,
+                             cudaStream_t s) {
+  k_decode<<<d.sm_count * 4, 256, 0, s>>>(d, pos_out, lo[0], lo[1], lo[2], cs);
+}
+
+cudaError_t cell_list_build(const int32_t* cell, const uint32_t* id, const uint8_t* label, uint64_t n,
+                            uint64_t ncell, uint32_t* cell_start, uint32_t* order, cudaStream_t s,
+                            int* bad_input) {
+  *bad_input = 0;
+  const long long pad = ((long long)ncell + 1 + kScanTile - 1) / kScanTile * kScanTile;
+  const int tiles = (int)(pad / kScanTile);
+  unsigned *cnt = nullptr, *part = nullptr, *start = nullptr, *slot = nullptr, *tmp = nullptr;
+  int* bad = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) {
+    if (e == cudaSuccess && r != cudaSuccess) e = r;
+  };
+  chk(cudaMallocAsync((void**)&cnt, (size_t)pad * sizeof(unsigned), s));
+  chk(cudaMallocAsync((void**)&part, (size_t)tiles * sizeof(unsigned), s));
+  chk(cudaMallocAsync((void**)&start, (size_t)(pad + 1) * sizeof(unsigned), s));
+  chk(cudaMallocAsync((void**)&slot, (size_t)(n ? n : 1) * sizeof(unsigned), s));
+  chk(cudaMallocAsync((void**)&tmp, (size_t)(n ? n : 1) * sizeof(unsigned), s));
+  chk(cudaMallocAsync((void**)&bad, sizeof(int), s));
+  if (e == cudaSuccess) {
+    chk(cudaMemsetAsync(cnt, 0, (size_t)pad * sizeof(unsigned), s));
+    chk(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = sms * 8;
+    const unsigned nn = (unsigned)n;
+    k_hist_raw<<<blocks, 256, 0, s>>>(cell, label, nn, (long long)ncell, cnt, slot, bad);
+    scan_cells(cnt, part, start, tiles, nullptr, s);
+    k_keys_raw<<<blocks, 256, 0, s>>>(cell, id, nn, slot, start, tmp);
+    k_order_raw<<<blocks, 256, 0, s>>>(cell, id, nn, slot, start, tmp, order);
+    chk(cudaGetLastError());
+    chk(cudaMemcpyAsync(cell_start, start, (size_t)(ncell + 1) * sizeof(unsigned), cudaMemcpyDeviceToDevice, s));
+    int hbad = 0;
+    chk(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    chk(cudaStreamSynchronize(s));
+    *bad_input = hbad;
+  }
+  if (cnt) cudaFreeAsync(cnt, s);
+  if (part) cudaFreeAsync(part, s);
+  if (start) cudaFreeAsync(start, s);
+  if (slot) cudaFreeAsync(slot, s);
+  if (tmp) cudaFreeAsync(tmp, s);
+  if (bad) cudaFreeAsync(bad, s);
+  return e;
+}
+
+}  // namespace sphbuf

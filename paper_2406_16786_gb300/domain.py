@@ -1,0 +1,247 @@
+"""Python binding of the sphbuf C ABI: argument marshalling only.
+
+Every step of the method runs in the CUDA library (libsphbuf.so); this module converts numpy
+arrays to pointers and status codes to exceptions.  A ``torch.cuda.Stream`` (or a raw
+``cudaStream_t`` integer) may be passed as the domain's stream.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from . import _ffi
+from ._ffi import BcParams, DomainDesc
+
+
+class SphbufError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("sphbuf status %d (%s): %s" % (status, _status_name(status), message))
+        self.status = status
+
+
+def _status_name(s):
+    lib = _ffi.load()
+    return lib.sphbuf_status_string(s).decode()
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    h = getattr(stream, "cuda_stream", None)
+    if h is None:
+        raise TypeError("stream must be a torch.cuda.Stream or an integer cudaStream_t")
+    return int(h)
+
+
+def rotation_from_normal(normal, roll: float = 0.0) -> np.ndarray:
+    lib = _ffi.load()
+    n = np.ascontiguousarray(normal, dtype=np.float64)
+    out = np.zeros(9, dtype=np.float64)
+    st = lib.sphbuf_rotation_from_normal(_ptr(n), float(roll), _ptr(out))
+    if st:
+        raise SphbufError(st, "rotation_from_normal")
+    return out.reshape(3, 3)
+
+
+def cell_list_build(cell_dev: int, id_dev: int, label_dev: Optional[int], n: int, ncell: int,
+                    cell_start_dev: int, order_dev: int, stream=None) -> None:
+    """Stand-alone counting-sort cell-linked list on device pointers (integers)."""
+    lib = _ffi.load()
+    st = lib.sphbuf_cell_list_build(ctypes.c_void_p(cell_dev), ctypes.c_void_p(id_dev),
+                                    None if label_dev is None else ctypes.c_void_p(label_dev), n, ncell,
+                                    ctypes.c_void_p(cell_start_dev), ctypes.c_void_p(order_dev),
+                                    None if stream is None else ctypes.c_void_p(_stream_handle(stream)))
+    if st:
+        raise SphbufError(st, "cell_list_build")
+
+
+class Domain:
+    """One simulation domain owned by the library (device memory, buffers, stream)."""
+
+    def __init__(self, dim, lo, hi, dp, h_over_dp, rho0, c0, nu, dt, capacity, stream=None):
+        self.lib = _ffi.load()
+        desc = DomainDesc()
+        desc.dim = int(dim)
+        for a in range(3):
+            desc.lo[a] = float(lo[a])
+            desc.hi[a] = float(hi[a])
+        desc.dp, desc.h_over_dp, desc.rho0 = float(dp), float(h_over_dp), float(rho0)
+        desc.c0, desc.nu, desc.dt = float(c0), float(nu), float(dt)
+        desc.capacity = int(capacity)
+        self.dim = int(dim)
+        self._stream = stream  # keep a torch stream alive
+        h = ctypes.c_void_p()
+        handle = _stream_handle(stream)
+        st = self.lib.sphbuf_create_domain(ctypes.byref(desc), None if handle is None else ctypes.c_void_p(handle),
+                                           ctypes.byref(h))
+        if st:
+            raise SphbufError(st, "create_domain")
+        self.h = h
+        self.nbuf = 0
+        dims = np.zeros(3, dtype=np.int32)
+        cs = ctypes.c_double()
+        nc = ctypes.c_uint64()
+        self.lib.sphbuf_grid_info(self.h, _ptr(dims), ctypes.byref(cs), ctypes.byref(nc))
+        self.dims = [int(x) for x in dims]
+        self.cs = cs.value
+        self.ncell = nc.value
+
+    # ------------------------------------------------------------------ helpers
+    def _check(self, st, what):
+        if st:
+            msg = self.lib.sphbuf_error_message(self.h)
+            raise SphbufError(st, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    @classmethod
+    def from_case(cls, case, stream=None, native=True, capacity=None):
+        """Domain for a ``workloads.Case``: walls, fluid (cell-relative encoding), buffers."""
+        from . import workloads
+
+        d = cls(case.dim, case.lo, case.hi, case.dp, case.h_over_dp, case.rho0, case.c0, case.nu, case.dt,
+                capacity or case.capacity, stream=stream)
+        d.set_walls(case.wall_pos)
+        for b in case.buffers:
+            d.add_buffer(b)
+        if native:
+            cell, frac = workloads.encode_positions(case.fluid_pos, case.lo, case.cs, case.grid_dims())
+            d.write_particles(cell, frac, case.fluid_vel, case.fluid_rho)
+        else:
+            d.set_fluid(case.fluid_pos, case.fluid_vel, case.fluid_rho)
+        return d
+
+    def set_walls(self, pos):
+        p = np.ascontiguousarray(np.asarray(pos, dtype=np.float64)[:, : self.dim])
+        self._check(self.lib.sphbuf_set_walls(self.h, _ptr(p), p.shape[0]), "set_walls")
+
+    def set_fluid(self, pos, vel, rho):
+        p = np.ascontiguousarray(np.asarray(pos, dtype=np.float64)[:, : self.dim])
+        v = np.ascontiguousarray(np.asarray(vel, dtype=np.float32)[:, : self.dim])
+        r = np.ascontiguousarray(rho, dtype=np.float32)
+        self._check(self.lib.sphbuf_set_fluid(self.h, _ptr(p), _ptr(v), _ptr(r), p.shape[0]), "set_fluid")
+
+    def write_particles(self, cell, frac, vel, rho, ids=None, labels=None, next_id=None):
+        c = np.ascontiguousarray(cell, dtype=np.int32)
+        f = np.ascontiguousarray(np.asarray(frac, dtype=np.float32)[:, : self.dim])
+        v = np.ascontiguousarray(np.asarray(vel, dtype=np.float32)[:, : self.dim])
+        r = np.ascontiguousarray(rho, dtype=np.float32)
+        i = None if ids is None else np.ascontiguousarray(ids, dtype=np.uint32)
+        lab = None if labels is None else np.ascontiguousarray(labels, dtype=np.uint8)
+        n = c.shape[0]
+        if next_id is None:
+            next_id = n if i is None else (int(i.max()) + 1 if n else 0)
+        self._check(self.lib.sphbuf_write_particles(self.h, _ptr(c), _ptr(f), _ptr(v), _ptr(r), _ptr(i), _ptr(lab),
+                                                    n, int(next_id)), "write_particles")
+
+    def add_buffer(self, spec) -> int:
+        o = np.ascontiguousarray(spec.origin, dtype=np.float64)
+        R = np.ascontiguousarray(np.asarray(spec.rotation, dtype=np.float64).reshape(9))
+        e = np.ascontiguousarray(spec.extent, dtype=np.float64)
+        prm = BcParams(float(spec.umax), float(spec.half_width), float(spec.p_b), float(getattr(spec, "p_amp", 0.0)),
+                       float(getattr(spec, "p_omega", 0.0)), float(getattr(spec, "p_phase", 0.0)))
+        k = ctypes.c_int()
+        self._check(self.lib.sphbuf_add_inout_buffer(self.h, _ptr(o), _ptr(R), _ptr(e), int(spec.bc), ctypes.byref(prm),
+                                                     ctypes.byref(k)), "add_inout_buffer")
+        self.nbuf += 1
+        return k.value
+
+    def step(self, nsteps=1, phases=_ffi.STEP_DEFAULT):
+        self._check(self.lib.sphbuf_step_phases(self.h, int(nsteps), int(phases)), "step")
+
+    def use_graph(self, enable=True):
+        self._check(self.lib.sphbuf_use_graph(self.h, 1 if enable else 0), "use_graph")
+
+    def sync(self):
+        self._check(self.lib.sphbuf_sync(self.h), "sync")
+
+    def count(self) -> int:
+        n = ctypes.c_uint64()
+        self._check(self.lib.sphbuf_count(self.h, ctypes.byref(n)), "count")
+        return n.value
+
+    def read(self):
+        """Sorted particle state as numpy arrays (cell, frac, vel, rho, id, label)."""
+        n = self.count()
+        d = self.dim
+        out = dict(cell=np.zeros(n, np.int32), frac=np.zeros((n, d), np.float32), vel=np.zeros((n, d), np.float32),
+                   rho=np.zeros(n, np.float32), id=np.zeros(n, np.uint32), label=np.zeros(n, np.uint8))
+        nn = ctypes.c_uint64()
+        self._check(self.lib.sphbuf_read_particles(self.h, _ptr(out["cell"]), _ptr(out["frac"]), _ptr(out["vel"]),
+                                                   _ptr(out["rho"]), _ptr(out["id"]), _ptr(out["label"]), n,
+                                                   ctypes.byref(nn)), "read_particles")
+        return out
+
+    def positions(self) -> np.ndarray:
+        n = self.count()
+        p = np.zeros((n, self.dim), np.float64)
+        nn = ctypes.c_uint64()
+        self._check(self.lib.sphbuf_read_positions(self.h, _ptr(p), n, ctypes.byref(nn)), "read_positions")
+        return p
+
+    def cell_start(self) -> np.ndarray:
+        cs = np.zeros(self.ncell + 1, np.uint32)
+        self._check(self.lib.sphbuf_read_cell_start(self.h, _ptr(cs), cs.shape[0]), "read_cell_start")
+        return cs
+
+    def counters(self, k: int):
+        i, dl = ctypes.c_uint64(), ctypes.c_uint64()
+        mi, mo, q = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.sphbuf_read_counters(self.h, k, ctypes.byref(i), ctypes.byref(dl), ctypes.byref(mi),
+                                                  ctypes.byref(mo), ctypes.byref(q)), "read_counters")
+        return dict(injected=i.value, deleted=dl.value, mass_in=mi.value, mass_out=mo.value, flux=q.value)
+
+    def global_counters(self):
+        e, s, nid = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint32()
+        self._check(self.lib.sphbuf_read_global(self.h, ctypes.byref(e), ctypes.byref(s), ctypes.byref(nid)),
+                    "read_global")
+        return dict(escaped=e.value, steps=s.value, next_id=nid.value)
+
+    def last_decisions(self):
+        ni, nd = ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(self.lib.sphbuf_last_decisions(self.h, None, None, None, ctypes.byref(ni), None, None,
+                                                   ctypes.byref(nd), 0), "last_decisions")
+        cap = max(ni.value, nd.value, 1)
+        ib, ip, inew = (np.zeros(cap, np.uint32) for _ in range(3))
+        db, did = np.zeros(cap, np.uint32), np.zeros(cap, np.uint32)
+        self._check(self.lib.sphbuf_last_decisions(self.h, _ptr(ib), _ptr(ip), _ptr(inew), ctypes.byref(ni), _ptr(db),
+                                                   _ptr(did), ctypes.byref(nd), cap), "last_decisions")
+        inj = [(int(ib[q]), int(ip[q]), int(inew[q])) for q in range(ni.value)]
+        dels = [(int(db[q]), int(did[q])) for q in range(nd.value)]
+        return inj, dels
+
+    def enable_phase_timing(self, enable=True):
+        self._check(self.lib.sphbuf_enable_phase_timing(self.h, 1 if enable else 0), "enable_phase_timing")
+
+    def phase_times(self):
+        ms = np.zeros(5, np.float64)
+        n = ctypes.c_uint64()
+        self._check(self.lib.sphbuf_read_phase_times(self.h, _ptr(ms), ctypes.byref(n)), "read_phase_times")
+        return dict(zip(["density", "force", "decide", "apply", "rebuild"], ms.tolist())), n.value
+
+    def candidate_count(self, k: int):
+        c, p = ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(self.lib.sphbuf_candidate_count(self.h, k, ctypes.byref(c), ctypes.byref(p)), "candidate_count")
+        return c.value, p.value
+
+    def launch_count(self) -> int:
+        n = ctypes.c_uint64()
+        self._check(self.lib.sphbuf_read_launch_count(self.h, ctypes.byref(n)), "read_launch_count")
+        return n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sphbuf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

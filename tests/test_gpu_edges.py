@@ -1,0 +1,77 @@
+"""Edge cases and error paths of the GPU library."""
+import numpy as np
+import pytest
+
+from paper_2406_16786_gb300 import _ffi
+from paper_2406_16786_gb300 import workloads as wl
+from tests import cases
+
+pytestmark = pytest.mark.gpu
+
+
+def _dom(case, **kw):
+    from paper_2406_16786_gb300.domain import Domain
+
+    return Domain.from_case(case, **kw)
+
+
+def test_empty_domain_steps():
+    from paper_2406_16786_gb300.domain import Domain
+
+    case = cases.lockstep_cases()[0][1]
+    d = Domain(2, case.lo, case.hi, case.dp, 1.3, 1000.0, 10.0, 1e-2, case.dt, 100)
+    d.set_walls(case.wall_pos)
+    d.add_buffer(case.buffers[0])
+    d.write_particles(np.zeros(0, np.int32), np.zeros((0, 2), np.float32), np.zeros((0, 2), np.float32),
+                      np.zeros(0, np.float32))
+    d.step(3)
+    assert d.count() == 0
+    assert d.last_decisions() == ([], [])
+    d.close()
+
+
+def test_capacity_overflow_is_latched_not_faulted():
+    from paper_2406_16786_gb300.domain import SphbufError
+
+    case = cases.lockstep_cases()[0][1]
+    d = _dom(case, capacity=case.n)  # no room for a single injected particle
+    with pytest.raises(SphbufError) as e:
+        for _ in range(20):
+            d.step(1, _ffi.PHASE_KINEMATIC | _ffi.PHASE_BUFFER)
+        d.sync()
+    assert e.value.status == 2
+    d.close()
+
+
+def test_overlapping_buffers_rejected():
+    from paper_2406_16786_gb300.domain import Domain, SphbufError
+
+    case = cases.lockstep_cases()[0][1]
+    d = Domain(2, case.lo, case.hi, case.dp, 1.3, 1000.0, 10.0, 1e-2, case.dt, case.capacity)
+    d.add_buffer(case.buffers[0])
+    b = case.buffers[0]
+    moved = wl.BufferSpec(origin=b.origin + 0.02 * b.rotation[0], rotation=b.rotation, extent=b.extent, bc=b.bc)
+    with pytest.raises(SphbufError) as e:
+        d.add_buffer(moved)
+    assert e.value.status == 3
+    bad = wl.BufferSpec(origin=b.origin + 0.5, rotation=2.0 * b.rotation, extent=b.extent, bc=b.bc)
+    with pytest.raises(SphbufError) as e:
+        d.add_buffer(bad)
+    assert e.value.status == 1
+    d.close()
+
+
+def test_particle_count_invariant_and_mass_balance():
+    case = cases.lockstep_cases()[3][1]
+    d = _dom(case)
+    n0 = d.count()
+    d.step(25)
+    inj = sum(d.counters(k)["injected"] for k in range(2))
+    dele = sum(d.counters(k)["deleted"] for k in range(2))
+    g = d.global_counters()
+    assert d.count() == n0 + inj - dele - g["escaped"]
+    m = case.rho0 * case.dp ** 3
+    mi = sum(d.counters(k)["mass_in"] for k in range(2))
+    mo = sum(d.counters(k)["mass_out"] for k in range(2))
+    assert mi - mo == pytest.approx((d.count() - n0 + g["escaped"]) * m, rel=1e-12, abs=1e-15)
+    d.close()

@@ -219,6 +219,27 @@ sphbuf_status sphbuf_cell_list_build(const int32_t *cell, const uint32_t *id, co
                                      uint64_t n, uint64_t ncell, uint32_t *cell_start,
                                      uint32_t *order, void *cuda_stream);
 
+/* The same cell-linked list as sphbuf_cell_list_build, for callers that must not allocate
+ * device memory: for example a host program whose GPU memory is already fully reserved by
+ * another allocator, or a latency-bound loop in which cudaMalloc / cudaFree (which can
+ * synchronise the device) are not acceptable.  This call performs no cudaMalloc, cudaFree or
+ * other allocating call; its scratch lives in a fixed array inside the library (about 16 MiB,
+ * held by every GPU that loads the library until the process exits).  The paper has no
+ * counterpart of this entry point.
+ *   Limits: n <= 1048576 particles and ncell <= 1048575 cells; larger sizes return
+ *   SPHBUF_ERR_CAPACITY without doing any work.
+ *   Inputs, outputs and errors as for sphbuf_cell_list_build (the call synchronises the stream).
+ *   The first call on each device looks up the array's device address with that device
+ *   current (the device current at the call); make that first call before any stream
+ *   capture.
+ *   All calls share the one array and it keeps the last call's contents (each call clears the
+ *   parts that must start at zero): calls whose work overlaps on the GPU, from several streams
+ *   or threads, race and give wrong results; serialise them. */
+sphbuf_status sphbuf_cell_list_build_noalloc(const int32_t *cell, const uint32_t *id,
+                                             const uint8_t *label, uint64_t n, uint64_t ncell,
+                                             uint32_t *cell_start, uint32_t *order,
+                                             void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

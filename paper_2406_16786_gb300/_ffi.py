@@ -52,6 +52,7 @@ SIGNATURES = {
     "sphbuf_candidate_count": (ctypes.c_int, [vp, ctypes.c_int, P(c_u64), P(c_u64)]),
     "sphbuf_read_launch_count": (ctypes.c_int, [vp, P(c_u64)]),
     "sphbuf_cell_list_build": (ctypes.c_int, [vp, vp, vp, c_u64, c_u64, vp, vp, vp]),
+    "sphbuf_cell_list_build_noalloc": (ctypes.c_int, [vp, vp, vp, c_u64, c_u64, vp, vp, vp]),
 }
 
 PHASE_PHYSICS = 1

@@ -987,4 +987,17 @@ sphbuf_status sphbuf_cell_list_build(const int32_t* cell, const uint32_t* id, co
   return bad ? SPHBUF_ERR_INVALID_ARG : SPHBUF_OK;
 }
 
+sphbuf_status sphbuf_cell_list_build_noalloc(const int32_t* cell, const uint32_t* id, const uint8_t* label,
+                                             uint64_t n, uint64_t ncell, uint32_t* cell_start, uint32_t* order,
+                                             void* cuda_stream) {
+  if ((n && (!cell || !id || !order)) || !cell_start || ncell == 0) return SPHBUF_ERR_INVALID_ARG;
+  if (n > sphbuf::cell_list_noalloc_max_particles() || ncell > sphbuf::cell_list_noalloc_max_cells())
+    return SPHBUF_ERR_CAPACITY;
+  int bad = 0;
+  cudaError_t e = sphbuf::cell_list_build_noalloc(cell, id, label, n, ncell, cell_start, order,
+                                                  static_cast<cudaStream_t>(cuda_stream), &bad);
+  if (e != cudaSuccess) return SPHBUF_ERR_CUDA;
+  return bad ? SPHBUF_ERR_INVALID_ARG : SPHBUF_OK;
+}
+
 }  // extern "C"

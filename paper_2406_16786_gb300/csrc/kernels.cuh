@@ -47,5 +47,11 @@ void launch_decode_positions(const DomainDev& d, double* pos_out, const double l
 cudaError_t cell_list_build(const int32_t* cell, const uint32_t* id, const uint8_t* label,
                             uint64_t n, uint64_t ncell, uint32_t* cell_start, uint32_t* order,
                             cudaStream_t s, int* bad_input);
+// Same list with scratch in a fixed file-scope device array (no allocation).
+unsigned long long cell_list_noalloc_max_particles();
+unsigned long long cell_list_noalloc_max_cells();
+cudaError_t cell_list_build_noalloc(const int32_t* cell, const uint32_t* id, const uint8_t* label,
+                                    uint64_t n, uint64_t ncell, uint32_t* cell_start, uint32_t* order,
+                                    cudaStream_t s, int* bad_input);
 
 }  // namespace sphbuf

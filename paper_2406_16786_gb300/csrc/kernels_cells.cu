@@ -9,6 +9,8 @@
 //           with the relabel test applied on the way
 // The result is sorted by (cell, id) whatever order the atomics took, so it is
 // deterministic and identical to a plain sort.
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace sphbuf {
@@ -315,6 +317,92 @@ cudaError_t cell_list_build(const int32_t* cell, const uint32_t* id, const uint8
   if (slot) cudaFreeAsync(slot, s);
   if (tmp) cudaFreeAsync(tmp, s);
   if (bad) cudaFreeAsync(bad, s);
+  return e;
+}
+
+// ---- the same cell-linked list with its scratch in a fixed, file-scope device array
+//
+// For callers that cannot allocate device memory.  Layout of the array (32-bit words):
+//   count[kNaPad] | start[kNaPad + 1] | part[kNaTiles] | slot[kNaMaxN] | tmp[kNaMaxN] | flag[1]
+// Every GPU that loads the library holds this array (about 16 MiB) until the process exits.
+namespace {
+
+constexpr unsigned long long kNaMaxN = 1ull << 20;          // particles per call
+constexpr unsigned long long kNaMaxCells = (1ull << 20) - 1;  // cells per call
+constexpr size_t kNaPad = ((kNaMaxCells + 1 + kScanTile - 1) / kScanTile) * kScanTile;
+constexpr size_t kNaTiles = kNaPad / kScanTile;
+constexpr size_t kNaCount = 0;
+constexpr size_t kNaStart = kNaCount + kNaPad;
+constexpr size_t kNaPart = kNaStart + kNaPad + 4;  // keeps the next block 16-byte aligned
+constexpr size_t kNaSlot = kNaPart + ((kNaTiles + 3) / 4) * 4;
+constexpr size_t kNaTmp = kNaSlot + kNaMaxN;
+constexpr size_t kNaFlag = kNaTmp + kNaMaxN;
+constexpr size_t kNaWords = kNaFlag + 4;
+
+static __device__ __align__(256) unsigned g_noalloc_scratch[kNaWords];
+
+constexpr int kNaMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned* g_noalloc_ptr[kNaMaxDevices] = {};
+
+// Device address of the scratch array for the current device, looked up once per device.
+cudaError_t noalloc_scratch(unsigned** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<unsigned*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+unsigned long long cell_list_noalloc_max_particles() { return kNaMaxN; }
+unsigned long long cell_list_noalloc_max_cells() { return kNaMaxCells; }
+
+cudaError_t cell_list_build_noalloc(const int32_t* cell, const uint32_t* id, const uint8_t* label, uint64_t n,
+                                    uint64_t ncell, uint32_t* cell_start, uint32_t* order, cudaStream_t s,
+                                    int* bad_input) {
+  *bad_input = 0;
+  unsigned* base = nullptr;
+  cudaError_t e = noalloc_scratch(&base);
+  if (e != cudaSuccess) return e;
+  const long long pad = ((long long)ncell + 1 + kScanTile - 1) / kScanTile * kScanTile;
+  const int tiles = (int)(pad / kScanTile);
+  unsigned* cnt = base + kNaCount;
+  unsigned* start = base + kNaStart;
+  unsigned* part = base + kNaPart;
+  unsigned* slot = base + kNaSlot;
+  unsigned* tmp = base + kNaTmp;
+  int* bad = reinterpret_cast<int*>(base + kNaFlag);
+  // the array keeps the previous call's contents: clear the counters and the error flag
+  e = cudaMemsetAsync(cnt, 0, (size_t)pad * sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = (sms > 0 ? sms : 1) * 8;
+  const unsigned nn = (unsigned)n;
+  k_hist_raw<<<blocks, 256, 0, s>>>(cell, label, nn, (long long)ncell, cnt, slot, bad);
+  scan_cells(cnt, part, start, tiles, nullptr, s);
+  k_keys_raw<<<blocks, 256, 0, s>>>(cell, id, nn, slot, start, tmp);
+  k_order_raw<<<blocks, 256, 0, s>>>(cell, id, nn, slot, start, tmp, order);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(cell_start, start, (size_t)(ncell + 1) * sizeof(unsigned), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  int hbad = 0;
+  e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  *bad_input = hbad;
   return e;
 }
 

@@ -1,0 +1,60 @@
+"""The allocation-free cell-linked-list entry point agrees with the allocating one.
+
+sphbuf_cell_list_build_noalloc serves callers that cannot allocate device memory (a program
+whose GPU memory is already reserved by another allocator, or a latency-bound loop in which a
+cudaMalloc/cudaFree, which can synchronise the device, is not acceptable).  Its scratch is a
+fixed array inside the library, shared by every call and keeping the previous call's
+contents.  Two different inputs in a row check that each call starts from cleared scratch.
+The entry point is called through the C ABI (ctypes), like sphbuf_cell_list_build.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+MAX_N = 1 << 20
+MAX_CELLS = (1 << 20) - 1
+
+
+def _call(fn, cell, ids, label, n, ncell, start, order):
+    return fn(ctypes.c_void_p(cell.data_ptr()), ctypes.c_void_p(ids.data_ptr()),
+              None if label is None else ctypes.c_void_p(label.data_ptr()), n, ncell,
+              ctypes.c_void_p(start.data_ptr()), ctypes.c_void_p(order.data_ptr()), None)
+
+
+def test_noalloc_matches_allocating_cell_list_on_two_calls_in_a_row():
+    import torch
+
+    from paper_2406_16786_gb300 import _ffi
+
+    lib = _ffi.load()
+    for rep, (n, ncell) in enumerate([(700_001, 1_000_003), (123_457, 40_961)]):
+        rng = np.random.default_rng(90 + rep)
+        cell = torch.from_numpy(rng.integers(0, ncell, n).astype(np.int32)).cuda()
+        ids = torch.from_numpy(rng.permutation(n).astype(np.int32) * 5 + 3).cuda()
+        label = torch.from_numpy(np.where(rng.random(n) < 0.02, 255, 0).astype(np.uint8)).cuda()
+        outs = []
+        for fn in (lib.sphbuf_cell_list_build, lib.sphbuf_cell_list_build_noalloc):
+            start = torch.full((ncell + 1,), -7, dtype=torch.int32, device="cuda")
+            order = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+            assert _call(fn, cell, ids, label, n, ncell, start, order) == 0
+            outs.append((start.cpu().numpy(), order.cpu().numpy()))
+        (s_ref, o_ref), (s_na, o_na) = outs
+        assert np.array_equal(s_na, s_ref)
+        assert np.array_equal(o_na, o_ref)
+        kept = int(s_ref[-1])
+        assert kept == int((label.cpu().numpy() != 255).sum())
+
+
+def test_noalloc_rejects_sizes_beyond_its_fixed_scratch():
+    import torch
+
+    from paper_2406_16786_gb300 import _ffi
+
+    lib = _ffi.load()
+    small = torch.zeros(8, dtype=torch.int32, device="cuda")
+    # size checks come before any device work, so the small arrays are never read
+    assert _call(lib.sphbuf_cell_list_build_noalloc, small, small, None, MAX_N + 1, 10, small, small) == 2
+    assert _call(lib.sphbuf_cell_list_build_noalloc, small, small, None, 4, MAX_CELLS + 1, small, small) == 2

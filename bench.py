@@ -202,7 +202,7 @@ def run_gpu(args):
     # per-phase device time (events around each phase on the domain's stream; plain launches)
     dom.use_graph(False)
     dom.enable_phase_timing(True)
-    dom.step(args.phase_steps)
+    dom.step(max(1, args.phase_steps))
     ph, nph = dom.phase_times()
     dom.enable_phase_timing(False)
     per = {k: v / nph for k, v in ph.items()}
@@ -237,7 +237,7 @@ def run_gpu(args):
     nid = dom.global_counters()["next_id"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    for _ in range(max(1, e2e_steps)):
         dom.write_particles(pin["cell"], pin["frac"], pin["vel"], pin["rho"], ids=pin["id"], labels=pin["label"],
                             next_id=nid)
         dom.step(1)
@@ -245,7 +245,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
     bytes_io = nn * state_bytes
-    e2e_value = world * nn * e2e_steps / te
+    e2e_value = world * nn * max(1, e2e_steps) / te
     del back
 
     cpu = None

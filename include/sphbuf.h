@@ -93,7 +93,7 @@ typedef struct {
   double h_over_dp;         /* smoothing length / dp (1.3 in the paper, Sec. 3) */
   double rho0, c0, nu, dt;  /* reference density, artificial sound speed, kinematic viscosity,
                                fixed time step */
-  uint64_t capacity;        /* maximum number of fluid particles */
+  uint64_t capacity;        /* maximum number of fluid particles, at most 2^25 - 1 (walls too) */
 } sphbuf_domain_desc;
 
 typedef struct {

@@ -17,6 +17,8 @@ using namespace sphbuf;
 namespace {
 
 constexpr int kPhases = 5;
+// Neighbour lists pack particle indices into 25 bits (see kernels_sph.cu).
+constexpr uint64_t kMaxParticles = (1ull << 25) - 1;
 
 struct BufHost {
   double origin[3], R[9], extent[3];
@@ -131,10 +133,6 @@ bool encode_axis(double x, double lo, double cs, float cs32, int n, int* c_out, 
   *c_out = (int)c;
   *f_out = f;
   return true;
-}
-
-void mat_T_vec(const double R[9], const double v[3], double out[3]) {
-  for (int x = 0; x < 3; ++x) out[x] = R[0 * 3 + x] * v[0] + R[1 * 3 + x] * v[1] + R[2 * 3 + x] * v[2];
 }
 
 // Separating-axis test of two oriented boxes (centre, frame rows, half extents); 2-D uses
@@ -350,7 +348,7 @@ sphbuf_status sphbuf_create_domain(const sphbuf_domain_desc* desc, void* cuda_st
   *out = nullptr;
   if (desc->dim != 2 && desc->dim != 3) return SPHBUF_ERR_INVALID_ARG;
   if (!(desc->dp > 0) || !(desc->h_over_dp > 0) || !(desc->rho0 > 0) || !(desc->c0 > 0) || !(desc->dt > 0) ||
-      !(desc->nu >= 0) || desc->capacity == 0 || desc->capacity >= 0xF0000000ull)
+      !(desc->nu >= 0) || desc->capacity == 0 || desc->capacity > kMaxParticles)
     return SPHBUF_ERR_INVALID_ARG;
   auto* d = new sphbuf_domain();
   d->desc = *desc;
@@ -435,11 +433,18 @@ sphbuf_status sphbuf_create_domain(const sphbuf_domain_desc* desc, void* cuda_st
     A(dalloc(d, &p->label, C));
   }
   A(dalloc(d, &v.rho_new, C));
+  // neighbour lists of the density pass, reused by the force pass (~80 neighbours in 3-D and
+  // ~20 in 2-D at h = 1.3 dp on the lattice; headroom for compression)
+  v.nb_cap = D == 3 ? 128 : 48;
+  A(dalloc(d, &v.nb, C * (size_t)v.nb_cap));
+  A(dalloc(d, &v.nb_cnt, C));
   A(dalloc(d, &v.slot, C));
   A(dalloc(d, &v.tmp_id, C));
   A(dalloc(d, &v.cell_start, (size_t)v.ncell_pad + 1));
   A(dalloc(d, &v.cnt, (size_t)v.ncell_pad));
   A(dalloc(d, &v.scan_part, (size_t)v.scan_tiles));
+  A(dalloc(d, &v.scan_part_occ, (size_t)v.scan_tiles));
+  A(dalloc(d, &v.occ_list, std::min<size_t>((size_t)d->ncell, C) + 1));
   A(dalloc(d, &v.inj, P.list_cap));
   A(dalloc(d, &v.del, P.list_cap));
   A(dalloc(d, &v.inj_sorted, P.list_cap));
@@ -479,6 +484,7 @@ sphbuf_status sphbuf_destroy(sphbuf_domain_t d) {
 
 sphbuf_status sphbuf_set_walls(sphbuf_domain_t d, const double* pos, uint64_t n) {
   if (!d || (!pos && n)) return SPHBUF_ERR_INVALID_ARG;
+  if (n > kMaxParticles) return fail(d, SPHBUF_ERR_CAPACITY, "too many wall particles");
   if (d->stepped) return fail(d, SPHBUF_ERR_STATE, "walls must be set before the first step");
   const int D = d->desc.dim;
   std::vector<int> cell(n);

@@ -64,6 +64,7 @@ struct StepState {
   unsigned n_inj;      // injections of the current step
   unsigned n_del;      // deletions of the current step
   unsigned next_id;
+  unsigned n_occ;      // occupied cells of the current cell-linked list
   unsigned long long step;
   int status;          // latched error code (sphbuf_status), 0 = OK
   unsigned long long escaped_total;

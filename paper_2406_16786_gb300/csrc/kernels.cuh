@@ -13,9 +13,14 @@ struct DomainDev {
   unsigned* cell_start;   // A's cell-linked list, ncell_pad + 1 entries
   unsigned* cnt;          // per-cell counters (zero between rebuilds), ncell_pad entries
   unsigned* scan_part;    // per-tile partial sums
+  unsigned* scan_part_occ;  // per-tile occupied-cell counts
+  unsigned* occ_list;     // occupied cells in increasing order (st->n_occ entries)
   unsigned* slot;         // per-particle slot from the histogram, capacity
   unsigned* tmp_id;       // ids scattered to their cell's range, capacity
   float* rho_new;         // density pass output, capacity
+  unsigned* nb;           // neighbour lists, nb_cap entries per particle (16-byte aligned)
+  unsigned* nb_cnt;       // neighbours found per particle (above nb_cap: direct path)
+  int nb_cap;             // multiple of 4
   Decision* inj;          // decisions of the current step, list_cap each
   Decision* del;
   InjRecord* inj_sorted;  // injections in (buffer, parent id) order

@@ -134,6 +134,122 @@ void scan_cells(unsigned* cnt, unsigned* part, unsigned* start, int tiles, const
   k_scan_down<<<tiles, kScanThreads, 0, s>>>(cnt, part, start, status);
 }
 
+// ---- domain scan: cell_start plus the ordered list of occupied cells (the work list of the
+// tiled neighbour passes)
+__device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned* ws, unsigned* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) ws[w] = incl;
+  __syncthreads();
+  unsigned wpre = 0, tot = 0;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+    if (q < w) wpre += ws[q];
+    tot += ws[q];
+  }
+  __syncthreads();
+  if (total) *total = tot;
+  return wpre + incl - x;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce_occ(const unsigned* __restrict__ cnt,
+                                                                  unsigned* __restrict__ part,
+                                                                  unsigned* __restrict__ part_occ,
+                                                                  const int* status) {
+  if (*status) return;
+  __shared__ unsigned ws[kScanThreads / 32];
+  const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
+  const uint4* p = reinterpret_cast<const uint4*>(cnt + base);
+  unsigned s = 0, o = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems / 4; ++q) {
+    const uint4 v = p[q];
+    s += v.x + v.y + v.z + v.w;
+    o += (v.x > 0) + (v.y > 0) + (v.z > 0) + (v.w > 0);
+  }
+  unsigned ts = 0, to = 0;
+  block_excl_scan(s, ws, &ts);
+  block_excl_scan(o, ws, &to);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = ts;
+    part_occ[blockIdx.x] = to;
+  }
+}
+
+// Exclusive scans of both per-tile sums (one block); the total occupied count goes to *n_occ.
+__global__ void __launch_bounds__(1024) k_scan_top_occ(unsigned* part, unsigned* part_occ, int ntiles,
+                                                       const int* status, unsigned* n_occ) {
+  if (*status) return;
+  __shared__ unsigned ws[32];
+  unsigned carry = 0, carry_o = 0;
+  for (int b0 = 0; b0 < ntiles; b0 += 1024) {
+    const int t = b0 + threadIdx.x;
+    const unsigned v = t < ntiles ? part[t] : 0u;
+    const unsigned vo = t < ntiles ? part_occ[t] : 0u;
+    unsigned tot = 0, toto = 0;
+    const unsigned ex = block_excl_scan(v, ws, &tot);
+    const unsigned exo = block_excl_scan(vo, ws, &toto);
+    if (t < ntiles) {
+      part[t] = carry + ex;
+      part_occ[t] = carry_o + exo;
+    }
+    carry += tot;
+    carry_o += toto;
+  }
+  if (threadIdx.x == 0) *n_occ = carry_o;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down_occ(unsigned* __restrict__ cnt,
+                                                                const unsigned* __restrict__ part,
+                                                                const unsigned* __restrict__ part_occ,
+                                                                unsigned* __restrict__ start,
+                                                                unsigned* __restrict__ occ_list,
+                                                                const int* status) {
+  if (*status) return;
+  __shared__ unsigned ws[kScanThreads / 32];
+  const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
+  uint4* p = reinterpret_cast<uint4*>(cnt + base);
+  unsigned v[kScanItems];
+#pragma unroll
+  for (int q = 0; q < kScanItems / 4; ++q) {
+    const uint4 t = p[q];
+    v[4 * q] = t.x;
+    v[4 * q + 1] = t.y;
+    v[4 * q + 2] = t.z;
+    v[4 * q + 3] = t.w;
+    p[q] = make_uint4(0, 0, 0, 0);
+  }
+  unsigned s = 0, o = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    s += v[q];
+    o += v[q] > 0;
+  }
+  unsigned run = part[blockIdx.x] + block_excl_scan(s, ws, nullptr);
+  unsigned orun = part_occ[blockIdx.x] + block_excl_scan(o, ws, nullptr);
+  uint4* out = reinterpret_cast<uint4*>(start + base);
+#pragma unroll
+  for (int q = 0; q < kScanItems / 4; ++q) {
+    uint4 t;
+    t.x = run;
+    run += v[4 * q];
+    t.y = run;
+    run += v[4 * q + 1];
+    t.z = run;
+    run += v[4 * q + 2];
+    t.w = run;
+    run += v[4 * q + 3];
+    out[q] = t;
+  }
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q)
+    if (v[q]) occ_list[orun++] = (unsigned)(base + q);
+}
+
 __global__ void __launch_bounds__(256) k_hist(DomainDev d) {
   if (d.st->status) return;
   const unsigned n = d.st->n + d.st->n_inj;
@@ -259,7 +375,10 @@ __global__ void k_order_raw(const int32_t* cell, const uint32_t* id, unsigned n,
 int launch_rebuild(const DomainDev& d, bool count_step, cudaStream_t s) {
   const int blocks = d.sm_count * 8;
   k_hist<<<blocks, 256, 0, s>>>(d);
-  scan_cells(d.cnt, d.scan_part, d.cell_start, d.scan_tiles, &d.st->status, s);
+  k_scan_reduce_occ<<<d.scan_tiles, kScanThreads, 0, s>>>(d.cnt, d.scan_part, d.scan_part_occ, &d.st->status);
+  k_scan_top_occ<<<1, 1024, 0, s>>>(d.scan_part, d.scan_part_occ, d.scan_tiles, &d.st->status, &d.st->n_occ);
+  k_scan_down_occ<<<d.scan_tiles, kScanThreads, 0, s>>>(d.cnt, d.scan_part, d.scan_part_occ, d.cell_start,
+                                                       d.occ_list, &d.st->status);
   k_keys<<<blocks, 256, 0, s>>>(d);
   if (d.g.dim == 2)
     k_scatter<2><<<blocks, 256, 0, s>>>(d);

@@ -1,9 +1,15 @@
 // WCSPH neighbour passes (Sec. 2, Sec. 4): density (Eq. (9) / Eq. (4)), force (Eqs. (5)-(8),
 // (18)) fused with the kick, the boundary velocity (Eqs. (19), (23)-(26)) and the drift.
 //
-// One thread per particle of the sorted set A; neighbours come from the 3^d cells around the
-// particle's cell, read as one contiguous range per (dy, dz) row (the three x-cells of a row
-// are adjacent in the sorted order).  Wall neighbours use the static wall list.
+// Neighbour lists.  One thread per particle of the sorted set A.  Its candidates are the
+// particles of the 3^d cells around its cell, one contiguous range per (dy, dz) row (the three
+// x-cells of a row are adjacent in the sorted order), plus the wall particles of the same
+// cells.  The neighbour-list pass tests every candidate once and appends the in-range ones,
+// packed into 32 bits, to the particle's own list (16-byte stores of 4 entries); the density
+// and force passes then loop over exactly those neighbours (~80 of ~475 candidates in 3-D), so
+// a warp no longer runs the interaction for candidates that only some of its lanes accept.
+// Lists are built in a fixed order, so every sum is evaluated in the same order on every run
+// (the step is deterministic).
 //
 // Wall neighbours carry the mirrored state of i (rho_j = rho_i, p_j = p_i, v_j = -v_i), the
 // reading of the cited one-sided Riemann solver with no-slip walls.  The intermediate
@@ -14,6 +20,8 @@
 namespace sphbuf {
 
 namespace {
+
+constexpr int kThreads = 256;
 
 // Step prologue, run by one thread of the step's first kernel: per-step constants.
 __device__ void begin_step(const DomainDev& d) {
@@ -30,115 +38,81 @@ __device__ void begin_step(const DomainDev& d) {
   }
 }
 
-// Calls fn(j, rx, ry, rz) for every sorted particle j in the 3^d cells around cell c of a
-// particle at in-cell offset fi; (rx, ry, rz) = r_i - r_j.
-template <int D, typename Fn>
-__device__ __forceinline__ void for_each_fluid(const DomainDev& d, const int c[3], const float fi[3],
-                                               Fn&& fn) {
-  const Grid& g = d.g;
-  const float cs = g.cs;
-  const int x0 = max(c[0] - 1, 0), x1 = min(c[0] + 1, g.nx - 1);
-  const int zlo = (D == 3) ? -1 : 0, zhi = (D == 3) ? 1 : 0;
-  for (int dz = zlo; dz <= zhi; ++dz) {
-    const int z = c[2] + dz;
-    if (z < 0 || z >= g.nz) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int y = c[1] + dy;
-      if (y < 0 || y >= g.ny) continue;
-      const int row = (z * g.ny + y) * g.nx;
-      const unsigned j0 = __ldg(d.cell_start + row + x0);
-      const unsigned j1 = __ldg(d.cell_start + row + x1 + 1);
-      const float oy = fi[1] - (float)dy * cs;
-      const float oz = (D == 3) ? fi[2] - (float)dz * cs : 0.f;
-      for (unsigned j = j0; j < j1; ++j) {
-        const int xj = __ldg(d.A.cell + j) - row;
-        const float rx = fi[0] - __ldg(d.A.f[0] + j) - (float)(xj - c[0]) * cs;
-        const float ry = oy - __ldg(d.A.f[1] + j);
-        const float rz = (D == 3) ? oz - __ldg(d.A.f[2] + j) : 0.f;
-        fn(j, rx, ry, rz);
-      }
-    }
-  }
-}
-
-template <int D, typename Fn>
-__device__ __forceinline__ void for_each_wall(const DomainDev& d, const int c[3], const float fi[3],
-                                              Fn&& fn) {
-  const Grid& g = d.g;
-  const float cs = g.cs;
-  const int x0 = max(c[0] - 1, 0), x1 = min(c[0] + 1, g.nx - 1);
-  const int zlo = (D == 3) ? -1 : 0, zhi = (D == 3) ? 1 : 0;
-  for (int dz = zlo; dz <= zhi; ++dz) {
-    const int z = c[2] + dz;
-    if (z < 0 || z >= g.nz) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int y = c[1] + dy;
-      if (y < 0 || y >= g.ny) continue;
-      const int row = (z * g.ny + y) * g.nx;
-      const unsigned j0 = __ldg(d.W.start + row + x0);
-      const unsigned j1 = __ldg(d.W.start + row + x1 + 1);
-      const float oy = fi[1] - (float)dy * cs;
-      const float oz = (D == 3) ? fi[2] - (float)dz * cs : 0.f;
-      for (unsigned j = j0; j < j1; ++j) {
-        const int xj = __ldg(d.W.cell + j) - row;
-        const float rx = fi[0] - __ldg(d.W.f[0] + j) - (float)(xj - c[0]) * cs;
-        const float ry = oy - __ldg(d.W.f[1] + j);
-        const float rz = (D == 3) ? oz - __ldg(d.W.f[2] + j) : 0.f;
-        fn(j, rx, ry, rz);
-      }
-    }
-  }
-}
-
+// ---------------------------------------------------------------- per-pair arithmetic
+// Eq. (9) term, or the Eq. (4) term for a buffer particle i.  (rx, ry, rz) = r_i - r_j.
 template <int D>
-__global__ void __launch_bounds__(256) k_density(DomainDev d) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) begin_step(d);
-  if (d.st->status) return;
-  const unsigned n = d.st->n;
-  const Phys P = d.P;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int c[3];
-    cell_coords(d.A.cell[i], d.g, c);
-    float fi[3] = {d.A.f[0][i], d.A.f[1][i], D == 3 ? d.A.f[2][i] : 0.f};
-    const uint8_t lab = d.A.label[i];
-    if (lab == 0) {
-      // Eq. (9): rho0 sum_j W_ij / sum W0 (self included through j = i)
-      float s = 0.f;
-      auto add = [&](unsigned, float rx, float ry, float rz) {
-        const float r2 = rx * rx + ry * ry + rz * rz;
-        if (r2 < P.two_h_sq) s += kernel_w(sqrtf(r2) * P.inv_h, P);
-      };
-      for_each_fluid<D>(d, c, fi, add);
-      for_each_wall<D>(d, c, fi, add);
-      d.rho_new[i] = P.rho0 * s * P.inv_sum_w0;
-    } else {
-      // Eq. (4) for buffer particles: drho/dt = 2 rho_i sum_j m/rho_j (v_i - v*) . grad W
-      const float vi[3] = {d.A.v[0][i], d.A.v[1][i], D == 3 ? d.A.v[2][i] : 0.f};
-      const float rho_i = d.A.rho[i];
-      const float p_i = P.c0sq * (rho_i - P.rho0);
-      float acc = 0.f;
-      for_each_fluid<D>(d, c, fi, [&](unsigned j, float rx, float ry, float rz) {
-        const float r2 = rx * rx + ry * ry + rz * rz;
-        if (r2 < P.two_h_sq && r2 > 0.f) {
-          const float r = sqrtf(r2), inv_r = 1.f / r;
-          const float vx = vi[0] - __ldg(d.A.v[0] + j), vy = vi[1] - __ldg(d.A.v[1] + j);
-          const float vz = (D == 3) ? vi[2] - __ldg(d.A.v[2] + j) : 0.f;
-          const float rho_j = __ldg(d.A.rho + j);
-          const float p_j = P.c0sq * (rho_j - P.rho0);
-          const float vij_e = (vx * rx + vy * ry + vz * rz) * inv_r;
-          const float term = 0.5f * vij_e + (p_i - p_j) / ((rho_i + rho_j) * P.c0);
-          acc += P.mass / rho_j * term * kernel_dw(r * P.inv_h, P);
+__device__ __forceinline__ float density_term(const Phys& P, bool buffer_i, bool wall, float rx, float ry, float rz,
+                                              float r, const float vi[3], float rho_i, float p_i, const float vj[3],
+                                              float rho_j) {
+  if (!buffer_i) return kernel_w(r * P.inv_h, P);
+  const float inv_r = 1.f / r;
+  float vx, vy, vz, p_j;
+  if (wall) {
+    vx = 2.f * vi[0], vy = 2.f * vi[1], vz = 2.f * vi[2];
+    rho_j = rho_i;
+    p_j = p_i;
+  } else {
+    vx = vi[0] - vj[0], vy = vi[1] - vj[1], vz = vi[2] - vj[2];
+    p_j = P.c0sq * (rho_j - P.rho0);
+  }
+  const float vij_e = (vx * rx + vy * ry + vz * rz) * inv_r;
+  const float term = 0.5f * vij_e + (p_i - p_j) / ((rho_i + rho_j) * P.c0);
+  return P.mass / rho_j * term * kernel_dw(r * P.inv_h, P);
+}
+
+// Eq. (5) / (18) pair term added to a.  pb2 = 2 p_b (0 for non-buffer particles).
+__device__ __forceinline__ void force_term(const Phys& P, bool wall, float rx, float ry, float rz, float r2,
+                                           const float vi[3], float rho_i, float p_i, float pb2, const float vj[3],
+                                           float rho_j, float a[3]) {
+  const float r = sqrtf(r2), inv_r = 1.f / r;
+  float vx, vy, vz, p_j;
+  if (wall) {
+    // mirrored wall state: v_ij = 2 v_i, rho_j = rho_i, p_j = p_i
+    vx = 2.f * vi[0], vy = 2.f * vi[1], vz = 2.f * vi[2];
+    rho_j = rho_i;
+    p_j = p_i;
+  } else {
+    vx = vi[0] - vj[0], vy = vi[1] - vj[1], vz = vi[2] - vj[2];
+    p_j = P.c0sq * (rho_j - P.rho0);
+  }
+  const float dU = -(vx * rx + vy * ry + vz * rz) * inv_r;  // U_L - U_R
+  const float beta = fminf(3.f * fmaxf(dU, 0.f), P.c0);
+  const float pstar = 0.5f * (p_i + p_j) + 0.25f * beta * (rho_i + rho_j) * dU;
+  const float m_rr = P.mass / (rho_i * rho_j) * kernel_dw(r * P.inv_h, P);
+  const float ce = m_rr * (pb2 - 2.f * pstar) * inv_r;  // along r_ij (e_ij = r_ij / r)
+  const float cv = m_rr * 2.f * P.eta * inv_r;
+  a[0] += ce * rx + cv * vx;
+  a[1] += ce * ry + cv * vy;
+  a[2] += ce * rz + cv * vz;
+}
+
+// Calls fn(wall, j, rx, ry, rz) for every particle of the 3^d cells around cell c (global
+// memory; the per-particle fallback path).
+template <int D, typename Fn>
+__device__ __forceinline__ void for_each_near(const DomainDev& d, const int c[3], const float fi[3], Fn&& fn) {
+  const Grid& g = d.g;
+  const float cs = g.cs;
+  const int x0 = max(c[0] - 1, 0), x1 = min(c[0] + 1, g.nx - 1);
+  for (int wall = 0; wall < 2; ++wall) {
+    const unsigned* start = wall ? d.W.start : d.cell_start;
+    const int* cell = wall ? d.W.cell : d.A.cell;
+    const float* const* F = wall ? d.W.f : (const float* const*)d.A.f;
+    for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); ++dz) {
+      const int z = c[2] + dz;
+      if (z < 0 || z >= g.nz) continue;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int y = c[1] + dy;
+        if (y < 0 || y >= g.ny) continue;
+        const int rb = (z * g.ny + y) * g.nx;
+        const unsigned j1 = start[rb + x1 + 1];
+        for (unsigned j = start[rb + x0]; j < j1; ++j) {
+          const int xoff = cell[j] - rb - c[0];
+          const float rx = fi[0] - F[0][j] - (float)xoff * cs;
+          const float ry = fi[1] - (float)dy * cs - F[1][j];
+          const float rz = (D == 3) ? fi[2] - (float)dz * cs - F[2][j] : 0.f;
+          fn(wall, j, rx, ry, rz);
         }
-      });
-      for_each_wall<D>(d, c, fi, [&](unsigned, float rx, float ry, float rz) {
-        const float r2 = rx * rx + ry * ry + rz * rz;
-        if (r2 < P.two_h_sq && r2 > 0.f) {
-          const float r = sqrtf(r2), inv_r = 1.f / r;
-          const float vi_e = (vi[0] * rx + vi[1] * ry + vi[2] * rz) * inv_r;  // mirrored: v_ij = 2 v_i
-          acc += P.mass / rho_i * vi_e * kernel_dw(r * P.inv_h, P);
-        }
-      });
-      d.rho_new[i] = rho_i + P.dt * (2.f * rho_i * acc);
+      }
     }
   }
 }
@@ -174,12 +148,239 @@ __device__ __forceinline__ void drift_store(const DomainDev& d, unsigned i, cons
   d.B.label[i] = lab;
 }
 
+// Kick, boundary velocity, flux, drift for centre particle i with acceleration a.
 template <int D>
-__global__ void __launch_bounds__(256) k_force(DomainDev d) {
+__device__ __forceinline__ void finish_force(const DomainDev& d, unsigned i, const int c[3], const float fi[3],
+                                             const float vi[3], float rho_i, uint8_t lab, const float a[3]) {
+  const Phys& P = d.P;
+  float v[3] = {vi[0] + a[0] * P.dt, vi[1] + a[1] * P.dt, D == 3 ? vi[2] + a[2] * P.dt : 0.f};
+  if (lab != 0) {
+    const int k = (int)lab - 1;
+    const BufDev& b = d.bufs[k];
+    if (b.vel_bc) {
+      // Eqs. (23)-(26): v = U profile(Y', Z') along u, from the start-of-step position
+      float X[3];
+      local_coords<D>(b, c, fi, d.g.cs, X, D);
+      float rr = X[1] * X[1];
+      if (D == 3) rr += X[2] * X[2];
+      const float prof = b.inv_hw2 > 0.f ? b.umax * fmaxf(1.f - rr * b.inv_hw2, 0.f) : b.umax;
+#pragma unroll
+      for (int x = 0; x < D; ++x) v[x] = prof * b.u[x];
+    } else {
+      // Eq. (19): v = (v . u) u
+      float vn = v[0] * b.u[0] + v[1] * b.u[1];
+      if (D == 3) vn += v[2] * b.u[2];
+#pragma unroll
+      for (int x = 0; x < D; ++x) v[x] = vn * b.u[x];
+    }
+    float vn = v[0] * b.u[0] + v[1] * b.u[1];
+    if (D == 3) vn += v[2] * b.u[2];
+    atomicAdd(&d.st->flux[k], (double)(vn * b.flux_scale));
+  }
+  drift_store<D>(d, i, c, fi, v, rho_i, lab);
+}
+
+__device__ __forceinline__ float boundary_pressure2(const DomainDev& d, uint8_t lab, float p_i) {
+  // Eq. (18): 2 p_b with p_b(t) prescribed, or p_b = p_i for velocity buffers (Sec. 4.2)
+  if (lab == 0) return 0.f;
+  const int k = (int)lab - 1;
+  return 2.f * (d.bufs[k].vel_bc ? p_i : d.st->pb[k]);
+}
+
+// ---------------------------------------------------------------- fallback: one particle from the cells
+template <int D>
+__device__ void force_one(const DomainDev& d, unsigned i) {
+  const Phys& P = d.P;
+  int c[3];
+  cell_coords(d.A.cell[i], d.g, c);
+  const float fi[3] = {d.A.f[0][i], d.A.f[1][i], D == 3 ? d.A.f[2][i] : 0.f};
+  const float vi[3] = {d.A.v[0][i], d.A.v[1][i], D == 3 ? d.A.v[2][i] : 0.f};
+  const uint8_t lab = d.A.label[i];
+  const float rho_i = d.rho_new[i];
+  const float p_i = P.c0sq * (rho_i - P.rho0);
+  const float pb2 = boundary_pressure2(d, lab, p_i);
+  float a[3] = {0.f, 0.f, 0.f};
+  for_each_near<D>(d, c, fi, [&](int wall, unsigned j, float rx, float ry, float rz) {
+    const float r2 = rx * rx + ry * ry + rz * rz;
+    if (r2 < P.two_h_sq && r2 > 0.f) {
+      float vj[3] = {0.f, 0.f, 0.f};
+      float rho_j = rho_i;
+      if (!wall) {
+        vj[0] = d.A.v[0][j];
+        vj[1] = d.A.v[1][j];
+        if (D == 3) vj[2] = d.A.v[2][j];
+        rho_j = d.rho_new[j];
+      }
+      force_term(P, wall, rx, ry, rz, r2, vi, rho_i, p_i, pb2, vj, rho_j, a);
+    }
+  });
+  finish_force<D>(d, i, c, fi, vi, rho_i, lab, a);
+}
+
+// ---------------------------------------------------------------- neighbour lists
+// Packed neighbour: index j (25 bits) | x-offset + 1 (2 bits) | row (4 bits) | wall (1 bit);
+// row = (dz + 1) * 3 + (dy + 1) in 3-D, dy + 1 in 2-D.
+
+// Unpacks entry e of particle (c, fi) and calls fn(wall, j, rx, ry, rz).
+template <int D, typename Fn>
+__device__ __forceinline__ void visit_entry(const DomainDev& d, unsigned ent, const float fi[3], Fn&& fn) {
+  const float cs = d.g.cs;
+  const unsigned j = ent & 0x1FFFFFFu;
+  const int xoff = (int)((ent >> 25) & 3u) - 1;
+  const int row = (int)((ent >> 27) & 15u);
+  const int wall = (int)(ent >> 31);
+  const int dy = (D == 3) ? row % 3 - 1 : row - 1;
+  const int dz = (D == 3) ? row / 3 - 1 : 0;
+  const float* f0 = wall ? d.W.f[0] : d.A.f[0];
+  const float* f1 = wall ? d.W.f[1] : d.A.f[1];
+  const float* f2 = wall ? d.W.f[2] : d.A.f[2];
+  const float rx = fi[0] - (float)xoff * cs - __ldg(f0 + j);
+  const float ry = fi[1] - (float)dy * cs - __ldg(f1 + j);
+  const float rz = (D == 3) ? fi[2] - (float)dz * cs - __ldg(f2 + j) : 0.f;
+  fn(wall, j, rx, ry, rz);
+}
+
+// Calls fn for the cnt listed neighbours of particle i (16-byte loads of 4 entries).
+template <int D, typename Fn>
+__device__ __forceinline__ void for_each_listed(const DomainDev& d, unsigned i, int cnt, const float fi[3], Fn&& fn) {
+  const uint4* lst = reinterpret_cast<const uint4*>(d.nb + (size_t)i * d.nb_cap);
+  for (int e = 0; e < cnt; e += 4) {
+    const uint4 q = __ldg(lst + (e >> 2));
+    visit_entry<D>(d, q.x, fi, fn);
+    if (e + 1 < cnt) visit_entry<D>(d, q.y, fi, fn);
+    if (e + 2 < cnt) visit_entry<D>(d, q.z, fi, fn);
+    if (e + 3 < cnt) visit_entry<D>(d, q.w, fi, fn);
+  }
+}
+
+// Neighbour-list pass: tests every candidate once and appends the in-range ones to the
+// particle's list (contiguous per particle, 16-byte stores of 4 entries, branch-free appends).
+template <int D>
+__global__ void __launch_bounds__(kThreads, 4) k_neighbours(DomainDev d) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) begin_step(d);
+  if (d.st->status) return;
+  const unsigned n = d.st->n;
+  const Grid& g = d.g;
+  const float cs = g.cs;
+  const float two_h_sq = d.P.two_h_sq;
+  const int cap = d.nb_cap;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int c[3];
+    cell_coords(d.A.cell[i], g, c);
+    const float fi[3] = {d.A.f[0][i], d.A.f[1][i], D == 3 ? d.A.f[2][i] : 0.f};
+    uint4* lst = reinterpret_cast<uint4*>(d.nb + (size_t)i * cap);
+    unsigned b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+    int cnt = 0;
+    const int x0 = max(c[0] - 1, 0), x1 = min(c[0] + 1, g.nx - 1);
+#pragma unroll 1
+    for (int wall = 0; wall < 2; ++wall) {
+      const unsigned* start = wall ? d.W.start : d.cell_start;
+      const int* cellp = wall ? d.W.cell : d.A.cell;
+      const float* f0 = wall ? d.W.f[0] : d.A.f[0];
+      const float* f1 = wall ? d.W.f[1] : d.A.f[1];
+      const float* f2 = wall ? d.W.f[2] : d.A.f[2];
+#pragma unroll 1
+      for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); ++dz) {
+        const int z = c[2] + dz;
+        if (z < 0 || z >= g.nz) continue;
+#pragma unroll 1
+        for (int dy = -1; dy <= 1; ++dy) {
+          const int y = c[1] + dy;
+          if (y < 0 || y >= g.ny) continue;
+          const int rb = (z * g.ny + y) * g.nx;
+          const unsigned tag = ((unsigned)((D == 3) ? (dz + 1) * 3 + (dy + 1) : dy + 1) << 27) |
+                               ((unsigned)wall << 31);
+          const float oy = fi[1] - (float)dy * cs;
+          const float oz = (D == 3) ? fi[2] - (float)dz * cs : 0.f;
+          const int xb = rb + c[0] - 1;  // x-offset + 1 = cell - xb
+          const unsigned j1 = __ldg(start + rb + x1 + 1);
+          for (unsigned j = __ldg(start + rb + x0); j < j1; ++j) {
+            const int xo1 = __ldg(cellp + j) - xb;
+            const float rx = fi[0] - __ldg(f0 + j) - (float)(xo1 - 1) * cs;
+            const float ry = oy - __ldg(f1 + j);
+            const float rz = (D == 3) ? oz - __ldg(f2 + j) : 0.f;
+            const float r2 = rx * rx + ry * ry + rz * rz;
+            const bool in = r2 < two_h_sq && r2 > 0.f;
+            const unsigned ent = j | ((unsigned)xo1 << 25) | tag;
+            const int slot = cnt & 3;
+            b0 = (in && slot == 0) ? ent : b0;
+            b1 = (in && slot == 1) ? ent : b1;
+            b2 = (in && slot == 2) ? ent : b2;
+            b3 = (in && slot == 3) ? ent : b3;
+            if (in && slot == 3 && cnt < cap) lst[cnt >> 2] = make_uint4(b0, b1, b2, b3);
+            cnt += in;
+          }
+        }
+      }
+    }
+    if ((cnt & 3) && cnt < cap) lst[cnt >> 2] = make_uint4(b0, b1, b2, b3);
+    d.nb_cnt[i] = (unsigned)cnt;
+  }
+}
+
+// Density pass over the lists: Eq. (9) for fluid particles, the Eq. (4) rate for buffer
+// particles.  A particle whose list overflowed (strong compression) reads its cells directly.
+template <int D>
+__global__ void __launch_bounds__(kThreads, 3) k_density(DomainDev d) {
   if (d.st->status) return;
   const unsigned n = d.st->n;
   const Phys P = d.P;
+  const int cap = d.nb_cap;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int cnt = (int)d.nb_cnt[i];
+    int c[3];
+    cell_coords(d.A.cell[i], d.g, c);
+    const float fi[3] = {d.A.f[0][i], d.A.f[1][i], D == 3 ? d.A.f[2][i] : 0.f};
+    const uint8_t lab = d.A.label[i];
+    const bool buf = lab != 0;
+    const float rho_i = d.A.rho[i];
+    const float p_i = P.c0sq * (rho_i - P.rho0);
+    float vi[3] = {0.f, 0.f, 0.f};
+    if (buf) {
+#pragma unroll
+      for (int x = 0; x < D; ++x) vi[x] = d.A.v[x][i];
+    }
+    float s = 0.f;
+    auto term = [&](int wall, unsigned j, float rx, float ry, float rz) {
+      const float r2 = rx * rx + ry * ry + rz * rz;
+      if (!buf) {
+        s += kernel_w(sqrtf(r2) * P.inv_h, P);
+      } else {
+        float vj[3] = {0.f, 0.f, 0.f};
+        float rho_j = rho_i;
+        if (!wall) {
+          vj[0] = __ldg(d.A.v[0] + j);
+          vj[1] = __ldg(d.A.v[1] + j);
+          if (D == 3) vj[2] = __ldg(d.A.v[2] + j);
+          rho_j = __ldg(d.A.rho + j);
+        }
+        s += density_term<D>(P, true, wall, rx, ry, rz, sqrtf(r2), vi, rho_i, p_i, vj, rho_j);
+      }
+    };
+    if (cnt <= cap) {
+      for_each_listed<D>(d, i, cnt, fi, term);
+    } else {
+      for_each_near<D>(d, c, fi, [&](int wall, unsigned j, float rx, float ry, float rz) {
+        const float r2 = rx * rx + ry * ry + rz * rz;
+        if (r2 < P.two_h_sq && r2 > 0.f) term(wall, j, rx, ry, rz);
+      });
+    }
+    d.rho_new[i] = buf ? rho_i + P.dt * (2.f * rho_i * s) : P.rho0 * (s + P.w_self) * P.inv_sum_w0;
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads, 3) k_force(DomainDev d) {
+  if (d.st->status) return;
+  const unsigned n = d.st->n;
+  const Phys P = d.P;
+  const int cap = d.nb_cap;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int cnt = (int)d.nb_cnt[i];
+    if (cnt > cap) {
+      force_one<D>(d, i);
+      continue;
+    }
     int c[3];
     cell_coords(d.A.cell[i], d.g, c);
     const float fi[3] = {d.A.f[0][i], d.A.f[1][i], D == 3 ? d.A.f[2][i] : 0.f};
@@ -187,74 +388,21 @@ __global__ void __launch_bounds__(256) k_force(DomainDev d) {
     const uint8_t lab = d.A.label[i];
     const float rho_i = d.rho_new[i];
     const float p_i = P.c0sq * (rho_i - P.rho0);
-    const int k = (int)lab - 1;
-    // Eq. (18): boundary pressure p_b(t), or p_i for velocity buffers (Sec. 4.2)
-    float pb2 = 0.f;
-    if (lab != 0) pb2 = 2.f * (d.bufs[k].vel_bc ? p_i : d.st->pb[k]);
-    float ax = 0.f, ay = 0.f, az = 0.f;
-    const float two_eta = 2.f * P.eta;
-    for_each_fluid<D>(d, c, fi, [&](unsigned j, float rx, float ry, float rz) {
+    const float pb2 = boundary_pressure2(d, lab, p_i);
+    float a[3] = {0.f, 0.f, 0.f};
+    for_each_listed<D>(d, i, cnt, fi, [&](int wall, unsigned j, float rx, float ry, float rz) {
       const float r2 = rx * rx + ry * ry + rz * rz;
-      if (r2 < P.two_h_sq && r2 > 0.f) {
-        const float r = sqrtf(r2), inv_r = 1.f / r;
-        const float vx = vi[0] - __ldg(d.A.v[0] + j), vy = vi[1] - __ldg(d.A.v[1] + j);
-        const float vz = (D == 3) ? vi[2] - __ldg(d.A.v[2] + j) : 0.f;
-        const float rho_j = __ldg(d.rho_new + j);
-        const float p_j = P.c0sq * (rho_j - P.rho0);
-        const float dU = -(vx * rx + vy * ry + vz * rz) * inv_r;  // U_L - U_R
-        const float beta = fminf(3.f * fmaxf(dU, 0.f), P.c0);
-        const float pstar = 0.5f * (p_i + p_j) + 0.25f * beta * (rho_i + rho_j) * dU;
-        const float dw = kernel_dw(r * P.inv_h, P);
-        const float m_rr = P.mass / (rho_i * rho_j) * dw;
-        const float ce = m_rr * (pb2 - 2.f * pstar) * inv_r;  // along r_ij (e_ij = r_ij / r)
-        const float cv = m_rr * two_eta * inv_r;
-        ax += ce * rx + cv * vx;
-        ay += ce * ry + cv * vy;
-        az += ce * rz + cv * vz;
+      float vj[3] = {0.f, 0.f, 0.f};
+      float rho_j = rho_i;
+      if (!wall) {
+        vj[0] = __ldg(d.A.v[0] + j);
+        vj[1] = __ldg(d.A.v[1] + j);
+        if (D == 3) vj[2] = __ldg(d.A.v[2] + j);
+        rho_j = __ldg(d.rho_new + j);
       }
+      force_term(P, wall, rx, ry, rz, r2, vi, rho_i, p_i, pb2, vj, rho_j, a);
     });
-    for_each_wall<D>(d, c, fi, [&](unsigned, float rx, float ry, float rz) {
-      const float r2 = rx * rx + ry * ry + rz * rz;
-      if (r2 < P.two_h_sq && r2 > 0.f) {
-        const float r = sqrtf(r2), inv_r = 1.f / r;
-        // mirrored wall state: v_ij = 2 v_i, rho_j = rho_i, p_j = p_i
-        const float vx = 2.f * vi[0], vy = 2.f * vi[1], vz = 2.f * vi[2];
-        const float dU = -(vx * rx + vy * ry + vz * rz) * inv_r;
-        const float beta = fminf(3.f * fmaxf(dU, 0.f), P.c0);
-        const float pstar = p_i + 0.5f * beta * rho_i * dU;
-        const float dw = kernel_dw(r * P.inv_h, P);
-        const float m_rr = P.mass / (rho_i * rho_i) * dw;
-        const float ce = m_rr * (pb2 - 2.f * pstar) * inv_r;
-        const float cv = m_rr * two_eta * inv_r;
-        ax += ce * rx + cv * vx;
-        ay += ce * ry + cv * vy;
-        az += ce * rz + cv * vz;
-      }
-    });
-    float v[3] = {vi[0] + ax * P.dt, vi[1] + ay * P.dt, D == 3 ? vi[2] + az * P.dt : 0.f};
-    if (lab != 0) {
-      const BufDev& b = d.bufs[k];
-      if (b.vel_bc) {
-        // Eqs. (23)-(26): v = U profile(Y', Z') along u, from the start-of-step position
-        float X[3];
-        local_coords<D>(b, c, fi, d.g.cs, X, D);
-        float rr = X[1] * X[1];
-        if (D == 3) rr += X[2] * X[2];
-        const float prof = b.inv_hw2 > 0.f ? b.umax * fmaxf(1.f - rr * b.inv_hw2, 0.f) : b.umax;
-#pragma unroll
-        for (int x = 0; x < D; ++x) v[x] = prof * b.u[x];
-      } else {
-        // Eq. (19): v = (v . u) u
-        float vn = v[0] * b.u[0] + v[1] * b.u[1];
-        if (D == 3) vn += v[2] * b.u[2];
-#pragma unroll
-        for (int x = 0; x < D; ++x) v[x] = vn * b.u[x];
-      }
-      float vn = v[0] * b.u[0] + v[1] * b.u[1];
-      if (D == 3) vn += v[2] * b.u[2];
-      atomicAdd(&d.st->flux[k], (double)(vn * b.flux_scale));
-    }
-    drift_store<D>(d, i, c, fi, v, rho_i, lab);
+    finish_force<D>(d, i, c, fi, vi, rho_i, lab, a);
   }
 }
 
@@ -277,26 +425,29 @@ int grid_for(const DomainDev& d, int per_sm) { return d.sm_count * per_sm; }
 }  // namespace
 
 int launch_density(const DomainDev& d, cudaStream_t s) {
-  if (d.g.dim == 2)
-    k_density<2><<<grid_for(d, 4), 256, 0, s>>>(d);
-  else
-    k_density<3><<<grid_for(d, 4), 256, 0, s>>>(d);
-  return 1;
+  if (d.g.dim == 2) {
+    k_neighbours<2><<<grid_for(d, 8), kThreads, 0, s>>>(d);
+    k_density<2><<<grid_for(d, 8), kThreads, 0, s>>>(d);
+  } else {
+    k_neighbours<3><<<grid_for(d, 8), kThreads, 0, s>>>(d);
+    k_density<3><<<grid_for(d, 8), kThreads, 0, s>>>(d);
+  }
+  return 2;
 }
 
 int launch_force(const DomainDev& d, cudaStream_t s) {
   if (d.g.dim == 2)
-    k_force<2><<<grid_for(d, 4), 256, 0, s>>>(d);
+    k_force<2><<<grid_for(d, 8), kThreads, 0, s>>>(d);
   else
-    k_force<3><<<grid_for(d, 4), 256, 0, s>>>(d);
+    k_force<3><<<grid_for(d, 8), kThreads, 0, s>>>(d);
   return 1;
 }
 
 int launch_drift(const DomainDev& d, cudaStream_t s) {
   if (d.g.dim == 2)
-    k_drift<2><<<grid_for(d, 8), 256, 0, s>>>(d);
+    k_drift<2><<<d.sm_count * 8, 256, 0, s>>>(d);
   else
-    k_drift<3><<<grid_for(d, 8), 256, 0, s>>>(d);
+    k_drift<3><<<d.sm_count * 8, 256, 0, s>>>(d);
   return 1;
 }
 

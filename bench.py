@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--length", type=float, default=PIPE_LEN)
     ap.add_argument("--phase-steps", type=int, default=10)
+    ap.add_argument("--spinup", type=int, default=250)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -119,7 +120,8 @@ def oracle_sample(target_particles):
     length = max(0.09, target_particles * 1e-6 / area)
     case = wl.pipe_case(name="oracle_sample", length=length, radius=0.5, dp=0.01, axis=(1.0, 1.0, 1.0),
                         inlet_bc=wl.BIDIR_PRESSURE, outlet_bc=wl.BIDIR_PRESSURE, p_in=0.0, p_amp=50.0,
-                        p_omega=math.pi, p_out=0.0, c0=3.0, nu=1e-2, seed=wl.BASE_SEED + 3)
+                        p_omega=math.pi, p_out=0.0, c0=3.0, nu=1e-2, umax=0.06, init_velocity="profile",
+                        umax_est=0.06, seed=wl.BASE_SEED + 3)
     return case, length
 
 
@@ -170,6 +172,9 @@ def run_gpu(args):
     stream = torch.cuda.Stream()
     dom = Domain.from_case(case, stream=stream)
     dom.use_graph(True)
+    # untimed spin-up from the developed profile: the lattice layers of the buffers start
+    # ~0.5 dp from the faces, so crossings begin after ~80 steps near the axis
+    dom.step(args.spinup)
     dom.step(args.warmup)
     dom.sync()
     n0 = dom.count()
@@ -207,7 +212,7 @@ def run_gpu(args):
     dom.enable_phase_timing(False)
     per = {k: v / nph for k, v in ph.items()}
 
-    # buffer-update roofline (decide + apply): algorithmic bytes per step
+    # buffer-update roofline (decisions + apply, one kernel): algorithmic bytes per step
     dim = 3
     cand = [dom.candidate_count(k) for k in range(len(case.buffers))]
     inj, dels = dom.last_decisions()
@@ -217,17 +222,22 @@ def run_gpu(args):
     bu_bytes = (4 * cells + parts * (4 * dim + 5) + len(inj) * (2 * state_bytes + 4 * dim + 4) + len(dels))
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
-    bu_s = (per["decide"] + per["apply"]) / 1e3
+    bu_s = per["buffer"] / 1e3
     bu_gbs = bu_bytes / bu_s / 1e9 if bu_s > 0 else None
 
-    # dominant kernel: the force pass, bound by FP32 arithmetic
-    pairs = lattice_pairs(dim, case.h_over_dp)
-    flops_pair = 58.0
-    force_flops = n_mean * pairs * flops_pair
-    force_tflops = force_flops / (per["force"] / 1e3) / 1e12
+    # neighbour passes, bound by FP32 arithmetic: algorithmic flops per particle
+    pairs = lattice_pairs(dim, case.h_over_dp)          # neighbours within 2h on the lattice
+    cands = 27 * (2 * case.h_over_dp) ** dim            # particles in the 27 cells of side 2h
+    flops = {"neighbours": cands * 9.0, "density": pairs * 14.0, "force": pairs * 58.0}
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     sm_max = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
     alu_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max / 1e12
+    kern = {}
+    for ph, name in (("neighbours", "k_neighbours"), ("density", "k_density"), ("force", "k_force")):
+        tf = n_mean * flops[ph] / (per[ph] / 1e3) / 1e12
+        kern[ph] = {"kernel": name, "ms": per[ph], "flops_per_particle": flops[ph], "achieved": tf,
+                    "frac": tf / alu_peak}
+    dom_ph = max(kern, key=lambda k: kern[k]["ms"])
 
     # end to end through the C ABI with host arrays
     st = dom.read()
@@ -262,14 +272,17 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "particles": int(n_mean), "walls": int(case.wall_pos.shape[0]),
                    "cells": int(dom.ncell), "buffers": len(case.buffers), "dt": case.dt,
                    "l2": "state (~%d MB) larger than L2; no flush" % (n_mean * 2 * state_bytes / 1e6),
-                   "parallelism": "replicas%d" % world, "graph": True},
-        "buffer_update_us_per_step": (per["decide"] + per["apply"]) * 1e3,
+                   "parallelism": "replicas%d" % world, "graph": True,
+                   "start": "developed parabolic profile, %d untimed spin-up steps" % args.spinup},
+        "buffer_update_us_per_step": per["buffer"] * 1e3,
         "phase_ms_per_step": per,
-        "roofline": {"bound": "alu", "kernel": "k_force", "achieved": force_tflops, "peak": alu_peak,
-                     "unit": "TFLOP/s", "frac": force_tflops / alu_peak, "traffic": None,
+        "roofline": {"bound": "alu", "kernel": kern[dom_ph]["kernel"], "achieved": kern[dom_ph]["achieved"],
+                     "peak": alu_peak, "unit": "TFLOP/s", "frac": kern[dom_ph]["frac"], "traffic": None,
                      "peak_source": "FP32 lanes x 2 x max SM clock (derived; not measured)",
-                     "flops_per_pair": flops_pair, "pairs_per_particle": pairs},
-        "roofline_buffer_update": {"bound": "hbm", "kernel": "k_decide+k_apply", "achieved": bu_gbs, "peak": hbm,
+                     "flops_per_particle": kern[dom_ph]["flops_per_particle"], "pairs_per_particle": pairs,
+                     "candidates_per_particle": cands},
+        "kernels_alu": kern,
+        "roofline_buffer_update": {"bound": "hbm", "kernel": "k_buffer", "achieved": bu_gbs, "peak": hbm,
                                    "unit": "GB/s", "frac": (bu_gbs / hbm) if (bu_gbs and hbm) else None,
                                    "traffic": None, "bytes_per_step": bu_bytes, "candidate_cells": cells,
                                    "candidate_particles": parts, "injected": len(inj), "deleted": len(dels),

@@ -193,8 +193,9 @@ sphbuf_status sphbuf_last_decisions(sphbuf_domain_t d, uint32_t *inj_buffer, uin
                                     uint32_t *del_id, uint64_t *n_del, uint64_t cap);
 
 /* Phase timing: when enabled, every step records CUDA events around its phases on the
- * domain's stream; sphbuf_read_phase_times returns the accumulated milliseconds per phase
- * [density, force, decide, apply, rebuild] and resets them (synchronises). */
+ * domain's stream (plain launches, no graph); sphbuf_read_phase_times returns the accumulated
+ * milliseconds per phase [neighbour lists, density, force (or kinematic drift), buffer update
+ * (decisions + apply), rebuild + relabel] and resets them (synchronises). */
 sphbuf_status sphbuf_enable_phase_timing(sphbuf_domain_t d, int enable);
 sphbuf_status sphbuf_read_phase_times(sphbuf_domain_t d, double ms[5], uint64_t *steps);
 

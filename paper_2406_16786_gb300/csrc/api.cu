@@ -183,7 +183,7 @@ sphbuf_status upload_buffers(sphbuf_domain* d) {
 // Inflow/bidirectional: box dilated by one cell (movement within a step); outflow: box
 // dilated by the candidate margin cs plus one cell.  A cell is kept when its centre passes
 // the separating-axis test on the box axes against the dilated box (a superset of the cells
-// the region touches).  Consecutive x-cells are merged into [lin0, lin1) segments.
+// the region touches).  One [lin, lin + 1) segment per candidate cell.
 sphbuf_status build_segments(sphbuf_domain* d) {
   const int D = d->desc.dim;
   const double cs = d->cs;
@@ -206,31 +206,23 @@ sphbuf_status build_segments(sphbuf_domain* d) {
     for (int r = 0; r < D; ++r)
       for (int x = 0; x < D; ++x) rad[r] += 0.5 * cs * std::fabs(b.R[3 * r + x]);
     for (int cz = lo_c[2]; cz <= hi_c[2]; ++cz)
-      for (int cy = lo_c[1]; cy <= hi_c[1]; ++cy) {
-        int run0 = -1;
-        for (int cx = lo_c[0]; cx <= hi_c[0] + 1; ++cx) {
-          bool keep = false;
-          if (cx <= hi_c[0]) {
-            const int cc[3] = {cx, cy, cz};
-            double ctr[3] = {0, 0, 0};
-            for (int x = 0; x < D; ++x) ctr[x] = d->desc.lo[x] + (cc[x] + 0.5) * cs - b.origin[x];
-            keep = true;
-            for (int r = 0; r < D; ++r) {
-              double X = 0;
-              for (int x = 0; x < D; ++x) X += b.R[3 * r + x] * ctr[x];
-              if (std::fabs(X) > half[r] + rad[r]) keep = false;
-            }
+      for (int cy = lo_c[1]; cy <= hi_c[1]; ++cy)
+        for (int cx = lo_c[0]; cx <= hi_c[0]; ++cx) {
+          const int cc[3] = {cx, cy, cz};
+          double ctr[3] = {0, 0, 0};
+          for (int x = 0; x < D; ++x) ctr[x] = d->desc.lo[x] + (cc[x] + 0.5) * cs - b.origin[x];
+          bool keep = true;
+          for (int r = 0; r < D; ++r) {
+            double X = 0;
+            for (int x = 0; x < D; ++x) X += b.R[3 * r + x] * ctr[x];
+            if (std::fabs(X) > half[r] + rad[r]) keep = false;
           }
+          if (!keep) continue;
           const int lin = (cz * d->dims[1] + cy) * d->dims[0] + cx;
-          if (keep && run0 < 0) run0 = lin;
-          if (!keep && run0 >= 0) {
-            seg.push_back(run0);
-            seg.push_back(lin);
-            segbuf.push_back((int)k);
-            run0 = -1;
-          }
+          seg.push_back(lin);
+          seg.push_back(lin + 1);
+          segbuf.push_back((int)k);
         }
-      }
   }
   if (d->seg_mem) {
     cudaFree(d->seg_mem);
@@ -283,6 +275,9 @@ sphbuf_status commit(sphbuf_domain* d) {
       CK(dalloc(d, &ws, (size_t)d->ncell + 1));
       CK(cudaMemset(ws, 0, ((size_t)d->ncell + 1) * sizeof(unsigned)));
       d->dev.W.start = ws;
+      float4* wp4 = nullptr;
+      CK(dalloc(d, &wp4, 1));
+      d->dev.wpos4 = wp4;
     }
     d->committed = true;
   }
@@ -299,23 +294,24 @@ sphbuf_status commit(sphbuf_domain* d) {
 int enqueue_step(sphbuf_domain* d, unsigned phases, bool timed) {
   const DomainDev& v = d->dev;
   cudaStream_t s = d->stream;
+  // phases timed: [neighbour lists, density, force (or drift), buffer update, rebuild]
   int k = 0;
   if (timed) cudaEventRecord(d->ev[0], s);
   if (phases & SPHBUF_PHASE_PHYSICS) {
-    k += launch_density(v, s);
+    k += launch_neighbours(v, s);
     if (timed) cudaEventRecord(d->ev[1], s);
+    k += launch_density(v, s);
+    if (timed) cudaEventRecord(d->ev[2], s);
     k += launch_force(v, s);
   } else {
-    k += launch_drift(v, s);
     if (timed) cudaEventRecord(d->ev[1], s);
+    if (timed) cudaEventRecord(d->ev[2], s);
+    k += launch_drift(v, s);
   }
-  if (timed) cudaEventRecord(d->ev[2], s);
+  if (timed) cudaEventRecord(d->ev[3], s);
   if (phases & SPHBUF_PHASE_BUFFER) {
     k += launch_decide(v, (phases & SPHBUF_PHASE_FULL_CHECK) != 0, s);
-    if (timed) cudaEventRecord(d->ev[3], s);
     k += launch_apply(v, s);
-  } else if (timed) {
-    cudaEventRecord(d->ev[3], s);
   }
   if (timed) cudaEventRecord(d->ev[4], s);
   k += launch_rebuild(v, true, s);
@@ -437,6 +433,8 @@ sphbuf_status sphbuf_create_domain(const sphbuf_domain_desc* desc, void* cuda_st
   // ~20 in 2-D at h = 1.3 dp on the lattice; headroom for compression)
   v.nb_cap = D == 3 ? 128 : 48;
   A(dalloc(d, &v.nb, C * (size_t)v.nb_cap));
+  A(dalloc(d, &v.pos4, C));
+  A(dalloc(d, &v.vel4, C));
   A(dalloc(d, &v.nb_cnt, C));
   A(dalloc(d, &v.slot, C));
   A(dalloc(d, &v.tmp_id, C));
@@ -513,13 +511,24 @@ sphbuf_status sphbuf_set_walls(sphbuf_domain_t d, const double* pos, uint64_t n)
     cudaFree(d->wall_mem);
     d->wall_mem = nullptr;
   }
+  // packed copy for the neighbour passes: (fx, fy, fz, cell x)
+  std::vector<float4> w4(n);
+  for (uint64_t p = 0; p < n; ++p) {
+    w4[p].x = sf[0][p];
+    w4[p].y = sf[1][p];
+    w4[p].z = D == 3 ? sf[2][p] : 0.f;
+    w4[p].w = (float)(sc[p] % d->dims[0]);
+  }
   const size_t nn = std::max<uint64_t>(n, 1);
-  const size_t bytes = nn * sizeof(int) + 3 * nn * sizeof(float) + ((size_t)d->ncell + 1) * sizeof(unsigned) + 64;
+  const size_t bytes =
+      nn * sizeof(float4) + nn * sizeof(int) + 3 * nn * sizeof(float) + ((size_t)d->ncell + 1) * sizeof(unsigned) + 64;
   CK(cudaMalloc(&d->wall_mem, bytes));
   char* p = static_cast<char*>(d->wall_mem);
-  int* wc = reinterpret_cast<int*>(p);
-  float* wf = reinterpret_cast<float*>(p + nn * sizeof(int));
-  unsigned* ws = reinterpret_cast<unsigned*>(p + nn * sizeof(int) + 3 * nn * sizeof(float));
+  float4* wp4 = reinterpret_cast<float4*>(p);
+  int* wc = reinterpret_cast<int*>(p + nn * sizeof(float4));
+  float* wf = reinterpret_cast<float*>(p + nn * sizeof(float4) + nn * sizeof(int));
+  unsigned* ws = reinterpret_cast<unsigned*>(p + nn * sizeof(float4) + nn * sizeof(int) + 3 * nn * sizeof(float));
+  if (n) CK(cudaMemcpy(wp4, w4.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
   if (n) CK(cudaMemcpy(wc, sc.data(), n * sizeof(int), cudaMemcpyHostToDevice));
   for (int x = 0; x < D; ++x)
     if (n) CK(cudaMemcpy(wf + x * nn, sf[x].data(), n * sizeof(float), cudaMemcpyHostToDevice));
@@ -527,6 +536,7 @@ sphbuf_status sphbuf_set_walls(sphbuf_domain_t d, const double* pos, uint64_t n)
   d->dev.W.cell = wc;
   for (int x = 0; x < 3; ++x) d->dev.W.f[x] = x < D ? wf + x * nn : nullptr;
   d->dev.W.start = ws;
+  d->dev.wpos4 = wp4;
   return SPHBUF_OK;
 }
 
@@ -584,6 +594,7 @@ sphbuf_status sphbuf_write_particles(sphbuf_domain_t d, const int32_t* cell, con
   st.n_del = 0;
   st.next_id = next_id;
   st.status = 0;
+  st.done_blocks = 0;
   CK(cudaMemcpy(d->dev.st, &st, sizeof(StepState), cudaMemcpyHostToDevice));
   d->labels_given = label != nullptr;
   d->need_rebuild = true;

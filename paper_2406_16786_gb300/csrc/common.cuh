@@ -65,6 +65,7 @@ struct StepState {
   unsigned n_del;      // deletions of the current step
   unsigned next_id;
   unsigned n_occ;      // occupied cells of the current cell-linked list
+  unsigned done_blocks;  // blocks of the buffer kernel that finished their decisions
   unsigned long long step;
   int status;          // latched error code (sphbuf_status), 0 = OK
   unsigned long long escaped_total;

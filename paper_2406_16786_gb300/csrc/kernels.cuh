@@ -18,6 +18,9 @@ struct DomainDev {
   unsigned* slot;         // per-particle slot from the histogram, capacity
   unsigned* tmp_id;       // ids scattered to their cell's range, capacity
   float* rho_new;         // density pass output, capacity
+  float4* pos4;           // A-order copies for the neighbour passes: (fx, fy, fz, cell x)
+  float4* vel4;           //   and (vx, vy, vz, rho); written by the rebuild scatter
+  const float4* wpos4;    // walls: (fx, fy, fz, cell x)
   unsigned* nb;           // neighbour lists, nb_cap entries per particle (16-byte aligned)
   unsigned* nb_cnt;       // neighbours found per particle (above nb_cap: direct path)
   int nb_cap;             // multiple of 4
@@ -38,6 +41,7 @@ struct DomainDev {
 };
 
 // sph (kernels_sph.cu)
+int launch_neighbours(const DomainDev& d, cudaStream_t s);  // starts the step (step constants)
 int launch_density(const DomainDev& d, cudaStream_t s);
 int launch_force(const DomainDev& d, cudaStream_t s);
 int launch_drift(const DomainDev& d, cudaStream_t s);

@@ -283,21 +283,25 @@ __global__ void __launch_bounds__(256) k_scatter(DomainDev d) {
     unsigned rank = 0;
     for (unsigned p = s0; p < s1; ++p) rank += __ldg(d.tmp_id + p) < my;
     const unsigned dst = s0 + rank;
-    float f[3];
+    float f[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f};
     d.A.cell[dst] = lin;
 #pragma unroll
     for (int x = 0; x < D; ++x) {
       f[x] = d.B.f[x][i];
+      v[x] = d.B.v[x][i];
       d.A.f[x][dst] = f[x];
-      d.A.v[x][dst] = d.B.v[x][i];
+      d.A.v[x][dst] = v[x];
     }
-    d.A.rho[dst] = d.B.rho[i];
+    const float rho = d.B.rho[i];
+    d.A.rho[dst] = rho;
     d.A.id[dst] = my;
+    int c[3];
+    cell_coords(lin, g, c);
+    d.pos4[dst] = make_float4(f[0], f[1], f[2], (float)c[0]);
+    d.vel4[dst] = make_float4(v[0], v[1], v[2], rho);
     // Algorithms 2-3, after the rebuild: in-box particles join the buffer, others leave it
     uint8_t lab = d.B.label[i];
     if (d.nrelabel) {
-      int c[3];
-      cell_coords(lin, g, c);
       for (int q = 0; q < d.nrelabel; ++q) {
         const BufDev& b = d.bufs[d.relabel_ids[q]];
         const bool near = c[0] >= b.box_lo[0] && c[0] <= b.box_hi[0] && c[1] >= b.box_lo[1] &&

@@ -24,7 +24,7 @@ namespace {
 constexpr int kThreads = 256;
 
 // Step prologue, run by one thread of the step's first kernel: per-step constants.
-__device__ void begin_step(const DomainDev& d) {
+__device__ __forceinline__ void begin_step(const DomainDev& d) {
   StepState* st = d.st;
   st->n_inj = 0;
   st->n_del = 0;
@@ -218,56 +218,57 @@ __device__ void force_one(const DomainDev& d, unsigned i) {
 }
 
 // ---------------------------------------------------------------- neighbour lists
-// Packed neighbour: index j (25 bits) | x-offset + 1 (2 bits) | row (4 bits) | wall (1 bit);
-// row = (dz + 1) * 3 + (dy + 1) in 3-D, dy + 1 in 2-D.
+// Packed neighbour: index j (25 bits) | row (4 bits, from bit 27) | wall (1 bit, bit 31);
+// row = (dz + 1) * 3 + (dy + 1) in 3-D, dy + 1 in 2-D.  The x-cell of j is pos4[j].w.
 
-// Unpacks entry e of particle (c, fi) and calls fn(wall, j, rx, ry, rz).
+// Unpacks one entry of the particle at (cell x cxf, offset fi) and calls fn(wall, j, rx, ry, rz).
 template <int D, typename Fn>
-__device__ __forceinline__ void visit_entry(const DomainDev& d, unsigned ent, const float fi[3], Fn&& fn) {
+__device__ __forceinline__ void visit_entry(const DomainDev& d, unsigned ent, float cxf, const float fi[3],
+                                            Fn&& fn) {
   const float cs = d.g.cs;
   const unsigned j = ent & 0x1FFFFFFu;
-  const int xoff = (int)((ent >> 25) & 3u) - 1;
   const int row = (int)((ent >> 27) & 15u);
   const int wall = (int)(ent >> 31);
   const int dy = (D == 3) ? row % 3 - 1 : row - 1;
   const int dz = (D == 3) ? row / 3 - 1 : 0;
-  const float* f0 = wall ? d.W.f[0] : d.A.f[0];
-  const float* f1 = wall ? d.W.f[1] : d.A.f[1];
-  const float* f2 = wall ? d.W.f[2] : d.A.f[2];
-  const float rx = fi[0] - (float)xoff * cs - __ldg(f0 + j);
-  const float ry = fi[1] - (float)dy * cs - __ldg(f1 + j);
-  const float rz = (D == 3) ? fi[2] - (float)dz * cs - __ldg(f2 + j) : 0.f;
+  const float4 p = __ldg((wall ? d.wpos4 : d.pos4) + j);
+  const float rx = fi[0] - p.x - (p.w - cxf) * cs;
+  const float ry = fi[1] - (float)dy * cs - p.y;
+  const float rz = (D == 3) ? fi[2] - (float)dz * cs - p.z : 0.f;
   fn(wall, j, rx, ry, rz);
 }
 
 // Calls fn for the cnt listed neighbours of particle i (16-byte loads of 4 entries).
 template <int D, typename Fn>
-__device__ __forceinline__ void for_each_listed(const DomainDev& d, unsigned i, int cnt, const float fi[3], Fn&& fn) {
+__device__ __forceinline__ void for_each_listed(const DomainDev& d, unsigned i, int cnt, float cxf, const float fi[3],
+                                                Fn&& fn) {
   const uint4* lst = reinterpret_cast<const uint4*>(d.nb + (size_t)i * d.nb_cap);
   for (int e = 0; e < cnt; e += 4) {
     const uint4 q = __ldg(lst + (e >> 2));
-    visit_entry<D>(d, q.x, fi, fn);
-    if (e + 1 < cnt) visit_entry<D>(d, q.y, fi, fn);
-    if (e + 2 < cnt) visit_entry<D>(d, q.z, fi, fn);
-    if (e + 3 < cnt) visit_entry<D>(d, q.w, fi, fn);
+    visit_entry<D>(d, q.x, cxf, fi, fn);
+    if (e + 1 < cnt) visit_entry<D>(d, q.y, cxf, fi, fn);
+    if (e + 2 < cnt) visit_entry<D>(d, q.z, cxf, fi, fn);
+    if (e + 3 < cnt) visit_entry<D>(d, q.w, cxf, fi, fn);
   }
 }
 
-// Neighbour-list pass: tests every candidate once and appends the in-range ones to the
-// particle's list (contiguous per particle, 16-byte stores of 4 entries, branch-free appends).
+// Neighbour-list pass: tests every candidate once (one 16-byte load each) and appends the
+// in-range ones to the particle's list (contiguous per particle, 16-byte stores of 4 entries,
+// branch-free appends).
 template <int D>
 __global__ void __launch_bounds__(kThreads, 4) k_neighbours(DomainDev d) {
   if (blockIdx.x == 0 && threadIdx.x == 0) begin_step(d);
   if (d.st->status) return;
   const unsigned n = d.st->n;
-  const Grid& g = d.g;
+  const Grid g = d.g;
   const float cs = g.cs;
   const float two_h_sq = d.P.two_h_sq;
   const int cap = d.nb_cap;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int c[3];
     cell_coords(d.A.cell[i], g, c);
-    const float fi[3] = {d.A.f[0][i], d.A.f[1][i], D == 3 ? d.A.f[2][i] : 0.f};
+    const float4 pi = d.pos4[i];
+    const float cxf = pi.w;
     uint4* lst = reinterpret_cast<uint4*>(d.nb + (size_t)i * cap);
     unsigned b0 = 0, b1 = 0, b2 = 0, b3 = 0;
     int cnt = 0;
@@ -275,10 +276,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_neighbours(DomainDev d) {
 #pragma unroll 1
     for (int wall = 0; wall < 2; ++wall) {
       const unsigned* start = wall ? d.W.start : d.cell_start;
-      const int* cellp = wall ? d.W.cell : d.A.cell;
-      const float* f0 = wall ? d.W.f[0] : d.A.f[0];
-      const float* f1 = wall ? d.W.f[1] : d.A.f[1];
-      const float* f2 = wall ? d.W.f[2] : d.A.f[2];
+      const float4* P4 = wall ? d.wpos4 : d.pos4;
 #pragma unroll 1
       for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); ++dz) {
         const int z = c[2] + dz;
@@ -290,18 +288,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_neighbours(DomainDev d) {
           const int rb = (z * g.ny + y) * g.nx;
           const unsigned tag = ((unsigned)((D == 3) ? (dz + 1) * 3 + (dy + 1) : dy + 1) << 27) |
                                ((unsigned)wall << 31);
-          const float oy = fi[1] - (float)dy * cs;
-          const float oz = (D == 3) ? fi[2] - (float)dz * cs : 0.f;
-          const int xb = rb + c[0] - 1;  // x-offset + 1 = cell - xb
+          const float ox = pi.x + cxf * cs;  // r_i.x relative to the grid row origin
+          const float oy = pi.y - (float)dy * cs;
+          const float oz = (D == 3) ? pi.z - (float)dz * cs : 0.f;
           const unsigned j1 = __ldg(start + rb + x1 + 1);
           for (unsigned j = __ldg(start + rb + x0); j < j1; ++j) {
-            const int xo1 = __ldg(cellp + j) - xb;
-            const float rx = fi[0] - __ldg(f0 + j) - (float)(xo1 - 1) * cs;
-            const float ry = oy - __ldg(f1 + j);
-            const float rz = (D == 3) ? oz - __ldg(f2 + j) : 0.f;
+            const float4 p = __ldg(P4 + j);
+            const float rx = ox - (p.x + p.w * cs);
+            const float ry = oy - p.y;
+            const float rz = (D == 3) ? oz - p.z : 0.f;
             const float r2 = rx * rx + ry * ry + rz * rz;
             const bool in = r2 < two_h_sq && r2 > 0.f;
-            const unsigned ent = j | ((unsigned)xo1 << 25) | tag;
+            const unsigned ent = j | tag;
             const int slot = cnt & 3;
             b0 = (in && slot == 0) ? ent : b0;
             b1 = (in && slot == 1) ? ent : b1;
@@ -328,18 +326,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_density(DomainDev d) {
   const int cap = d.nb_cap;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int cnt = (int)d.nb_cnt[i];
-    int c[3];
-    cell_coords(d.A.cell[i], d.g, c);
-    const float fi[3] = {d.A.f[0][i], d.A.f[1][i], D == 3 ? d.A.f[2][i] : 0.f};
+    const float4 pi = d.pos4[i];
+    const float fi[3] = {pi.x, pi.y, pi.z};
     const uint8_t lab = d.A.label[i];
     const bool buf = lab != 0;
-    const float rho_i = d.A.rho[i];
+    const float4 vi4 = d.vel4[i];
+    const float rho_i = vi4.w;
     const float p_i = P.c0sq * (rho_i - P.rho0);
-    float vi[3] = {0.f, 0.f, 0.f};
-    if (buf) {
-#pragma unroll
-      for (int x = 0; x < D; ++x) vi[x] = d.A.v[x][i];
-    }
+    const float vi[3] = {vi4.x, vi4.y, vi4.z};
     float s = 0.f;
     auto term = [&](int wall, unsigned j, float rx, float ry, float rz) {
       const float r2 = rx * rx + ry * ry + rz * rz;
@@ -349,17 +343,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_density(DomainDev d) {
         float vj[3] = {0.f, 0.f, 0.f};
         float rho_j = rho_i;
         if (!wall) {
-          vj[0] = __ldg(d.A.v[0] + j);
-          vj[1] = __ldg(d.A.v[1] + j);
-          if (D == 3) vj[2] = __ldg(d.A.v[2] + j);
-          rho_j = __ldg(d.A.rho + j);
+          const float4 v = __ldg(d.vel4 + j);
+          vj[0] = v.x, vj[1] = v.y, vj[2] = v.z;
+          rho_j = v.w;
         }
         s += density_term<D>(P, true, wall, rx, ry, rz, sqrtf(r2), vi, rho_i, p_i, vj, rho_j);
       }
     };
     if (cnt <= cap) {
-      for_each_listed<D>(d, i, cnt, fi, term);
+      for_each_listed<D>(d, i, cnt, pi.w, fi, term);
     } else {
+      int c[3];
+      cell_coords(d.A.cell[i], d.g, c);
       for_each_near<D>(d, c, fi, [&](int wall, unsigned j, float rx, float ry, float rz) {
         const float r2 = rx * rx + ry * ry + rz * rz;
         if (r2 < P.two_h_sq && r2 > 0.f) term(wall, j, rx, ry, rz);
@@ -381,27 +376,28 @@ __global__ void __launch_bounds__(kThreads, 3) k_force(DomainDev d) {
       force_one<D>(d, i);
       continue;
     }
-    int c[3];
-    cell_coords(d.A.cell[i], d.g, c);
-    const float fi[3] = {d.A.f[0][i], d.A.f[1][i], D == 3 ? d.A.f[2][i] : 0.f};
-    const float vi[3] = {d.A.v[0][i], d.A.v[1][i], D == 3 ? d.A.v[2][i] : 0.f};
+    const float4 pi = d.pos4[i];
+    const float fi[3] = {pi.x, pi.y, pi.z};
+    const float4 vi4 = d.vel4[i];
+    const float vi[3] = {vi4.x, vi4.y, vi4.z};
     const uint8_t lab = d.A.label[i];
     const float rho_i = d.rho_new[i];
     const float p_i = P.c0sq * (rho_i - P.rho0);
     const float pb2 = boundary_pressure2(d, lab, p_i);
     float a[3] = {0.f, 0.f, 0.f};
-    for_each_listed<D>(d, i, cnt, fi, [&](int wall, unsigned j, float rx, float ry, float rz) {
+    for_each_listed<D>(d, i, cnt, pi.w, fi, [&](int wall, unsigned j, float rx, float ry, float rz) {
       const float r2 = rx * rx + ry * ry + rz * rz;
       float vj[3] = {0.f, 0.f, 0.f};
       float rho_j = rho_i;
       if (!wall) {
-        vj[0] = __ldg(d.A.v[0] + j);
-        vj[1] = __ldg(d.A.v[1] + j);
-        if (D == 3) vj[2] = __ldg(d.A.v[2] + j);
+        const float4 v = __ldg(d.vel4 + j);
+        vj[0] = v.x, vj[1] = v.y, vj[2] = v.z;
         rho_j = __ldg(d.rho_new + j);
       }
       force_term(P, wall, rx, ry, rz, r2, vi, rho_i, p_i, pb2, vj, rho_j, a);
     });
+    int c[3];
+    cell_coords(d.A.cell[i], d.g, c);
     finish_force<D>(d, i, c, fi, vi, rho_i, lab, a);
   }
 }
@@ -424,15 +420,20 @@ int grid_for(const DomainDev& d, int per_sm) { return d.sm_count * per_sm; }
 
 }  // namespace
 
-int launch_density(const DomainDev& d, cudaStream_t s) {
-  if (d.g.dim == 2) {
+int launch_neighbours(const DomainDev& d, cudaStream_t s) {
+  if (d.g.dim == 2)
     k_neighbours<2><<<grid_for(d, 8), kThreads, 0, s>>>(d);
-    k_density<2><<<grid_for(d, 8), kThreads, 0, s>>>(d);
-  } else {
+  else
     k_neighbours<3><<<grid_for(d, 8), kThreads, 0, s>>>(d);
+  return 1;
+}
+
+int launch_density(const DomainDev& d, cudaStream_t s) {
+  if (d.g.dim == 2)
+    k_density<2><<<grid_for(d, 8), kThreads, 0, s>>>(d);
+  else
     k_density<3><<<grid_for(d, 8), kThreads, 0, s>>>(d);
-  }
-  return 2;
+  return 1;
 }
 
 int launch_force(const DomainDev& d, cudaStream_t s) {

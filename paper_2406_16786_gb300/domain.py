@@ -223,7 +223,7 @@ class Domain:
         ms = np.zeros(5, np.float64)
         n = ctypes.c_uint64()
         self._check(self.lib.sphbuf_read_phase_times(self.h, _ptr(ms), ctypes.byref(n)), "read_phase_times")
-        return dict(zip(["density", "force", "decide", "apply", "rebuild"], ms.tolist())), n.value
+        return dict(zip(["neighbours", "density", "force", "buffer", "rebuild"], ms.tolist())), n.value
 
     def candidate_count(self, k: int):
         c, p = ctypes.c_uint64(), ctypes.c_uint64()

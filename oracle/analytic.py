@@ -17,11 +17,16 @@ def rmsep(v_exact, v_num) -> float:
 
 
 def womersley(r, t, R: float, rho: float, eta: float, omega: float, P_n):
-    """Eq. (29): pipe velocity for a pressure gradient sum_n P'_n e^{i n omega t} (n >= 1).
+    """Eq. (29): pipe velocity for a driving pressure drop per length sum_n P'_n e^{i n omega t}.
 
-    v(r, t) = Re{ sum_n i P'_n / (rho n omega) [1 - J0(alpha n^1/2 i^3/2 r/R) / J0(alpha n^1/2 i^3/2)]
+    v(r, t) = Re{ sum_n -i P'_n / (rho n omega) [1 - J0(alpha n^1/2 i^3/2 r/R) / J0(alpha n^1/2 i^3/2)]
     e^{i n omega t} },  alpha = R sqrt(omega rho / eta).  ``P_n`` lists P'_1, P'_2, ... (complex
-    allowed); P'_n is the driving gradient -dp/dx of harmonic n.
+    allowed).
+
+    Reading: Sec. 6.1 defines P' = dP / L = 25 cos(t) as the pressure drop per length, which
+    drives flow along +X'; Eq. (29) as printed (factor +i) is written for P' = dp/dx, and at
+    small alpha gives v = -P' (R^2 - r^2) / (4 eta).  The factor -i used here gives the
+    quasi-steady Poiseuille flow v = +P' (R^2 - r^2) / (4 eta) for the text's P'.
     """
     r = np.asarray(r, dtype=np.float64)
     alpha = R * np.sqrt(omega * rho / eta)
@@ -30,7 +35,7 @@ def womersley(r, t, R: float, rho: float, eta: float, omega: float, P_n):
     for n, Pn in enumerate(P_n, start=1):
         z = alpha * np.sqrt(n) * i32
         shape = 1.0 - special.jv(0, z * r / R) / special.jv(0, z)
-        out = out + 1j * Pn / (rho * n * omega) * shape * np.exp(1j * n * omega * np.asarray(t))
+        out = out - 1j * Pn / (rho * n * omega) * shape * np.exp(1j * n * omega * np.asarray(t))
     return np.real(out)
 
 

@@ -91,11 +91,16 @@ struct Walls {
   const unsigned* start;  // wall cell_start[ncell + 1]
 };
 
-// Decision list entry: buffer k, particle index in B, particle id.
+// Decision list entry: buffer k, particle index in B, particle id; for injections also the
+// parent's state before recycling (the duplicate's state).
 struct Decision {
   unsigned k;
   unsigned idx;
   unsigned id;
+  int cell;
+  float f[3];
+  float v[3];
+  float rho;
 };
 
 struct InjRecord {

@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--length", type=float, default=PIPE_LEN)
     ap.add_argument("--phase-steps", type=int, default=10)
     ap.add_argument("--spinup", type=int, default=250)
+    ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -258,6 +260,9 @@ def run_gpu(args):
     e2e_value = world * nn * max(1, e2e_steps) / te
     del back
 
+    dom.close()
+    batched = None if args.no_batched else run_batched(args, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate = oracle_rate_probe()
@@ -292,13 +297,66 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "batched_vs_plain": batched,
     }
-    dom.close()
     if rank == 0:
         print(json.dumps(out))
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_batched(args, stream):
+    """64 independent 2-D star channels: one batch vs 64 sequential plain runs, same GPU."""
+    import torch
+
+    from paper_2406_16786_gb300 import workloads
+    from paper_2406_16786_gb300.domain import Batch, Domain
+
+    cases = workloads.config5()
+    K, W = args.batch_steps, 3
+    # plain: each domain alone (graph replays), one after another
+    plain = [Domain.from_case(c, stream=stream) for c in cases]
+    for d in plain:
+        d.use_graph(True)
+        d.step(W)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for d in plain:
+        d.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1)
+    n_plain = sum(d.count() for d in plain)
+    for d in plain:
+        d.close()
+    # batched: the same 64 domains in one batch (grid multiplier from the autotuner)
+    doms = [Domain.from_case(c, stream=stream) for c in cases]
+    b = Batch(doms, stream=stream)
+    m, _ = b.autotune(trial_steps=2)
+    b.use_graph(True)
+    b.step(W)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1)
+    b.sync()
+    n_batch = sum(d.count() for d in doms)
+    b.close()
+    for d in doms:
+        d.close()
+    nd = len(cases)
+    return {"workload": "64 2-D star channels (1-6 arms, 10k-500k particles log-uniform, mixed BCs)",
+            "domains": nd, "particles": n_batch, "steps": K,
+            "plain_domain_steps_per_s": nd * K / (t_plain / 1e3),
+            "batched_domain_steps_per_s": nd * K / (t_batch / 1e3),
+            "speedup": t_plain / t_batch, "plain_ms": t_plain, "batched_ms": t_batch,
+            "plain_particle_steps_per_s": n_plain * K / (t_plain / 1e3),
+            "batched_particle_steps_per_s": n_batch * K / (t_batch / 1e3),
+            "autotune_blocks_per_sm": m}
 
 
 def run_reference(args):

@@ -220,6 +220,34 @@ sphbuf_status sphbuf_cell_list_build(const int32_t *cell, const uint32_t *id, co
                                      uint64_t n, uint64_t ncell, uint32_t *cell_start,
                                      uint32_t *order, void *cuda_stream);
 
+/* ---------------------------------------------------------------- batched domains
+ * Many independent domains (same dim, same device) stepped together: every kernel of the
+ * step is launched once for all domains, its blocks split among the domains in proportion
+ * to their work (particles, candidate cells, scan tiles).  Results are identical to stepping
+ * each domain alone.  The batch enqueues on its own stream (cuda_stream, or a private one if
+ * NULL) after the domains' pending work, and each domain's stream waits for the batch's
+ * steps, so sphbuf_read_* on a domain after sphbuf_batch_step sees the new state.  Domains
+ * must not be stepped on their own while they belong to a batch; a domain's particles are
+ * committed (Algorithm 1 identification, first cell list) when the batch is created.  The
+ * batch does not own the domains: destroy the batch before its domains. */
+typedef struct sphbuf_batch *sphbuf_batch_t;
+
+sphbuf_status sphbuf_batch_create(sphbuf_domain_t *domains, int n, void *cuda_stream,
+                                  sphbuf_batch_t *out);
+/* nsteps steps with the given phase mask (see sphbuf_step_phases) for every domain. */
+sphbuf_status sphbuf_batch_step(sphbuf_batch_t b, int nsteps, unsigned phases);
+/* Capture one batched step into a CUDA graph and replay it (enable = 1), or plain launches. */
+sphbuf_status sphbuf_batch_use_graph(sphbuf_batch_t b, int enable);
+/* Grid-size autotuner: for each candidate multiplier m in {1, 2, 4, 8, 16} (blocks per SM of
+ * the particle kernels) runs trial_steps real steps (the domains advance), times them with
+ * CUDA events and keeps the fastest; *best_m receives it.  Candidates of the buffer kernel
+ * (cells per warp fixed) are not tuned. */
+sphbuf_status sphbuf_batch_autotune(sphbuf_batch_t b, int trial_steps, unsigned phases, int *best_m,
+                                    double ms_per_step[5]);
+/* Waits for the batch's stream and returns the first latched error of its domains. */
+sphbuf_status sphbuf_batch_sync(sphbuf_batch_t b);
+sphbuf_status sphbuf_batch_destroy(sphbuf_batch_t b);
+
 /* The same cell-linked list as sphbuf_cell_list_build, for callers that must not allocate
  * device memory: for example a host program whose GPU memory is already fully reserved by
  * another allocator, or a latency-bound loop in which cudaMalloc / cudaFree (which can

@@ -7,11 +7,11 @@ every call raises.
 """
 from . import workloads  # noqa: F401
 
-__all__ = ["workloads", "Domain", "SphbufError", "rotation_from_normal", "cell_list_build"]
+__all__ = ["workloads", "Domain", "Batch", "SphbufError", "rotation_from_normal", "cell_list_build"]
 
 
 def __getattr__(name):
-    if name in ("Domain", "SphbufError", "rotation_from_normal", "cell_list_build"):
+    if name in ("Domain", "Batch", "SphbufError", "rotation_from_normal", "cell_list_build"):
         from . import domain
 
         return getattr(domain, name)

@@ -51,6 +51,12 @@ SIGNATURES = {
     "sphbuf_read_phase_times": (ctypes.c_int, [vp, vp, P(c_u64)]),
     "sphbuf_candidate_count": (ctypes.c_int, [vp, ctypes.c_int, P(c_u64), P(c_u64)]),
     "sphbuf_read_launch_count": (ctypes.c_int, [vp, P(c_u64)]),
+    "sphbuf_batch_create": (ctypes.c_int, [vp, ctypes.c_int, vp, P(vp)]),
+    "sphbuf_batch_step": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_uint]),
+    "sphbuf_batch_use_graph": (ctypes.c_int, [vp, ctypes.c_int]),
+    "sphbuf_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_uint, P(ctypes.c_int), vp]),
+    "sphbuf_batch_sync": (ctypes.c_int, [vp]),
+    "sphbuf_batch_destroy": (ctypes.c_int, [vp]),
     "sphbuf_cell_list_build": (ctypes.c_int, [vp, vp, vp, c_u64, c_u64, vp, vp, vp]),
     "sphbuf_cell_list_build_noalloc": (ctypes.c_int, [vp, vp, vp, c_u64, c_u64, vp, vp, vp]),
 }

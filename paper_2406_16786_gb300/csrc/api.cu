@@ -966,6 +966,303 @@ sphbuf_status sphbuf_read_phase_times(sphbuf_domain_t d, double ms[5], uint64_t*
   return SPHBUF_OK;
 }
 
+// ---------------------------------------------------------------- batched domains
+struct sphbuf_batch {
+  std::vector<sphbuf_domain*> doms;
+  std::vector<uint64_t> n0;  // particles per domain when the batch was made (block shares)
+  int dim = 0;
+  int sm_count = 1;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  DomainDev* d_doms = nullptr;
+  int4* d_maps[K_COUNT] = {};
+  int nblocks[K_COUNT] = {};
+  int mult = 8;
+  bool use_graph = false;
+  cudaGraphExec_t graph = nullptr;
+  unsigned graph_phases = 0;
+  uint64_t graph_launches = 0;
+  cudaEvent_t ev[kPhases + 1] = {};
+  cudaEvent_t done = nullptr;
+  std::vector<cudaEvent_t> dom_ev;
+  std::string err;
+};
+
+static sphbuf_status batch_fail(sphbuf_batch* b, sphbuf_status s, const std::string& msg) {
+  if (b) b->err = msg;
+  return s;
+}
+
+#define BCK(call)                                                                            \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) return batch_fail(b, SPHBUF_ERR_CUDA, std::string(#call) + ": " + \
+                                             cudaGetErrorString(e_));                        \
+  } while (0)
+
+// Block maps of every batched kernel: domain d gets a share of the blocks proportional to
+// its work (particles for the particle kernels, candidate cells for the buffer kernel, scan
+// tiles for the scans, one block for the per-domain single-block kernels).
+static sphbuf_status batch_build_maps(sphbuf_batch* b, int mult) {
+  const int nd = (int)b->doms.size();
+  double total_n = 0;
+  for (uint64_t v : b->n0) total_n += (double)std::max<uint64_t>(v, 1);
+  const double T = (double)b->sm_count * mult;
+  for (int k = 0; k < K_COUNT; ++k) {
+    std::vector<int4> map;
+    for (int q = 0; q < nd; ++q) {
+      const DomainDev& v = b->doms[q]->dev;
+      int cnt = 1;
+      switch (k) {
+        case K_BUFFER:
+          cnt = std::max(1, (v.nseg + 31) / 32);
+          break;
+        case K_SCAN_REDUCE:
+        case K_SCAN_DOWN:
+          cnt = v.scan_tiles;
+          break;
+        case K_SCAN_TOP:
+        case K_FINALIZE:
+          cnt = 1;
+          break;
+        default:
+          cnt = std::max(1, (int)std::lround(T * (double)std::max<uint64_t>(b->n0[q], 1) / total_n));
+      }
+      for (int l = 0; l < cnt; ++l) map.push_back(make_int4(q, l, cnt, 0));
+    }
+    if (b->d_maps[k]) cudaFree(b->d_maps[k]);
+    b->d_maps[k] = nullptr;
+    BCK(cudaMalloc(&b->d_maps[k], map.size() * sizeof(int4)));
+    BCK(cudaMemcpy(b->d_maps[k], map.data(), map.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    b->nblocks[k] = (int)map.size();
+  }
+  b->mult = mult;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return SPHBUF_OK;
+}
+
+static int batch_launch(sphbuf_batch* b, Kern k) {
+  const BatchDev bd{b->d_doms, b->d_maps[k]};
+  const int n = b->nblocks[k];
+  switch (k) {
+    case K_NEIGHBOURS:
+    case K_DENSITY:
+    case K_FORCE:
+    case K_DRIFT:
+      return launch_batch_sph(k, b->dim, bd, n, b->stream);
+    case K_BUFFER:
+    case K_BUFFER_FULL:
+      return launch_batch_buffer(k, b->dim, bd, n, b->stream);
+    default:
+      return launch_batch_cells(k, b->dim, bd, n, b->stream);
+  }
+}
+
+// One batched step; phases timed as for a single domain.
+static int batch_enqueue_step(sphbuf_batch* b, unsigned phases, bool timed) {
+  cudaStream_t s = b->stream;
+  int k = 0;
+  if (timed) cudaEventRecord(b->ev[0], s);
+  if (phases & SPHBUF_PHASE_PHYSICS) {
+    k += batch_launch(b, K_NEIGHBOURS);
+    if (timed) cudaEventRecord(b->ev[1], s);
+    k += batch_launch(b, K_DENSITY);
+    if (timed) cudaEventRecord(b->ev[2], s);
+    k += batch_launch(b, K_FORCE);
+  } else {
+    if (timed) cudaEventRecord(b->ev[1], s);
+    if (timed) cudaEventRecord(b->ev[2], s);
+    k += batch_launch(b, K_DRIFT);
+  }
+  if (timed) cudaEventRecord(b->ev[3], s);
+  if (phases & SPHBUF_PHASE_BUFFER) k += batch_launch(b, (phases & SPHBUF_PHASE_FULL_CHECK) ? K_BUFFER_FULL : K_BUFFER);
+  if (timed) cudaEventRecord(b->ev[4], s);
+  for (Kern r : {K_HIST, K_SCAN_REDUCE, K_SCAN_TOP, K_SCAN_DOWN, K_KEYS, K_SCATTER, K_FINALIZE}) k += batch_launch(b, r);
+  if (timed) cudaEventRecord(b->ev[5], s);
+  return k;
+}
+
+static sphbuf_status batch_run(sphbuf_batch* b, int nsteps, unsigned phases, bool timed, double* acc_ms) {
+  // order after the domains' pending work
+  for (size_t q = 0; q < b->doms.size(); ++q) {
+    BCK(cudaEventRecord(b->dom_ev[q], b->doms[q]->stream));
+    BCK(cudaStreamWaitEvent(b->stream, b->dom_ev[q], 0));
+  }
+  uint64_t launched = 0;
+  for (int s = 0; s < nsteps; ++s) {
+    if (timed) {
+      launched += (uint64_t)batch_enqueue_step(b, phases, true);
+      BCK(cudaEventSynchronize(b->ev[kPhases]));
+      for (int p = 0; p < kPhases; ++p) {
+        float ms = 0;
+        BCK(cudaEventElapsedTime(&ms, b->ev[p], b->ev[p + 1]));
+        if (acc_ms) acc_ms[p] += ms;
+      }
+    } else if (b->use_graph) {
+      if (!b->graph || b->graph_phases != phases) {
+        if (b->graph) {
+          cudaGraphExecDestroy(b->graph);
+          b->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        b->graph_launches = (uint64_t)batch_enqueue_step(b, phases, false);
+        BCK(cudaStreamEndCapture(b->stream, &g));
+        BCK(cudaGraphInstantiate(&b->graph, g, 0));
+        cudaGraphDestroy(g);
+        b->graph_phases = phases;
+      }
+      BCK(cudaGraphLaunch(b->graph, b->stream));
+      launched += b->graph_launches;
+    } else {
+      launched += (uint64_t)batch_enqueue_step(b, phases, false);
+    }
+  }
+  BCK(cudaGetLastError());
+  // the domains' later work waits for the batch
+  BCK(cudaEventRecord(b->done, b->stream));
+  for (sphbuf_domain* d : b->doms) {
+    BCK(cudaStreamWaitEvent(d->stream, b->done, 0));
+    d->launches += launched;  // every kernel of the batch works for every domain
+    d->stepped = true;
+  }
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_batch_create(sphbuf_domain_t* domains, int n, void* cuda_stream, sphbuf_batch_t* out) {
+  if (!domains || n <= 0 || !out) return SPHBUF_ERR_INVALID_ARG;
+  *out = nullptr;
+  auto* b = new sphbuf_batch();
+  b->dim = domains[0] ? domains[0]->desc.dim : 0;
+  for (int q = 0; q < n; ++q) {
+    sphbuf_domain* d = domains[q];
+    if (!d || d->desc.dim != b->dim) {
+      delete b;
+      return SPHBUF_ERR_INVALID_ARG;
+    }
+    for (int r = 0; r < q; ++r)
+      if (domains[r] == d) {
+        delete b;
+        return SPHBUF_ERR_INVALID_ARG;
+      }
+    if (!d->committed && !d->need_rebuild) {
+      delete b;
+      return SPHBUF_ERR_STATE;
+    }
+    sphbuf_status s = commit(d);
+    if (s != SPHBUF_OK) {
+      delete b;
+      return s;
+    }
+    StepState st;
+    s = read_state(d, &st);
+    if (s != SPHBUF_OK) {
+      delete b;
+      return s;
+    }
+    b->doms.push_back(d);
+    b->n0.push_back(st.n);
+  }
+  b->sm_count = b->doms[0]->dev.sm_count;
+  if (cuda_stream) {
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess) {
+    b->own_stream = true;
+  } else {
+    delete b;
+    return SPHBUF_ERR_CUDA;
+  }
+  std::vector<DomainDev> host(n);
+  for (int q = 0; q < n; ++q) host[q] = b->doms[q]->dev;
+  bool ok = cudaMalloc(&b->d_doms, n * sizeof(DomainDev)) == cudaSuccess &&
+            cudaMemcpy(b->d_doms, host.data(), n * sizeof(DomainDev), cudaMemcpyHostToDevice) == cudaSuccess;
+  for (int p = 0; ok && p <= kPhases; ++p) ok = cudaEventCreate(&b->ev[p]) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess;
+  b->dom_ev.assign(n, nullptr);
+  for (int q = 0; ok && q < n; ++q) ok = cudaEventCreateWithFlags(&b->dom_ev[q], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok || batch_build_maps(b, 8) != SPHBUF_OK) {
+    sphbuf_batch_destroy(b);
+    return SPHBUF_ERR_CUDA;
+  }
+  *out = b;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_batch_step(sphbuf_batch_t b, int nsteps, unsigned phases) {
+  if (!b || nsteps < 0) return SPHBUF_ERR_INVALID_ARG;
+  const bool phys = phases & SPHBUF_PHASE_PHYSICS, kin = phases & SPHBUF_PHASE_KINEMATIC;
+  if (phys == kin || (phases & ~15u)) return batch_fail(b, SPHBUF_ERR_INVALID_ARG, "bad phase mask");
+  for (sphbuf_domain* d : b->doms)
+    if (d->need_rebuild) return batch_fail(b, SPHBUF_ERR_STATE, "a domain was rewritten after batching");
+  return batch_run(b, nsteps, phases, false, nullptr);
+}
+
+sphbuf_status sphbuf_batch_use_graph(sphbuf_batch_t b, int enable) {
+  if (!b) return SPHBUF_ERR_INVALID_ARG;
+  b->use_graph = enable != 0;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_batch_autotune(sphbuf_batch_t b, int trial_steps, unsigned phases, int* best_m,
+                                    double ms_per_step[5]) {
+  if (!b || trial_steps <= 0) return SPHBUF_ERR_INVALID_ARG;
+  const int cands[] = {1, 2, 4, 8, 16};
+  double best = 1e300;
+  int bm = b->mult;
+  std::vector<double> best_ph(kPhases, 0.0);
+  for (int m : cands) {
+    sphbuf_status s = batch_build_maps(b, m);
+    if (s != SPHBUF_OK) return s;
+    double acc[kPhases] = {0, 0, 0, 0, 0};
+    s = batch_run(b, trial_steps, phases, true, acc);
+    if (s != SPHBUF_OK) return s;
+    double tot = 0;
+    for (double v : acc) tot += v;
+    if (tot < best) {
+      best = tot;
+      bm = m;
+      for (int p = 0; p < kPhases; ++p) best_ph[p] = acc[p] / trial_steps;
+    }
+  }
+  sphbuf_status s = batch_build_maps(b, bm);
+  if (s != SPHBUF_OK) return s;
+  if (best_m) *best_m = bm;
+  if (ms_per_step)
+    for (int p = 0; p < kPhases; ++p) ms_per_step[p] = best_ph[p];
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_batch_sync(sphbuf_batch_t b) {
+  if (!b) return SPHBUF_ERR_INVALID_ARG;
+  BCK(cudaStreamSynchronize(b->stream));
+  for (sphbuf_domain* d : b->doms) {
+    StepState st;
+    sphbuf_status s = read_state(d, &st);
+    if (s != SPHBUF_OK) return batch_fail(b, s, d->err);
+  }
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_batch_destroy(sphbuf_batch_t b) {
+  if (!b) return SPHBUF_ERR_INVALID_ARG;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (int k = 0; k < K_COUNT; ++k)
+    if (b->d_maps[k]) cudaFree(b->d_maps[k]);
+  if (b->d_doms) cudaFree(b->d_doms);
+  for (int p = 0; p <= kPhases; ++p)
+    if (b->ev[p]) cudaEventDestroy(b->ev[p]);
+  if (b->done) cudaEventDestroy(b->done);
+  for (cudaEvent_t e : b->dom_ev)
+    if (e) cudaEventDestroy(e);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return SPHBUF_OK;
+}
+
 sphbuf_status sphbuf_candidate_count(sphbuf_domain_t d, int k, uint64_t* cells, uint64_t* particles) {
   if (!d || k < 0 || (size_t)k >= d->bufs.size()) return SPHBUF_ERR_INVALID_ARG;
   if (!d->committed) return fail(d, SPHBUF_ERR_STATE, "no cell-linked list yet");

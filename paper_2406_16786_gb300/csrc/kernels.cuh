@@ -40,6 +40,44 @@ struct DomainDev {
   int sm_count;
 };
 
+// Multi-domain (batched) launches: block b works for domain map[b].x as its local block
+// map[b].y of map[b].z.
+struct BatchDev {
+  const DomainDev* doms;
+  const int4* map;
+};
+
+enum Kern : int {
+  K_NEIGHBOURS,
+  K_DENSITY,
+  K_FORCE,
+  K_DRIFT,
+  K_BUFFER,
+  K_BUFFER_FULL,
+  K_HIST,
+  K_SCAN_REDUCE,
+  K_SCAN_TOP,
+  K_SCAN_DOWN,
+  K_KEYS,
+  K_SCATTER,
+  K_FINALIZE,
+  K_COUNT
+};
+
+// Copies one domain descriptor into shared memory (whole block; ends with a barrier).
+__device__ __forceinline__ void load_domain(DomainDev& dst, const DomainDev* src) {
+  const int words = (int)(sizeof(DomainDev) / sizeof(int));
+  const int* s = reinterpret_cast<const int*>(src);
+  int* t = reinterpret_cast<int*>(&dst);
+  for (int q = threadIdx.x; q < words; q += blockDim.x) t[q] = s[q];
+  __syncthreads();
+}
+
+int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s);
+int launch_batch_buffer(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s);
+int launch_batch_cells(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s);
+int batch_threads(Kern k);  // threads per block of each batched kernel
+
 // sph (kernels_sph.cu)
 int launch_neighbours(const DomainDev& d, cudaStream_t s);  // starts the step (step constants)
 int launch_density(const DomainDev& d, cudaStream_t s);

@@ -189,13 +189,13 @@ __device__ void apply_all(const DomainDev& d, unsigned long long* keys, unsigned
 // Decisions (restricted to candidate cells, or over all particles), then the duplicates by
 // the last block to finish.
 template <int D, bool FULL>
-__global__ void __launch_bounds__(kBufThreads) k_buffer(DomainDev d) {
+__device__ __forceinline__ void buffer_body(const DomainDev& d, unsigned bid, unsigned nblk) {
   __shared__ unsigned long long s_keys[kSortCap];
   __shared__ unsigned s_idx[kSortCap];
   __shared__ int s_last;
   const int lane = threadIdx.x & 31;
-  const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+  const unsigned warp = (bid * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nwarps = (nblk * blockDim.x) >> 5;
   // every block takes part in the completion count, even after an error was latched
   if (d.st->status) {
   } else if (FULL) {
@@ -228,12 +228,25 @@ __global__ void __launch_bounds__(kBufThreads) k_buffer(DomainDev d) {
   // the last block to finish writes the step's duplicates
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(&d.st->done_blocks, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) s_last = atomicAdd(&d.st->done_blocks, 1u) == nblk - 1;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
   apply_all<D>(d, s_keys, s_idx);
   if (threadIdx.x == 0) d.st->done_blocks = 0;
+}
+
+template <int D, bool FULL>
+__global__ void __launch_bounds__(kBufThreads) k_buffer(DomainDev d) {
+  buffer_body<D, FULL>(d, blockIdx.x, gridDim.x);
+}
+
+template <int D, bool FULL>
+__global__ void __launch_bounds__(kBufThreads) k_buffer_batch(BatchDev b) {
+  __shared__ DomainDev sd;
+  const int4 m = b.map[blockIdx.x];
+  load_domain(sd, b.doms + m.x);
+  buffer_body<D, FULL>(sd, (unsigned)m.y, (unsigned)m.z);
 }
 
 template <int D>
@@ -301,5 +314,23 @@ int launch_decide(const DomainDev& d, bool full_domain, cudaStream_t s) {
 }
 
 int launch_apply(const DomainDev&, cudaStream_t) { return 0; }  // applied inside k_buffer
+
+int launch_batch_buffer(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s) {
+  if (k == K_BUFFER) {
+    if (dim == 2)
+      k_buffer_batch<2, false><<<nblocks, kBufThreads, 0, s>>>(b);
+    else
+      k_buffer_batch<3, false><<<nblocks, kBufThreads, 0, s>>>(b);
+    return 1;
+  }
+  if (k == K_BUFFER_FULL) {
+    if (dim == 2)
+      k_buffer_batch<2, true><<<nblocks, kBufThreads, 0, s>>>(b);
+    else
+      k_buffer_batch<3, true><<<nblocks, kBufThreads, 0, s>>>(b);
+    return 1;
+  }
+  return 0;
+}
 
 }  // namespace sphbuf

@@ -156,13 +156,10 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned* ws, un
   return wpre + incl - x;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce_occ(const unsigned* __restrict__ cnt,
-                                                                  unsigned* __restrict__ part,
-                                                                  unsigned* __restrict__ part_occ,
-                                                                  const int* status) {
-  if (*status) return;
+__device__ __forceinline__ void scan_reduce_occ_body(const unsigned* __restrict__ cnt, unsigned* __restrict__ part,
+                                                     unsigned* __restrict__ part_occ, unsigned tile) {
   __shared__ unsigned ws[kScanThreads / 32];
-  const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
+  const size_t base = (size_t)tile * kScanTile + (size_t)threadIdx.x * kScanItems;
   const uint4* p = reinterpret_cast<const uint4*>(cnt + base);
   unsigned s = 0, o = 0;
 #pragma unroll
@@ -175,18 +172,16 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce_occ(const unsigned
   block_excl_scan(s, ws, &ts);
   block_excl_scan(o, ws, &to);
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = ts;
-    part_occ[blockIdx.x] = to;
+    part[tile] = ts;
+    part_occ[tile] = to;
   }
 }
 
 // Exclusive scans of both per-tile sums (one block); the total occupied count goes to *n_occ.
-__global__ void __launch_bounds__(1024) k_scan_top_occ(unsigned* part, unsigned* part_occ, int ntiles,
-                                                       const int* status, unsigned* n_occ) {
-  if (*status) return;
+__device__ __forceinline__ void scan_top_occ_body(unsigned* part, unsigned* part_occ, int ntiles, unsigned* n_occ) {
   __shared__ unsigned ws[32];
   unsigned carry = 0, carry_o = 0;
-  for (int b0 = 0; b0 < ntiles; b0 += 1024) {
+  for (int b0 = 0; b0 < ntiles; b0 += blockDim.x) {
     const int t = b0 + threadIdx.x;
     const unsigned v = t < ntiles ? part[t] : 0u;
     const unsigned vo = t < ntiles ? part_occ[t] : 0u;
@@ -203,15 +198,11 @@ __global__ void __launch_bounds__(1024) k_scan_top_occ(unsigned* part, unsigned*
   if (threadIdx.x == 0) *n_occ = carry_o;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_down_occ(unsigned* __restrict__ cnt,
-                                                                const unsigned* __restrict__ part,
-                                                                const unsigned* __restrict__ part_occ,
-                                                                unsigned* __restrict__ start,
-                                                                unsigned* __restrict__ occ_list,
-                                                                const int* status) {
-  if (*status) return;
+__device__ __forceinline__ void scan_down_occ_body(unsigned* __restrict__ cnt, const unsigned* __restrict__ part,
+                                                   const unsigned* __restrict__ part_occ, unsigned* __restrict__ start,
+                                                   unsigned* __restrict__ occ_list, unsigned tile) {
   __shared__ unsigned ws[kScanThreads / 32];
-  const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
+  const size_t base = (size_t)tile * kScanTile + (size_t)threadIdx.x * kScanItems;
   uint4* p = reinterpret_cast<uint4*>(cnt + base);
   unsigned v[kScanItems];
 #pragma unroll
@@ -229,8 +220,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down_occ(unsigned* __rest
     s += v[q];
     o += v[q] > 0;
   }
-  unsigned run = part[blockIdx.x] + block_excl_scan(s, ws, nullptr);
-  unsigned orun = part_occ[blockIdx.x] + block_excl_scan(o, ws, nullptr);
+  unsigned run = part[tile] + block_excl_scan(s, ws, nullptr);
+  unsigned orun = part_occ[tile] + block_excl_scan(o, ws, nullptr);
   uint4* out = reinterpret_cast<uint4*>(start + base);
 #pragma unroll
   for (int q = 0; q < kScanItems / 4; ++q) {
@@ -250,10 +241,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down_occ(unsigned* __rest
     if (v[q]) occ_list[orun++] = (unsigned)(base + q);
 }
 
-__global__ void __launch_bounds__(256) k_hist(DomainDev d) {
+__device__ __forceinline__ void hist_body(const DomainDev& d, unsigned bid, unsigned nblk) {
   if (d.st->status) return;
   const unsigned n = d.st->n + d.st->n_inj;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
     if (d.B.label[i] == kDead)
       d.slot[i] = kNoSlot;
     else
@@ -261,21 +252,21 @@ __global__ void __launch_bounds__(256) k_hist(DomainDev d) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_keys(DomainDev d) {
+__device__ __forceinline__ void keys_body(const DomainDev& d, unsigned bid, unsigned nblk) {
   if (d.st->status) return;
   const unsigned n = d.st->n + d.st->n_inj;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
     const unsigned sl = d.slot[i];
     if (sl != kNoSlot) d.tmp_id[d.cell_start[d.B.cell[i]] + sl] = d.B.id[i];
   }
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) k_scatter(DomainDev d) {
+__device__ __forceinline__ void scatter_body(const DomainDev& d, unsigned bid, unsigned nblk) {
   if (d.st->status) return;
   const unsigned n = d.st->n + d.st->n_inj;
   const Grid& g = d.g;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
     if (d.slot[i] == kNoSlot) continue;
     const int lin = d.B.cell[i];
     const unsigned s0 = d.cell_start[lin], s1 = d.cell_start[lin + 1];
@@ -319,13 +310,74 @@ __global__ void __launch_bounds__(256) k_scatter(DomainDev d) {
   }
 }
 
-__global__ void k_finalize(DomainDev d, int count_step) {
+__device__ __forceinline__ void finalize_body(const DomainDev& d, int count_step) {
   StepState* st = d.st;
   if (st->status) return;
   st->n = d.cell_start[d.g.ncell];
   st->next_id += min(st->n_inj, d.P.list_cap);
   if (count_step) st->step += 1;
 }
+
+// ---- single-domain kernels
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce_occ(DomainDev d) {
+  if (d.st->status) return;
+  scan_reduce_occ_body(d.cnt, d.scan_part, d.scan_part_occ, blockIdx.x);
+}
+__global__ void __launch_bounds__(1024) k_scan_top_occ(DomainDev d) {
+  if (d.st->status) return;
+  scan_top_occ_body(d.scan_part, d.scan_part_occ, d.scan_tiles, &d.st->n_occ);
+}
+__global__ void __launch_bounds__(kScanThreads) k_scan_down_occ(DomainDev d) {
+  if (d.st->status) return;
+  scan_down_occ_body(d.cnt, d.scan_part, d.scan_part_occ, d.cell_start, d.occ_list, blockIdx.x);
+}
+__global__ void __launch_bounds__(256) k_hist(DomainDev d) { hist_body(d, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(256) k_keys(DomainDev d) { keys_body(d, blockIdx.x, gridDim.x); }
+template <int D>
+__global__ void __launch_bounds__(256) k_scatter(DomainDev d) {
+  scatter_body<D>(d, blockIdx.x, gridDim.x);
+}
+__global__ void k_finalize(DomainDev d, int count_step) { finalize_body(d, count_step); }
+
+// ---- batched twins (block -> (domain, local block, blocks of the domain))
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce_occ_batch(BatchDev b) {
+  const int4 m = b.map[blockIdx.x];
+  const DomainDev* d = b.doms + m.x;
+  if (d->st->status) return;
+  scan_reduce_occ_body(d->cnt, d->scan_part, d->scan_part_occ, (unsigned)m.y);
+}
+__global__ void __launch_bounds__(1024) k_scan_top_occ_batch(BatchDev b) {
+  const int4 m = b.map[blockIdx.x];
+  const DomainDev* d = b.doms + m.x;
+  if (d->st->status) return;
+  scan_top_occ_body(d->scan_part, d->scan_part_occ, d->scan_tiles, &d->st->n_occ);
+}
+__global__ void __launch_bounds__(kScanThreads) k_scan_down_occ_batch(BatchDev b) {
+  const int4 m = b.map[blockIdx.x];
+  const DomainDev* d = b.doms + m.x;
+  if (d->st->status) return;
+  scan_down_occ_body(d->cnt, d->scan_part, d->scan_part_occ, d->cell_start, d->occ_list, (unsigned)m.y);
+}
+__global__ void __launch_bounds__(256) k_hist_batch(BatchDev b) {
+  __shared__ DomainDev sd;
+  const int4 m = b.map[blockIdx.x];
+  load_domain(sd, b.doms + m.x);
+  hist_body(sd, (unsigned)m.y, (unsigned)m.z);
+}
+__global__ void __launch_bounds__(256) k_keys_batch(BatchDev b) {
+  __shared__ DomainDev sd;
+  const int4 m = b.map[blockIdx.x];
+  load_domain(sd, b.doms + m.x);
+  keys_body(sd, (unsigned)m.y, (unsigned)m.z);
+}
+template <int D>
+__global__ void __launch_bounds__(256) k_scatter_batch(BatchDev b) {
+  __shared__ DomainDev sd;
+  const int4 m = b.map[blockIdx.x];
+  load_domain(sd, b.doms + m.x);
+  scatter_body<D>(sd, (unsigned)m.y, (unsigned)m.z);
+}
+__global__ void k_finalize_batch(BatchDev b) { finalize_body(b.doms[b.map[blockIdx.x].x], 1); }
 
 __global__ void k_decode(DomainDev d, double* out, double lo0, double lo1, double lo2, double cs) {
   const unsigned n = d.st->n;
@@ -379,10 +431,9 @@ __global__ void k_order_raw(const int32_t* cell, const uint32_t* id, unsigned n,
 int launch_rebuild(const DomainDev& d, bool count_step, cudaStream_t s) {
   const int blocks = d.sm_count * 8;
   k_hist<<<blocks, 256, 0, s>>>(d);
-  k_scan_reduce_occ<<<d.scan_tiles, kScanThreads, 0, s>>>(d.cnt, d.scan_part, d.scan_part_occ, &d.st->status);
-  k_scan_top_occ<<<1, 1024, 0, s>>>(d.scan_part, d.scan_part_occ, d.scan_tiles, &d.st->status, &d.st->n_occ);
-  k_scan_down_occ<<<d.scan_tiles, kScanThreads, 0, s>>>(d.cnt, d.scan_part, d.scan_part_occ, d.cell_start,
-                                                       d.occ_list, &d.st->status);
+  k_scan_reduce_occ<<<d.scan_tiles, kScanThreads, 0, s>>>(d);
+  k_scan_top_occ<<<1, 1024, 0, s>>>(d);
+  k_scan_down_occ<<<d.scan_tiles, kScanThreads, 0, s>>>(d);
   k_keys<<<blocks, 256, 0, s>>>(d);
   if (d.g.dim == 2)
     k_scatter<2><<<blocks, 256, 0, s>>>(d);
@@ -390,6 +441,48 @@ int launch_rebuild(const DomainDev& d, bool count_step, cudaStream_t s) {
     k_scatter<3><<<blocks, 256, 0, s>>>(d);
   k_finalize<<<1, 1, 0, s>>>(d, count_step ? 1 : 0);
   return 7;
+}
+
+int launch_batch_cells(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s) {
+  switch (k) {
+    case K_HIST:
+      k_hist_batch<<<nblocks, 256, 0, s>>>(b);
+      return 1;
+    case K_SCAN_REDUCE:
+      k_scan_reduce_occ_batch<<<nblocks, kScanThreads, 0, s>>>(b);
+      return 1;
+    case K_SCAN_TOP:
+      k_scan_top_occ_batch<<<nblocks, 1024, 0, s>>>(b);
+      return 1;
+    case K_SCAN_DOWN:
+      k_scan_down_occ_batch<<<nblocks, kScanThreads, 0, s>>>(b);
+      return 1;
+    case K_KEYS:
+      k_keys_batch<<<nblocks, 256, 0, s>>>(b);
+      return 1;
+    case K_SCATTER:
+      if (dim == 2)
+        k_scatter_batch<2><<<nblocks, 256, 0, s>>>(b);
+      else
+        k_scatter_batch<3><<<nblocks, 256, 0, s>>>(b);
+      return 1;
+    case K_FINALIZE:
+      k_finalize_batch<<<nblocks, 1, 0, s>>>(b);
+      return 1;
+    default:
+      return 0;
+  }
+}
+
+int batch_threads(Kern k) {
+  switch (k) {
+    case K_SCAN_TOP:
+      return 1024;
+    case K_FINALIZE:
+      return 1;
+    default:
+      return 256;
+  }
 }
 
 void launch_decode_positions(const DomainDev& d, double* pos_out, const double lo[3], double cs,

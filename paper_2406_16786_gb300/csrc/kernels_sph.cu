@@ -256,15 +256,15 @@ __device__ __forceinline__ void for_each_listed(const DomainDev& d, unsigned i, 
 // in-range ones to the particle's list (contiguous per particle, 16-byte stores of 4 entries,
 // branch-free appends).
 template <int D>
-__global__ void __launch_bounds__(kThreads, 4) k_neighbours(DomainDev d) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) begin_step(d);
+__device__ __forceinline__ void neighbours_body(const DomainDev& d, unsigned bid, unsigned nblk) {
+  if (bid == 0 && threadIdx.x == 0) begin_step(d);
   if (d.st->status) return;
   const unsigned n = d.st->n;
   const Grid g = d.g;
   const float cs = g.cs;
   const float two_h_sq = d.P.two_h_sq;
   const int cap = d.nb_cap;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
     int c[3];
     cell_coords(d.A.cell[i], g, c);
     const float4 pi = d.pos4[i];
@@ -319,12 +319,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_neighbours(DomainDev d) {
 // Density pass over the lists: Eq. (9) for fluid particles, the Eq. (4) rate for buffer
 // particles.  A particle whose list overflowed (strong compression) reads its cells directly.
 template <int D>
-__global__ void __launch_bounds__(kThreads, 3) k_density(DomainDev d) {
+__device__ __forceinline__ void density_body(const DomainDev& d, unsigned bid, unsigned nblk) {
   if (d.st->status) return;
   const unsigned n = d.st->n;
   const Phys P = d.P;
   const int cap = d.nb_cap;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
     const int cnt = (int)d.nb_cnt[i];
     const float4 pi = d.pos4[i];
     const float fi[3] = {pi.x, pi.y, pi.z};
@@ -365,12 +365,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_density(DomainDev d) {
 }
 
 template <int D>
-__global__ void __launch_bounds__(kThreads, 3) k_force(DomainDev d) {
+__device__ __forceinline__ void force_body(const DomainDev& d, unsigned bid, unsigned nblk) {
   if (d.st->status) return;
   const unsigned n = d.st->n;
   const Phys P = d.P;
   const int cap = d.nb_cap;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
     const int cnt = (int)d.nb_cnt[i];
     if (cnt > cap) {
       force_one<D>(d, i);
@@ -403,11 +403,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_force(DomainDev d) {
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) k_drift(DomainDev d) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) begin_step(d);
+__device__ __forceinline__ void drift_body(const DomainDev& d, unsigned bid, unsigned nblk) {
+  if (bid == 0 && threadIdx.x == 0) begin_step(d);
   if (d.st->status) return;
   const unsigned n = d.st->n;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
     int c[3];
     cell_coords(d.A.cell[i], d.g, c);
     const float fi[3] = {d.A.f[0][i], d.A.f[1][i], D == 3 ? d.A.f[2][i] : 0.f};
@@ -415,6 +415,28 @@ __global__ void __launch_bounds__(256) k_drift(DomainDev d) {
     drift_store<D>(d, i, c, fi, v, d.A.rho[i], d.A.label[i]);
   }
 }
+
+// Single-domain kernels and their multi-domain (batched) twins: block b of a batched launch
+// works for domain map[b].x as its block map[b].y of map[b].z; the domain's descriptor is
+// copied to shared memory first.
+#define SPHBUF_PAIR(NAME, BODY, BOUNDS)                                                          \
+  template <int D>                                                                             \
+  __global__ void __launch_bounds__ BOUNDS NAME(DomainDev d) {                                 \
+    BODY<D>(d, blockIdx.x, gridDim.x);                                                         \
+  }                                                                                            \
+  template <int D>                                                                             \
+  __global__ void __launch_bounds__ BOUNDS NAME##_batch(BatchDev b) {                          \
+    __shared__ DomainDev sd;                                                                   \
+    const int4 m = b.map[blockIdx.x];                                                          \
+    load_domain(sd, b.doms + m.x);                                                             \
+    BODY<D>(sd, (unsigned)m.y, (unsigned)m.z);                                                 \
+  }
+
+SPHBUF_PAIR(k_neighbours, neighbours_body, (kThreads, 4))
+SPHBUF_PAIR(k_density, density_body, (kThreads, 3))
+SPHBUF_PAIR(k_force, force_body, (kThreads, 3))
+SPHBUF_PAIR(k_drift, drift_body, (kThreads))
+#undef SPHBUF_PAIR
 
 int grid_for(const DomainDev& d, int per_sm) { return d.sm_count * per_sm; }
 
@@ -446,10 +468,29 @@ int launch_force(const DomainDev& d, cudaStream_t s) {
 
 int launch_drift(const DomainDev& d, cudaStream_t s) {
   if (d.g.dim == 2)
-    k_drift<2><<<d.sm_count * 8, 256, 0, s>>>(d);
+    k_drift<2><<<d.sm_count * 8, kThreads, 0, s>>>(d);
   else
-    k_drift<3><<<d.sm_count * 8, 256, 0, s>>>(d);
+    k_drift<3><<<d.sm_count * 8, kThreads, 0, s>>>(d);
   return 1;
+}
+
+int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s) {
+#define SPHBUF_CASE(KID, NAME)                                             \
+  case KID:                                                                \
+    if (dim == 2)                                                          \
+      NAME##_batch<2><<<nblocks, kThreads, 0, s>>>(b);                     \
+    else                                                                   \
+      NAME##_batch<3><<<nblocks, kThreads, 0, s>>>(b);                     \
+    return 1;
+  switch (k) {
+    SPHBUF_CASE(K_NEIGHBOURS, k_neighbours)
+    SPHBUF_CASE(K_DENSITY, k_density)
+    SPHBUF_CASE(K_FORCE, k_force)
+    SPHBUF_CASE(K_DRIFT, k_drift)
+    default:
+      return 0;
+  }
+#undef SPHBUF_CASE
 }
 
 }  // namespace sphbuf

@@ -63,6 +63,55 @@ def cell_list_build(cell_dev: int, id_dev: int, label_dev: Optional[int], n: int
         raise SphbufError(st, "cell_list_build")
 
 
+class Batch:
+    """Independent domains stepped together by multi-domain kernel launches."""
+
+    def __init__(self, domains, stream=None):
+        self.lib = _ffi.load()
+        self.domains = list(domains)  # keeps the domains alive while batched
+        self._stream = stream
+        arr = (ctypes.c_void_p * len(self.domains))(*[d.h.value for d in self.domains])
+        h = ctypes.c_void_p()
+        handle = _stream_handle(stream)
+        st = self.lib.sphbuf_batch_create(arr, len(self.domains),
+                                          None if handle is None else ctypes.c_void_p(handle), ctypes.byref(h))
+        if st:
+            raise SphbufError(st, "batch_create")
+        self.h = h
+
+    def step(self, nsteps=1, phases=_ffi.STEP_DEFAULT):
+        st = self.lib.sphbuf_batch_step(self.h, int(nsteps), int(phases))
+        if st:
+            raise SphbufError(st, "batch_step")
+
+    def use_graph(self, enable=True):
+        self.lib.sphbuf_batch_use_graph(self.h, 1 if enable else 0)
+
+    def autotune(self, trial_steps=3, phases=_ffi.STEP_DEFAULT):
+        m = ctypes.c_int()
+        ms = np.zeros(5, np.float64)
+        st = self.lib.sphbuf_batch_autotune(self.h, int(trial_steps), int(phases), ctypes.byref(m), _ptr(ms))
+        if st:
+            raise SphbufError(st, "batch_autotune")
+        return m.value, dict(zip(["neighbours", "density", "force", "buffer", "rebuild"], ms.tolist()))
+
+    def sync(self):
+        st = self.lib.sphbuf_batch_sync(self.h)
+        if st:
+            raise SphbufError(st, "batch_sync")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sphbuf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Domain:
     """One simulation domain owned by the library (device memory, buffers, stream)."""
 

@@ -413,6 +413,90 @@ def perturbed_state(case: Case, dv: float, drho: float, seed: int = 11):
     return vel, rho
 
 
+def star_case(*, seed, n_target, arms, width, name="star", umax=1.0, c0=10.0, nu=1e-2, rho0=1000.0,
+              h_over_dp=1.3, buffer_layers=4, p_amp=500.0, p_freq=2.0, capacity_factor=1.6) -> Case:
+    """2-D "star" channel: ``arms`` straight arms of width ``width`` leaving a central junction.
+
+    Arm directions are seeded uniform angles at least 40 deg apart; arm length = 4 x width; the
+    spacing dp is chosen so that about ``n_target`` fluid particles fill the star.  Fluid = a
+    global lattice (jittered) inside any arm rectangle or the junction disc; walls = three
+    lattice layers around it, left open at the arm ends.  With two or more arms, arm 0 ends in
+    a plug velocity inlet (U = ``umax``) and the others in pressure outlets (p = 0); a single
+    arm is a dead end whose open end carries a bidirectional pressure buffer with
+    p_b(t) = ``p_amp`` sin(2 pi ``p_freq`` t).
+    """
+    rng = np.random.default_rng(seed)
+    for _ in range(1000):
+        ang = np.sort(rng.uniform(0.0, 2.0 * math.pi, arms))
+        gaps = np.diff(np.concatenate([ang, ang[:1] + 2.0 * math.pi]))
+        if arms == 1 or gaps.min() >= math.radians(40.0):
+            break
+    L = 4.0 * width
+    half = 0.5 * width
+    area = arms * L * width + math.pi * half * half
+    dp = math.sqrt(area / n_target)
+    ext = L + 4 * dp
+    ax = (np.arange(-int(ext / dp) - 1, int(ext / dp) + 2) + 0.5) * dp
+    X, Y = np.meshgrid(ax, ax, indexing="ij")
+    P = np.stack([X.ravel(), Y.ravel()], axis=1)
+    E = np.stack([np.cos(ang), np.sin(ang)], axis=1)
+    N = np.stack([-np.sin(ang), np.cos(ang)], axis=1)
+    s = P @ E.T  # (npts, arms)
+    t = P @ N.T
+    r = np.linalg.norm(P, axis=1)
+    fluid_m = (r < half) | np.any((s >= 0.0) & (s < L) & (np.abs(t) < half), axis=1)
+    wall_band = 3 * dp
+    near = (r < half + wall_band) | np.any((s >= -half) & (s < L + wall_band) & (np.abs(t) < half + wall_band),
+                                           axis=1)
+    wall_m = near & ~fluid_m
+    # keep the arm ends open: no wall beyond s = L in front of an arm's cross-section
+    for k in range(arms):
+        wall_m &= ~((s[:, k] >= L) & (np.abs(t[:, k]) < half))
+    fluid = P[fluid_m] + rng.uniform(-0.01 * dp, 0.01 * dp, size=(int(fluid_m.sum()), 2))
+    wall = P[wall_m]
+    h = h_over_dp * dp
+    lo, hi = _grid_box([fluid, wall], margin=2.0 * (2.0 * h))
+    a = buffer_layers * dp
+    bufs = []
+    for k in range(arms):
+        e = E[k]
+        theta = math.atan2(e[1], e[0])
+        centre = np.array([e[0] * (L - 0.5 * a), e[1] * (L - 0.5 * a), 0.0])
+        if arms == 1:
+            bufs.append(BufferSpec(origin=centre, rotation=frame_2d(theta + math.pi), extent=np.array([a, width, 0.0]),
+                                   bc=BIDIR_PRESSURE, p_b=0.0, p_amp=p_amp, p_omega=2.0 * math.pi * p_freq))
+        elif k == 0:
+            bufs.append(BufferSpec(origin=centre, rotation=frame_2d(theta + math.pi), extent=np.array([a, width, 0.0]),
+                                   bc=VELOCITY_INLET, umax=umax, half_width=0.0))
+        else:
+            bufs.append(BufferSpec(origin=centre, rotation=frame_2d(theta), extent=np.array([a, width, 0.0]),
+                                   bc=PRESSURE_OUTLET, p_b=0.0))
+    vel = np.zeros_like(fluid)
+    if arms >= 2:
+        loc = fluid @ E[0]
+        tt = fluid @ N[0]
+        inb = (loc > L - a) & (np.abs(tt) < half)
+        vel[inb] = -umax * E[0][None, :]
+    dt = min(0.25 * h / (c0 + umax), 0.125 * h * h / nu)
+    n = fluid.shape[0]
+    return Case(name="%s_k%d_w%.2f_n%d" % (name, arms, width, n), dim=2, lo=lo, hi=hi, dp=dp, h_over_dp=h_over_dp,
+                rho0=rho0, c0=c0, nu=nu, dt=dt, fluid_pos=fluid, fluid_vel=vel, fluid_rho=np.full(n, rho0),
+                wall_pos=wall, buffers=bufs, capacity=int(capacity_factor * n) + 1024, steps=500)
+
+
+def config5(ndomains=64, n_lo=10_000, n_hi=500_000, seed=BASE_SEED + 5) -> List[Case]:
+    """64 independent 2-D star channels: log-uniform sizes in [10 k, 500 k] particles, 1-6 arms,
+    widths 0.2-1 m, seeded angles (the batched workload)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(ndomains):
+        n_t = int(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi))))
+        arms = int(rng.integers(1, 7))
+        width = float(rng.uniform(0.2, 1.0))
+        out.append(star_case(seed=seed * 1000 + q, n_target=n_t, arms=arms, width=width, name="star%02d" % q))
+    return out
+
+
 def config1() -> Case:
     """10 x 1 m straight channel along x, dp 0.025: plug velocity inlet U = 1, pressure outlet p = 0."""
     return straight_channel_case(name="cfg1_channel_10x1_dp0.025", length=10.0, width=1.0, dp=0.025,

@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--spinup", type=int, default=250)
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--tj-steps", type=int, default=10)
+    ap.add_argument("--no-tjunction", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -262,6 +264,7 @@ def run_gpu(args):
 
     dom.close()
     batched = None if args.no_batched else run_batched(args, stream)
+    tjunction = None if args.no_tjunction else run_restricted_vs_full(args, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -298,6 +301,7 @@ def run_gpu(args):
         "clocks": clk,
         "cpu_baseline": cpu,
         "batched_vs_plain": batched,
+        "restricted_vs_full_16M": tjunction,
     }
     if rank == 0:
         print(json.dumps(out))
@@ -357,6 +361,48 @@ def run_batched(args, stream):
             "plain_particle_steps_per_s": n_plain * K / (t_plain / 1e3),
             "batched_particle_steps_per_s": n_batch * K / (t_batch / 1e3),
             "autotune_blocks_per_sm": m}
+
+
+def run_restricted_vs_full(args, stream):
+    """16 M-particle T-junction: buffer update restricted to the cells around each buffer
+    (the paper's method) vs every particle against every buffer (same decisions)."""
+    import torch
+
+    from paper_2406_16786_gb300 import _ffi, workloads
+    from paper_2406_16786_gb300.domain import Domain
+
+    case = workloads.config4()
+    dom = Domain.from_case(case, stream=stream)
+    dom.use_graph(True)
+    dom.step(3)
+    K = args.tj_steps
+    res = {"workload": "3-D T-junction R0.5 L4 + branch R0.3 L1.2 at 60 deg, arbitrary rotation, dp 0.006, "
+                       "velocity inlet + 2 pressure outlets", "particles": dom.count(), "buffers": 3}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for tag, ph in (("restricted", _ffi.STEP_DEFAULT), ("full", _ffi.STEP_DEFAULT | _ffi.PHASE_FULL_CHECK)):
+        dom.step(2, ph)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        dom.step(K, ph)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[tag + "_ms_per_step"] = e0.elapsed_time(e1) / K
+        dom.use_graph(False)
+        dom.enable_phase_timing(True)
+        dom.step(args.phase_steps, ph)
+        t, nph = dom.phase_times()
+        dom.enable_phase_timing(False)
+        dom.use_graph(True)
+        res[tag + "_buffer_us_per_step"] = t["buffer"] / nph * 1e3
+    cand = [dom.candidate_count(k) for k in range(3)]
+    res["candidate_cells"] = sum(c for c, _ in cand)
+    res["candidate_particles"] = sum(p for _, p in cand)
+    inj, dels = dom.last_decisions()
+    res["injected_last_step"], res["deleted_last_step"] = len(inj), len(dels)
+    res["buffer_speedup_restricted_vs_full"] = res["full_buffer_us_per_step"] / res["restricted_buffer_us_per_step"]
+    res["particle_steps_per_s"] = res["particles"] / (res["restricted_ms_per_step"] / 1e3)
+    dom.close()
+    return res
 
 
 def run_reference(args):

@@ -413,6 +413,97 @@ def perturbed_state(case: Case, dv: float, drho: float, seed: int = 11):
     return vel, rho
 
 
+def random_rotation(rng) -> np.ndarray:
+    """A seeded proper rotation (QR of a Gaussian matrix, sign-fixed)."""
+    q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+    q = q @ np.diag(np.sign(np.diag(r)))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+def tjunction_case(*, dp=0.006, R=0.5, L=4.0, Rb=0.3, Lb=1.2, branch_deg=60.0, umax=1.0, c0=10.0, nu=1e-2,
+                   rho0=1000.0, h_over_dp=1.3, buffer_layers=4, seed=BASE_SEED + 4, developed=True,
+                   capacity_factor=1.15, name="cfg4_tjunction") -> Case:
+    """3-D T-junction: main pipe (R, L) with a branch (Rb, Lb from the main axis) leaving its
+    middle at ``branch_deg`` to the main axis; the assembly is given a seeded arbitrary rotation.
+    Velocity inlet (pipe profile, ``umax``) at the main pipe's start, pressure outlets (p = 0) at
+    the main pipe's end and the branch end.  With ``developed`` the main pipe starts on the
+    Poiseuille profile so that particles cross both main-pipe buffers from the first step.
+    """
+    rng = np.random.default_rng(seed)
+    wl_ = 3 * dp
+    ph = math.radians(branch_deg)
+    eb = np.array([math.cos(ph), math.sin(ph), 0.0])  # branch axis in the main pipe's frame
+    sb0 = 0.5 * L
+    m = int(math.ceil((R + wl_) / dp)) + 1
+    xs = (np.arange(-4, int(math.ceil(L / dp)) + 4) + 0.5) * dp
+    ys_max = sb0 * 0 + Lb * eb[1] + Rb + wl_
+    ys = (np.arange(-m, int(math.ceil(ys_max / dp)) + 1) + 0.5) * dp
+    zs = (np.arange(-m, m) + 0.5) * dp
+    fluid_l, wall_l = [], []
+    for x in xs:  # slab by slab keeps memory bounded
+        Y, Z = np.meshgrid(ys, zs, indexing="ij")
+        Y, Z = Y.ravel(), Z.ravel()
+        X = np.full_like(Y, x)
+        r_main = np.sqrt(Y * Y + Z * Z)
+        in_main = (X >= 0) & (X < L) & (r_main < R)
+        rel = np.stack([X - sb0, Y, Z], axis=1)
+        sb = rel @ eb
+        rb = np.linalg.norm(rel - sb[:, None] * eb[None, :], axis=1)
+        in_br = (sb >= 0) & (sb < Lb) & (rb < Rb)
+        fl = in_main | in_br
+        near_main = (X >= -wl_) & (X < L + wl_) & (r_main < R + wl_)
+        near_br = (sb >= 0) & (sb < Lb + wl_) & (rb < Rb + wl_)
+        wa = (near_main | near_br) & ~fl
+        # open ends: no wall in front of the three cross-sections
+        wa &= ~((X < 0) & (r_main < R))
+        wa &= ~((X >= L) & (r_main < R))
+        wa &= ~((sb >= Lb) & (rb < Rb))
+        pts = np.stack([X, Y, Z], axis=1)
+        fluid_l.append(pts[fl])
+        wall_l.append(pts[wa])
+    fluid_l = np.concatenate(fluid_l)
+    wall_l = np.concatenate(wall_l)
+    fluid_l = fluid_l + rng.uniform(-0.01 * dp, 0.01 * dp, fluid_l.shape)
+    Q = random_rotation(rng)  # local -> global: x_g = Q x_l
+    fluid = fluid_l @ Q.T
+    wall = wall_l @ Q.T
+    h = h_over_dp * dp
+    lo, hi = _grid_box([fluid, wall], margin=2.0 * (2.0 * h))
+    a = buffer_layers * dp
+    e_main = Q[:, 0]
+    e_br = Q @ eb
+    bufs = [
+        BufferSpec(origin=Q @ np.array([0.5 * a, 0.0, 0.0]), rotation=frame_3d(e_main, rng.uniform(0, 6.28)),
+                   extent=np.array([a, 2 * R, 2 * R]), bc=VELOCITY_INLET, umax=umax, half_width=R),
+        BufferSpec(origin=Q @ np.array([L - 0.5 * a, 0.0, 0.0]), rotation=frame_3d(e_main, rng.uniform(0, 6.28)),
+                   extent=np.array([a, 2 * R, 2 * R]), bc=PRESSURE_OUTLET, p_b=0.0),
+        BufferSpec(origin=Q @ (np.array([sb0, 0.0, 0.0]) + (Lb - 0.5 * a) * eb),
+                   rotation=frame_3d(e_br, rng.uniform(0, 6.28)), extent=np.array([a, 2 * Rb, 2 * Rb]),
+                   bc=PRESSURE_OUTLET, p_b=0.0),
+    ]
+    vel = np.zeros_like(fluid)
+    r2 = fluid_l[:, 1] ** 2 + fluid_l[:, 2] ** 2
+    in_main = (fluid_l[:, 0] >= 0) & (fluid_l[:, 0] < L) & (r2 < R * R)
+    if developed:
+        u = umax * np.clip(1.0 - r2 / (R * R), 0.0, None) * in_main
+    else:
+        u = umax * np.clip(1.0 - r2 / (R * R), 0.0, None) * (in_main & (fluid_l[:, 0] < a))
+    vel = u[:, None] * e_main[None, :]
+    dt = min(0.25 * h / (c0 + umax), 0.125 * h * h / nu)
+    n = fluid.shape[0]
+    return Case(name="%s_dp%g_n%d" % (name, dp, n), dim=3, lo=lo, hi=hi, dp=dp, h_over_dp=h_over_dp, rho0=rho0,
+                c0=c0, nu=nu, dt=dt, fluid_pos=fluid, fluid_vel=vel, fluid_rho=np.full(n, rho0), wall_pos=wall,
+                buffers=bufs, capacity=int(capacity_factor * n) + 8192, steps=500)
+
+
+def config4(dp=0.006) -> Case:
+    """3-D T-junction, main pipe R 0.5 x 4 m, branch R 0.3 x 1.2 m at 60 deg, arbitrary rotation,
+    one velocity inlet (Umax 1) and two pressure outlets; about 16 M fluid particles at dp 0.006."""
+    return tjunction_case(dp=dp)
+
+
 def star_case(*, seed, n_target, arms, width, name="star", umax=1.0, c0=10.0, nu=1e-2, rho0=1000.0,
               h_over_dp=1.3, buffer_layers=4, p_amp=500.0, p_freq=2.0, capacity_factor=1.6) -> Case:
     """2-D "star" channel: ``arms`` straight arms of width ``width`` leaving a central junction.

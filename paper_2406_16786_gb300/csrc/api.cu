@@ -229,15 +229,19 @@ sphbuf_status build_segments(sphbuf_domain* d) {
     d->seg_mem = nullptr;
   }
   const size_t nseg = segbuf.size();
-  const size_t bytes = (2 * nseg + nseg) * sizeof(int);
+  // [seg_range: 4 nseg words, 16-byte aligned][seg_lin: 2 nseg][seg_buf: nseg]; the ranges
+  // are written by every rebuild (the first one runs before the first step)
+  const size_t bytes = (4 * nseg + 2 * nseg + nseg) * sizeof(int);
   CK(cudaMalloc(&d->seg_mem, std::max<size_t>(bytes, 16)));
   int* p = static_cast<int*>(d->seg_mem);
+  CK(cudaMemset(p, 0, std::max<size_t>(bytes, 16)));
   if (nseg) {
-    CK(cudaMemcpy(p, seg.data(), 2 * nseg * sizeof(int), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(p + 2 * nseg, segbuf.data(), nseg * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p + 4 * nseg, seg.data(), 2 * nseg * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p + 6 * nseg, segbuf.data(), nseg * sizeof(int), cudaMemcpyHostToDevice));
   }
-  d->dev.seg_lin = p;
-  d->dev.seg_buf = p + 2 * nseg;
+  d->dev.seg_range = reinterpret_cast<uint4*>(p);
+  d->dev.seg_lin = p + 4 * nseg;
+  d->dev.seg_buf = p + 6 * nseg;
   d->dev.nseg = (int)nseg;
   d->seg_host = seg;
   d->segbuf_host = segbuf;
@@ -594,7 +598,6 @@ sphbuf_status sphbuf_write_particles(sphbuf_domain_t d, const int32_t* cell, con
   st.n_del = 0;
   st.next_id = next_id;
   st.status = 0;
-  st.done_blocks = 0;
   CK(cudaMemcpy(d->dev.st, &st, sizeof(StepState), cudaMemcpyHostToDevice));
   d->labels_given = label != nullptr;
   d->need_rebuild = true;
@@ -1022,8 +1025,10 @@ static sphbuf_status batch_build_maps(sphbuf_batch* b, int mult) {
           cnt = v.scan_tiles;
           break;
         case K_SCAN_TOP:
-        case K_FINALIZE:
           cnt = 1;
+          break;
+        case K_FINALIZE:
+          cnt = finalize_blocks(v);
           break;
         default:
           cnt = std::max(1, (int)std::lround(T * (double)std::max<uint64_t>(b->n0[q], 1) / total_n));

@@ -65,7 +65,6 @@ struct StepState {
   unsigned n_del;      // deletions of the current step
   unsigned next_id;
   unsigned n_occ;      // occupied cells of the current cell-linked list
-  unsigned done_blocks;  // blocks of the buffer kernel that finished their decisions
   unsigned long long step;
   int status;          // latched error code (sphbuf_status), 0 = OK
   unsigned long long escaped_total;
@@ -135,6 +134,31 @@ __device__ __forceinline__ bool move_fold(float& f, int& c, float delta, float c
     }
   }
   return isfinite(f);
+}
+
+// The cell part of X - O' in the contract's FP32 order: fl(fl(c - cO) cs) per axis.
+template <int D>
+__device__ __forceinline__ void cell_part(const BufDev& b, const int c[3], float cs, float cp[3]) {
+#pragma unroll
+  for (int x = 0; x < 3; ++x) cp[x] = x < D ? __fmul_rn(__int2float_rn(c[x] - b.cO[x]), cs) : 0.f;
+}
+
+// X' = R (X - O') rows [0, nrow) from the cell part cp and the offset f:
+// Delta = fl(cp + fl(f - fO)), X'_r = fl(fl(fl(R_r0 Delta_0) + fl(R_r1 Delta_1)) + fl(R_r2 Delta_2)).
+template <int D>
+__device__ __forceinline__ void local_from_part(const BufDev& b, const float cp[3], const float f[3], float X[3],
+                                                int nrow) {
+  float Dl[3];
+#pragma unroll
+  for (int x = 0; x < D; ++x) Dl[x] = __fadd_rn(cp[x], __fadd_rn(f[x], -b.fO[x]));
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    if (r >= D || r >= nrow) break;
+    float acc = __fmul_rn(b.R[r][0], Dl[0]);
+    acc = __fadd_rn(acc, __fmul_rn(b.R[r][1], Dl[1]));
+    if (D == 3) acc = __fadd_rn(acc, __fmul_rn(b.R[r][2], Dl[2]));
+    X[r] = acc;
+  }
 }
 
 // Local coordinates X' = R (X - O') in the contract's FP32 order, rows [0, nrow).

@@ -33,6 +33,7 @@ struct DomainDev {
   int nrelabel;
   const int* seg_lin;     // candidate cell segments: [lin0, lin1) pairs
   const int* seg_buf;     // buffer of each segment
+  uint4* seg_range;       // (cell_start[lin0], cell_start[lin1], lin0, buffer) of each segment
   int nseg;
   StepState* st;
   long long ncell_pad;
@@ -89,6 +90,7 @@ int launch_decide(const DomainDev& d, bool full_domain, cudaStream_t s);
 int launch_apply(const DomainDev& d, cudaStream_t s);
 // cells (kernels_cells.cu)
 int launch_rebuild(const DomainDev& d, bool count_step, cudaStream_t s);
+int finalize_blocks(const DomainDev& d);  // blocks of the finalize pass (candidate segments / 256)
 void launch_decode_positions(const DomainDev& d, double* pos_out, const double lo[3], double cs,
                              cudaStream_t s);
 cudaError_t cell_list_build(const int32_t* cell, const uint32_t* id, const uint8_t* label,

@@ -1,16 +1,17 @@
 // The arbitrary-positioned buffer (Sec. 3, Algorithms 1-3) on the GPU: one launch per step.
 //
-// decide: only the particles listed in the cells around each buffer's box are visited (four
-//   candidate cells per warp, eight lanes per cell; label, cell and offset are loaded
-//   together); each is transformed into the buffer's local frame (Eqs. (11), (15)) with the
-//   FP32 decision contract and compared on the normal axis only.  Crossings are compacted with
-//   a warp ballot and one atomic per warp into the injection / deletion lists.  The deciding
-//   thread also does the work that does not depend on the injection order: it records the
-//   parent's state (the duplicate's state), recycles the parent by -a u (Eqs. (16)-(17)),
-//   resets its density for pressure buffers (Eq. (22)), and marks deleted particles dead.
-// apply: the last block to finish (atomic ticket after a fence) ranks the injections by
-//   (buffer, parent id) with a bitonic sort in shared memory (a pairwise rank count for very
-//   long lists) and writes duplicate r at the tail of B with id next_id + r.
+// Only the particles listed in the cells around each buffer's box are visited (four candidate
+// cells per warp, eight lanes per cell, four particles per lane loaded before any is tested;
+// the cells' particle ranges come from the last rebuild).  Each is transformed into
+// the buffer's local frame (Eqs. (11), (15)) with the FP32 decision contract and compared on
+// the normal axis only.  Crossings are compacted with a warp ballot into per-block lists in
+// shared memory, and each block reserves its range of the step's global lists with one
+// atomic per list.  The deciding thread does everything that does not depend on the order
+// of the injections: it recycles the parent by -a u (Eqs. (16)-(17)), resets its density for
+// pressure buffers (Eq. (22)) and marks deleted particles dead; the block writes each
+// duplicate (the parent's state before recycling, label 0) at the tail of B.  The ids of the
+// duplicates follow the (buffer, parent id) order and are assigned by the first pass of the
+// rebuild (rank_injections, in apply.cuh), which needs every decision of the step.
 // The full-domain variant takes the same decisions over every particle and every buffer.
 #include "kernels.cuh"
 
@@ -20,82 +21,148 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kBufThreads = 256;
-constexpr int kSortCap = 2048;  // injections ranked by the in-block bitonic sort
+constexpr unsigned kStage = 128;  // decisions staged per block and list (more go straight out)
 
-// Warp-ballot compaction of one record per flagged lane into `list` (lanes may belong to
-// different buffers; each flagged lane also counts itself in its buffer's counter).
-__device__ __forceinline__ void emit(bool flag, const Decision& rec, Decision* list, unsigned* counter,
-                                     unsigned long long* per_buffer, unsigned cap, StepState* st) {
+// What the test of one particle of B needs (its id, velocity and density are read only when
+// it crossed a face).
+struct Cand {
+  uint8_t lab;
+  int cell;
+  float f[3];
+};
+
+template <int D>
+__device__ __forceinline__ void load_cand(const DomainDev& d, unsigned i, bool ok, Cand& p) {
+  p.lab = kDead;
+  p.cell = 0;
+#pragma unroll
+  for (int x = 0; x < 3; ++x) p.f[x] = 0.f;
+  if (!ok) return;
+  p.lab = d.B.label[i];
+  p.cell = d.B.cell[i];
+#pragma unroll
+  for (int x = 0; x < D; ++x) p.f[x] = d.B.f[x][i];
+}
+
+// Writes injection `slot` of the step: its record and its duplicate at B[n + slot] (id
+// assigned by the rebuild).
+template <int D>
+__device__ __forceinline__ void write_injection(const DomainDev& d, const Decision& e, unsigned slot, unsigned n) {
+  if (slot >= d.P.list_cap || (unsigned long long)n + slot >= d.P.capacity) {
+    latch(d.st, 2 /* SPHBUF_ERR_CAPACITY */);
+    return;
+  }
+  d.inj[slot] = e;
+  const unsigned dst = n + slot;
+  d.B.cell[dst] = e.cell;
+#pragma unroll
+  for (int x = 0; x < D; ++x) {
+    d.B.f[x][dst] = e.f[x];
+    d.B.v[x][dst] = e.v[x];
+  }
+  d.B.rho[dst] = e.rho;
+  d.B.id[dst] = kNoSlot;
+  d.B.label[dst] = 0;  // the duplicate is ordinary fluid (Algorithm 1)
+}
+
+__device__ __forceinline__ void write_deletion(const DomainDev& d, const Decision& e, unsigned slot) {
+  if (slot >= d.P.list_cap) {
+    latch(d.st, 2 /* SPHBUF_ERR_CAPACITY */);
+    return;
+  }
+  d.del[slot] = e;
+}
+
+// Per-block decision lists, plus the buffers' constants and this step's recycled density, in
+// shared memory.
+struct Staged {
+  Decision inj[kStage];
+  Decision del[kStage];
+  BufDev bufs[kMaxBuffers];
+  float rho_pb[kMaxBuffers];
+  unsigned ninj, ndel, base_inj, base_del, n, bad;
+};
+
+// Warp-ballot compaction of one record per flagged lane into the block's list; records
+// beyond the staging capacity are written to the global list directly.
+template <int D, bool INJ>
+__device__ __forceinline__ void stage(const DomainDev& d, Staged& sm, bool flag, const Decision& rec) {
   const unsigned m = __ballot_sync(kFull, flag);
   if (m == 0) return;
   const int lane = threadIdx.x & 31;
   unsigned base = 0;
-  if (lane == 0) base = atomicAdd(counter, (unsigned)__popc(m));
-  base = __shfl_sync(kFull, base, 0);
-  if (flag) {
-    atomicAdd(per_buffer, 1ull);
-    const unsigned r = base + __popc(m & ((1u << lane) - 1u));
-    if (r < cap)
-      list[r] = rec;
-    else
-      latch(st, 2 /* SPHBUF_ERR_CAPACITY */);
+  if (lane == __ffs(m) - 1) base = atomicAdd(INJ ? &sm.ninj : &sm.ndel, (unsigned)__popc(m));
+  base = __shfl_sync(kFull, base, __ffs(m) - 1);
+  if (!flag) return;
+  atomicAdd(INJ ? &d.st->injected[rec.k] : &d.st->deleted[rec.k], 1ull);
+  const unsigned r = base + __popc(m & ((1u << lane) - 1u));
+  if (r < kStage) {
+    (INJ ? sm.inj : sm.del)[r] = rec;
+  } else if (INJ) {
+    write_injection<D>(d, rec, atomicAdd(&d.st->n_inj, 1u), sm.n);
+  } else {
+    write_deletion(d, rec, atomicAdd(&d.st->n_del, 1u));
   }
 }
 
-// Algorithms 1-3 for particle i of B against buffer k; the warp emits the decisions.
+// Algorithms 1-3 for particle i of B (test state p) against buffer k; the warp stages the
+// decisions.  (lin_c, c_c, cp_c): a cell, its coordinates and its cell part for buffer k,
+// used when the particle is still in that cell (the cell it was sorted into).
 template <int D>
-__device__ __forceinline__ void decide_emit(const DomainDev& d, int k, unsigned i, bool valid) {
-  const BufDev& b = d.bufs[k];
+__device__ __forceinline__ void decide(const DomainDev& d, Staged& sm, int k, unsigned i, const Cand& p, int lin_c,
+                                       const int c_c[3], const float cp_c[3]) {
+  const BufDev& b = sm.bufs[k];
   const Grid& g = d.g;
   bool inj = false, del = false;
+  int c[3] = {c_c[0], c_c[1], c_c[2]};
+  const bool test = (b.kind == KIND_OUTFLOW) ? (p.lab != kDead) : (p.lab == (uint8_t)b.label);
+  if (test) {
+    float cp[3] = {cp_c[0], cp_c[1], cp_c[2]};
+    if (p.cell != lin_c) {
+      cell_coords(p.cell, g, c);
+      cell_part<D>(b, c, g.cs, cp);
+    }
+    float X[3];
+    if (b.kind == KIND_OUTFLOW) {
+      // Algorithm 2: candidates within one cell of the box, deleted once X' > a/2
+      local_from_part<D>(b, cp, p.f, X, D);
+      bool cand = fabsf(X[0]) < b.da && fabsf(X[1]) < b.db;
+      if (D == 3) cand = cand && fabsf(X[2]) < b.dc;
+      del = cand && X[0] > b.ha;
+    } else {
+      // Algorithms 1 and 3: buffer particles crossing X' = a/2 generate; Algorithm 3 deletes
+      // those crossing X' = -a/2
+      local_from_part<D>(b, cp, p.f, X, 1);
+      inj = X[0] > b.ha;
+      if (b.kind == KIND_BIDIR) del = X[0] < -b.ha;
+    }
+  }
+  if (!__any_sync(kFull, inj || del)) return;
   Decision rec;
   rec.k = (unsigned)k;
   rec.idx = i;
   rec.id = 0;
-  rec.cell = 0;
+  rec.cell = p.cell;
   rec.rho = 0.f;
 #pragma unroll
-  for (int x = 0; x < 3; ++x) rec.f[x] = rec.v[x] = 0.f;
-  int c[3] = {0, 0, 0};
-  if (valid) {
-    // independent loads, issued together
-    const uint8_t lab = d.B.label[i];
-    rec.cell = d.B.cell[i];
-#pragma unroll
-    for (int x = 0; x < 3; ++x) rec.f[x] = x < D ? d.B.f[x][i] : 0.f;
-    rec.id = d.B.id[i];
-    const bool test = (b.kind == KIND_OUTFLOW) ? (lab != kDead) : (lab == (uint8_t)b.label);
-    if (test) {
-      cell_coords(rec.cell, g, c);
-      float X[3];
-      if (b.kind == KIND_OUTFLOW) {
-        // Algorithm 2: candidates within one cell of the box, deleted once X' > a/2
-        local_coords<D>(b, c, rec.f, g.cs, X, D);
-        bool cand = fabsf(X[0]) < b.da && fabsf(X[1]) < b.db;
-        if (D == 3) cand = cand && fabsf(X[2]) < b.dc;
-        del = cand && X[0] > b.ha;
-      } else {
-        // Algorithms 1 and 3: buffer particles crossing X' = a/2 generate; Algorithm 3 deletes
-        // those crossing X' = -a/2
-        local_coords<D>(b, c, rec.f, g.cs, X, 1);
-        inj = X[0] > b.ha;
-        if (b.kind == KIND_BIDIR) del = X[0] < -b.ha;
-      }
-    }
+  for (int x = 0; x < 3; ++x) {
+    rec.f[x] = p.f[x];
+    rec.v[x] = 0.f;
   }
+  if (inj || del) rec.id = d.B.id[i];
   if (inj) {
 #pragma unroll
-    for (int x = 0; x < 3; ++x) rec.v[x] = x < D ? d.B.v[x][i] : 0.f;
+    for (int x = 0; x < D; ++x) rec.v[x] = d.B.v[x][i];
     rec.rho = d.B.rho[i];
   }
-  emit(inj, rec, d.inj, &d.st->n_inj, &d.st->injected[k], d.P.list_cap, d.st);
+  stage<D, true>(d, sm, inj, rec);
   if (inj) {
-    // recycle the parent: r' - [a, 0, 0]^T mapped back, i.e. r - a u (same thread, after the
-    // record captured the duplicate's state)
+    // recycle the parent: r' - [a, 0, 0]^T mapped back, i.e. r - a u (after the record
+    // captured the duplicate's state)
     bool ok = true;
 #pragma unroll
     for (int x = 0; x < D; ++x) {
-      float fx = rec.f[x];
+      float fx = p.f[x];
       ok &= move_fold(fx, c[x], b.shift[x], g.cs);
       d.B.f[x][i] = fx;
     }
@@ -106,134 +173,90 @@ __device__ __forceinline__ void decide_emit(const DomainDev& d, int k, unsigned 
       d.B.label[i] = kDead;
       atomicAdd(&d.st->escaped_total, 1ull);
     }
-    if (!b.vel_bc) d.B.rho[i] = d.st->rho_pb[k];  // Eq. (22)
+    if (!b.vel_bc) d.B.rho[i] = sm.rho_pb[k];  // Eq. (22)
   }
   if (del) d.B.label[i] = kDead;
-  emit(del, rec, d.del, &d.st->n_del, &d.st->deleted[k], d.P.list_cap, d.st);
+  stage<D, false>(d, sm, del, rec);
 }
 
-// Writes duplicate number r from its record.
-template <int D>
-__device__ __forceinline__ void write_duplicate(const DomainDev& d, const Decision* e, unsigned rank, unsigned n,
-                                                unsigned next_id) {
-  const unsigned dst = n + rank;
-  const unsigned child = next_id + rank;
-  d.B.cell[dst] = __ldcg(&e->cell);
-#pragma unroll
-  for (int x = 0; x < D; ++x) {
-    d.B.f[x][dst] = __ldcg(&e->f[x]);
-    d.B.v[x][dst] = __ldcg(&e->v[x]);
-  }
-  d.B.rho[dst] = __ldcg(&e->rho);
-  d.B.id[dst] = child;
-  d.B.label[dst] = 0;  // the duplicate is ordinary fluid (Algorithm 1)
-  d.inj_sorted[rank] = InjRecord{__ldcg(&e->k), __ldcg(&e->id), child};
-}
-
-__device__ __forceinline__ unsigned long long inj_key(unsigned k, unsigned id) {
-  return ((unsigned long long)k << 32) | id;
-}
-
-// Ranks the step's injections and writes the duplicates; run by one block.
-template <int D>
-__device__ void apply_all(const DomainDev& d, unsigned long long* keys, unsigned* idx) {
-  StepState* st = d.st;
-  const unsigned n_inj = min(__ldcg(&st->n_inj), d.P.list_cap);
-  const unsigned n = st->n;
-  const unsigned next_id = st->next_id;
-  if (n_inj == 0 || __ldcg(&st->status)) return;
-  if ((unsigned long long)n + n_inj > d.P.capacity) {
-    if (threadIdx.x == 0) latch(st, 2 /* SPHBUF_ERR_CAPACITY */);
-    return;
-  }
-  const Decision* inj = d.inj;
-  if (n_inj <= (unsigned)kSortCap) {
-    unsigned p2 = 1;
-    while (p2 < n_inj) p2 <<= 1;
-    for (unsigned e = threadIdx.x; e < p2; e += blockDim.x) {
-      keys[e] = e < n_inj ? inj_key(__ldcg(&inj[e].k), __ldcg(&inj[e].id)) : ~0ull;
-      idx[e] = e;
-    }
-    // bitonic sort of (key, entry) pairs, ascending keys (keys are distinct)
-    for (unsigned size = 2; size <= p2; size <<= 1) {
-      for (unsigned stride = size >> 1; stride > 0; stride >>= 1) {
-        __syncthreads();
-        for (unsigned t = threadIdx.x; t < (p2 >> 1); t += blockDim.x) {
-          const unsigned lo = 2 * t - (t & (stride - 1));
-          const unsigned hi = lo + stride;
-          const bool up = (lo & size) == 0;
-          const unsigned long long a = keys[lo], b = keys[hi];
-          if ((a > b) == up) {
-            keys[lo] = b;
-            keys[hi] = a;
-            const unsigned ti = idx[lo];
-            idx[lo] = idx[hi];
-            idx[hi] = ti;
-          }
-        }
-      }
-    }
-    __syncthreads();
-    for (unsigned r = threadIdx.x; r < n_inj; r += blockDim.x) write_duplicate<D>(d, inj + idx[r], r, n, next_id);
-  } else {
-    // long lists: rank = number of smaller keys
-    for (unsigned e = threadIdx.x; e < n_inj; e += blockDim.x) {
-      const unsigned long long key = inj_key(__ldcg(&inj[e].k), __ldcg(&inj[e].id));
-      unsigned rank = 0;
-      for (unsigned q = 0; q < n_inj; ++q) rank += inj_key(__ldcg(&inj[q].k), __ldcg(&inj[q].id)) < key;
-      write_duplicate<D>(d, inj + e, rank, n, next_id);
-    }
-  }
-}
-
-// Decisions (restricted to candidate cells, or over all particles), then the duplicates by
-// the last block to finish.
+// Decisions (restricted to candidate cells, or over all particles), then the block's lists
+// and duplicates.
 template <int D, bool FULL>
 __device__ __forceinline__ void buffer_body(const DomainDev& d, unsigned bid, unsigned nblk) {
-  __shared__ unsigned long long s_keys[kSortCap];
-  __shared__ unsigned s_idx[kSortCap];
-  __shared__ int s_last;
+  __shared__ Staged sm;
   const int lane = threadIdx.x & 31;
   const unsigned warp = (bid * blockDim.x + threadIdx.x) >> 5;
   const unsigned nwarps = (nblk * blockDim.x) >> 5;
-  // every block takes part in the completion count, even after an error was latched
-  if (d.st->status) {
-  } else if (FULL) {
-    const unsigned n = d.st->n;
+  // four candidate cells per warp, eight lanes per cell; the first cells' particle ranges are
+  // requested before the block copies the buffers' constants
+  const unsigned grp = lane >> 3, gl = lane & 7;
+  const unsigned nseg = FULL ? 0u : (unsigned)d.nseg;
+  unsigned s0 = warp * 4;
+  uint4 r = make_uint4(0, 0, 0, 0);  // (first particle, end, cell, buffer)
+  if (s0 + grp < nseg) r = d.seg_range[s0 + grp];
+  if (threadIdx.x == 0) {
+    sm.ninj = sm.ndel = 0;
+    sm.n = d.st->n;
+    sm.bad = d.st->status != 0;
+  }
+  {
+    const int words = d.nbuf * (int)(sizeof(BufDev) / sizeof(int));
+    const int* src = reinterpret_cast<const int*>(d.bufs);
+    int* dst = reinterpret_cast<int*>(sm.bufs);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+    if (threadIdx.x < (unsigned)d.nbuf) sm.rho_pb[threadIdx.x] = d.st->rho_pb[threadIdx.x];
+  }
+  __syncthreads();
+  if (sm.bad) return;
+  if (FULL) {
+    const unsigned n = sm.n;
     for (unsigned base = warp * 32; base < n; base += nwarps * 32) {
       const unsigned i = base + lane;
-      for (int k = 0; k < d.nbuf; ++k) decide_emit<D>(d, k, i, i < n);
+      Cand p;
+      load_cand<D>(d, i, i < n, p);
+      const int none[3] = {0, 0, 0};
+      const float zero[3] = {0.f, 0.f, 0.f};
+      for (int kk = 0; kk < d.nbuf; ++kk) decide<D>(d, sm, kk, i, p, -1, none, zero);
     }
   } else {
-    // four candidate cells per warp, eight lanes per cell
-    const unsigned grp = lane >> 3, gl = lane & 7;
-    const unsigned nseg = (unsigned)d.nseg;
-    for (unsigned s0 = warp * 4; s0 < nseg; s0 += nwarps * 4) {
-      const unsigned s = s0 + grp;
-      unsigned j0 = 0, j1 = 0;
-      int k = 0;
-      if (s < nseg) {
-        const int lin0 = d.seg_lin[2 * s], lin1 = d.seg_lin[2 * s + 1];
-        k = d.seg_buf[s];
-        j0 = d.cell_start[lin0];
-        j1 = d.cell_start[lin1];
+    // four particles per lane are loaded before any is tested (cells of up to 32 particles
+    // take one pass)
+    while (s0 < nseg) {
+      const unsigned j0 = r.x, j1 = r.y;
+      const int lin = (int)r.z, kc = (int)r.w;
+      // next cells' ranges, requested before this group is tested
+      const unsigned s1 = s0 + nwarps * 4;
+      r = make_uint4(0, 0, 0, 0);
+      if (s1 + grp < nseg) r = d.seg_range[s1 + grp];
+      // the cell's coordinates and cell part, shared by its particles that stayed in it
+      int cc[3];
+      float cp[3];
+      cell_coords(lin, d.g, cc);
+      cell_part<D>(sm.bufs[kc], cc, d.g.cs, cp);
+      const unsigned passes = __reduce_max_sync(kFull, (j1 - j0 + 31) >> 5);
+      for (unsigned it = 0; it < passes; ++it) {
+        Cand p[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const unsigned i = j0 + it * 32 + q * 8 + gl;
+          load_cand<D>(d, i, i < j1, p[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) decide<D>(d, sm, kc, j0 + it * 32 + q * 8 + gl, p[q], lin, cc, cp);
       }
-      const unsigned iters = __reduce_max_sync(kFull, (j1 - j0 + 7) >> 3);
-      for (unsigned it = 0; it < iters; ++it) {
-        const unsigned i = j0 + it * 8 + gl;
-        decide_emit<D>(d, k, i, i < j1);
-      }
+      s0 = s1;
     }
   }
-  // the last block to finish writes the step's duplicates
-  __threadfence();
+  // one reservation per block and list, then the block writes its records and duplicates
   __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(&d.st->done_blocks, 1u) == nblk - 1;
+  const unsigned ni = min(sm.ninj, kStage), nd = min(sm.ndel, kStage);
+  if (threadIdx.x == 0) {
+    if (ni) sm.base_inj = atomicAdd(&d.st->n_inj, ni);
+    if (nd) sm.base_del = atomicAdd(&d.st->n_del, nd);
+  }
   __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  apply_all<D>(d, s_keys, s_idx);
-  if (threadIdx.x == 0) d.st->done_blocks = 0;
+  for (unsigned e = threadIdx.x; e < ni; e += blockDim.x) write_injection<D>(d, sm.inj[e], sm.base_inj + e, sm.n);
+  for (unsigned e = threadIdx.x; e < nd; e += blockDim.x) write_deletion(d, sm.del[e], sm.base_del + e);
 }
 
 template <int D, bool FULL>
@@ -268,8 +291,8 @@ __global__ void __launch_bounds__(256) k_identify(DomainDev d) {
   }
 }
 
-// Blocks of k_buffer resident at once (one wave: the last block's apply starts as soon as the
-// decisions end).
+// Blocks of k_buffer resident at once (at most one wave: every block reserves its list ranges
+// as soon as its own decisions end).
 template <typename K>
 int one_wave(const DomainDev& d, K kernel) {
   int per_sm = 0;
@@ -313,7 +336,7 @@ int launch_decide(const DomainDev& d, bool full_domain, cudaStream_t s) {
   return 1;
 }
 
-int launch_apply(const DomainDev&, cudaStream_t) { return 0; }  // applied inside k_buffer
+int launch_apply(const DomainDev&, cudaStream_t) { return 0; }  // ids assigned by the rebuild
 
 int launch_batch_buffer(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s) {
   if (k == K_BUFFER) {

@@ -1,16 +1,19 @@
 // Cell-linked list rebuild (the end of each step, Sec. 3.1) as a counting sort, fused with the
 // relabelling of outflow and bidirectional buffers (Algorithms 2-3, after the rebuild).
 //
-//   hist    slot_i = atomicAdd(count[cell_i], 1) for every live particle of B
+//   hist    slot_i = atomicAdd(count[cell_i], 1) for every live particle of B (the first
+//           threads name the step's duplicates first, see apply.cuh)
 //   scan    cell_start = exclusive prefix sum of count (3 passes over tiles of 4096 cells;
 //           count is re-zeroed on the way)
 //   keys    tmp_id[cell_start[cell_i] + slot_i] = id_i  (the cell's ids, in arbitrary order)
 //   scatter rank_i = #{ids of the same cell smaller than id_i}; A[cell_start + rank] = B[i]
 //           with the relabel test applied on the way
+//   finalize particle count, next id, and the particle ranges of the buffers' candidate cells
 // The result is sorted by (cell, id) whatever order the atomics took, so it is
 // deterministic and identical to a plain sort.
 #include <mutex>
 
+#include "apply.cuh"
 #include "kernels.cuh"
 
 namespace sphbuf {
@@ -243,6 +246,7 @@ __device__ __forceinline__ void scan_down_occ_body(unsigned* __restrict__ cnt, c
 
 __device__ __forceinline__ void hist_body(const DomainDev& d, unsigned bid, unsigned nblk) {
   if (d.st->status) return;
+  rank_injections(d, bid, nblk);
   const unsigned n = d.st->n + d.st->n_inj;
   for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
     if (d.B.label[i] == kDead)
@@ -310,12 +314,20 @@ __device__ __forceinline__ void scatter_body(const DomainDev& d, unsigned bid, u
   }
 }
 
-__device__ __forceinline__ void finalize_body(const DomainDev& d, int count_step) {
+__device__ __forceinline__ void finalize_body(const DomainDev& d, int count_step, unsigned bid, unsigned nblk) {
   StepState* st = d.st;
   if (st->status) return;
-  st->n = d.cell_start[d.g.ncell];
-  st->next_id += min(st->n_inj, d.P.list_cap);
-  if (count_step) st->step += 1;
+  if (bid == 0 && threadIdx.x == 0) {
+    st->n = d.cell_start[d.g.ncell];
+    st->next_id += min(st->n_inj, d.P.list_cap);
+    if (count_step) st->step += 1;
+  }
+  // (first particle, end, cell, buffer) of the candidate cell segments
+  for (unsigned s = bid * blockDim.x + threadIdx.x; s < (unsigned)d.nseg; s += nblk * blockDim.x) {
+    const int lin0 = d.seg_lin[2 * s];
+    d.seg_range[s] = make_uint4(d.cell_start[lin0], d.cell_start[d.seg_lin[2 * s + 1]], (unsigned)lin0,
+                                (unsigned)d.seg_buf[s]);
+  }
 }
 
 // ---- single-domain kernels
@@ -337,7 +349,9 @@ template <int D>
 __global__ void __launch_bounds__(256) k_scatter(DomainDev d) {
   scatter_body<D>(d, blockIdx.x, gridDim.x);
 }
-__global__ void k_finalize(DomainDev d, int count_step) { finalize_body(d, count_step); }
+__global__ void __launch_bounds__(256) k_finalize(DomainDev d, int count_step) {
+  finalize_body(d, count_step, blockIdx.x, gridDim.x);
+}
 
 // ---- batched twins (block -> (domain, local block, blocks of the domain))
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce_occ_batch(BatchDev b) {
@@ -377,7 +391,10 @@ __global__ void __launch_bounds__(256) k_scatter_batch(BatchDev b) {
   load_domain(sd, b.doms + m.x);
   scatter_body<D>(sd, (unsigned)m.y, (unsigned)m.z);
 }
-__global__ void k_finalize_batch(BatchDev b) { finalize_body(b.doms[b.map[blockIdx.x].x], 1); }
+__global__ void __launch_bounds__(256) k_finalize_batch(BatchDev b) {
+  const int4 m = b.map[blockIdx.x];
+  finalize_body(b.doms[m.x], 1, (unsigned)m.y, (unsigned)m.z);
+}
 
 __global__ void k_decode(DomainDev d, double* out, double lo0, double lo1, double lo2, double cs) {
   const unsigned n = d.st->n;
@@ -428,6 +445,8 @@ __global__ void k_order_raw(const int32_t* cell, const uint32_t* id, unsigned n,
 
 }  // namespace
 
+int finalize_blocks(const DomainDev& d) { return d.nseg > 256 ? (d.nseg + 255) / 256 : 1; }
+
 int launch_rebuild(const DomainDev& d, bool count_step, cudaStream_t s) {
   const int blocks = d.sm_count * 8;
   k_hist<<<blocks, 256, 0, s>>>(d);
@@ -439,7 +458,7 @@ int launch_rebuild(const DomainDev& d, bool count_step, cudaStream_t s) {
     k_scatter<2><<<blocks, 256, 0, s>>>(d);
   else
     k_scatter<3><<<blocks, 256, 0, s>>>(d);
-  k_finalize<<<1, 1, 0, s>>>(d, count_step ? 1 : 0);
+  k_finalize<<<finalize_blocks(d), 256, 0, s>>>(d, count_step ? 1 : 0);
   return 7;
 }
 
@@ -467,7 +486,7 @@ int launch_batch_cells(Kern k, int dim, const BatchDev& b, int nblocks, cudaStre
         k_scatter_batch<3><<<nblocks, 256, 0, s>>>(b);
       return 1;
     case K_FINALIZE:
-      k_finalize_batch<<<nblocks, 1, 0, s>>>(b);
+      k_finalize_batch<<<nblocks, 256, 0, s>>>(b);
       return 1;
     default:
       return 0;
@@ -478,8 +497,6 @@ int batch_threads(Kern k) {
   switch (k) {
     case K_SCAN_TOP:
       return 1024;
-    case K_FINALIZE:
-      return 1;
     default:
       return 256;
   }

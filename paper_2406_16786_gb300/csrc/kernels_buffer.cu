@@ -190,10 +190,12 @@ __device__ __forceinline__ void buffer_body(const DomainDev& d, unsigned bid, un
   // four candidate cells per warp, eight lanes per cell; the first cells' particle ranges are
   // requested before the block copies the buffers' constants
   const unsigned grp = lane >> 3, gl = lane & 7;
-  const unsigned nseg = FULL ? 0u : (unsigned)d.nseg;
+  const unsigned nseg = (unsigned)d.nseg;
   unsigned s0 = warp * 4;
   uint4 r = make_uint4(0, 0, 0, 0);  // (first particle, end, cell, buffer)
-  if (s0 + grp < nseg) r = d.seg_range[s0 + grp];
+  if constexpr (!FULL) {
+    if (s0 + grp < nseg) r = d.seg_range[s0 + grp];
+  }
   if (threadIdx.x == 0) {
     sm.ninj = sm.ndel = 0;
     sm.n = d.st->n;
@@ -208,7 +210,7 @@ __device__ __forceinline__ void buffer_body(const DomainDev& d, unsigned bid, un
   }
   __syncthreads();
   if (sm.bad) return;
-  if (FULL) {
+  if constexpr (FULL) {
     const unsigned n = sm.n;
     for (unsigned base = warp * 32; base < n; base += nwarps * 32) {
       const unsigned i = base + lane;

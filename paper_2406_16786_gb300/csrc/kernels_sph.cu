@@ -218,8 +218,9 @@ __device__ void force_one(const DomainDev& d, unsigned i) {
 }
 
 // ---------------------------------------------------------------- neighbour lists
-// Packed neighbour: index j (25 bits) | row (4 bits, from bit 27) | wall (1 bit, bit 31);
-// row = (dz + 1) * 3 + (dy + 1) in 3-D, dy + 1 in 2-D.  The x-cell of j is pos4[j].w.
+// Packed neighbour: index j (25 bits) | dy + 1 (2 bits, from bit 25) | dz + 1 (2 bits, from
+// bit 27) | wall (1 bit, bit 31); (dy, dz) is the row of j's cell relative to the particle's.
+// The x-cell of j is pos4[j].w.
 
 // Unpacks one entry of the particle at (cell x cxf, offset fi) and calls fn(wall, j, rx, ry, rz).
 template <int D, typename Fn>
@@ -227,10 +228,9 @@ __device__ __forceinline__ void visit_entry(const DomainDev& d, unsigned ent, fl
                                             Fn&& fn) {
   const float cs = d.g.cs;
   const unsigned j = ent & 0x1FFFFFFu;
-  const int row = (int)((ent >> 27) & 15u);
   const int wall = (int)(ent >> 31);
-  const int dy = (D == 3) ? row % 3 - 1 : row - 1;
-  const int dz = (D == 3) ? row / 3 - 1 : 0;
+  const int dy = (int)((ent >> 25) & 3u) - 1;
+  const int dz = (D == 3) ? (int)((ent >> 27) & 3u) - 1 : 0;
   const float4 p = __ldg((wall ? d.wpos4 : d.pos4) + j);
   const float rx = fi[0] - p.x - (p.w - cxf) * cs;
   const float ry = fi[1] - (float)dy * cs - p.y;
@@ -252,9 +252,26 @@ __device__ __forceinline__ void for_each_listed(const DomainDev& d, unsigned i, 
   }
 }
 
-// Neighbour-list pass: tests every candidate once (one 16-byte load each) and appends the
-// in-range ones to the particle's list (contiguous per particle, 16-byte stores of 4 entries,
-// branch-free appends).
+// One candidate of the neighbour-list pass: appends j to the particle's list when within 2h.
+// The last four entries are held in q0..q3 (oldest first) and stored 16 bytes at a time.
+struct ListTail {
+  unsigned q0, q1, q2, q3;
+  int cnt;
+};
+
+__device__ __forceinline__ void list_append(ListTail& t, bool in, unsigned ent, uint4* lst, int cap) {
+  t.q0 = in ? t.q1 : t.q0;
+  t.q1 = in ? t.q2 : t.q1;
+  t.q2 = in ? t.q3 : t.q2;
+  t.q3 = in ? ent : t.q3;
+  t.cnt += in;
+  if (in && (t.cnt & 3) == 0 && t.cnt <= cap) lst[(t.cnt >> 2) - 1] = make_uint4(t.q0, t.q1, t.q2, t.q3);
+}
+
+// Neighbour-list pass: tests every candidate of the 3^d cells once (one 16-byte load each)
+// and appends the in-range ones to the particle's list (contiguous per particle, 16-byte
+// stores of 4 entries, branch-free appends).  (Skipping rows and end cells that cannot hold
+// a neighbour, per particle, was slower: the lanes of a warp rarely agree on the skip.)
 template <int D>
 __device__ __forceinline__ void neighbours_body(const DomainDev& d, unsigned bid, unsigned nblk) {
   if (bid == 0 && threadIdx.x == 0) begin_step(d);
@@ -270,9 +287,7 @@ __device__ __forceinline__ void neighbours_body(const DomainDev& d, unsigned bid
     const float4 pi = d.pos4[i];
     const float cxf = pi.w;
     uint4* lst = reinterpret_cast<uint4*>(d.nb + (size_t)i * cap);
-    unsigned b0 = 0, b1 = 0, b2 = 0, b3 = 0;
-    int cnt = 0;
-    const int x0 = max(c[0] - 1, 0), x1 = min(c[0] + 1, g.nx - 1);
+    ListTail t{0u, 0u, 0u, 0u, 0};
 #pragma unroll 1
     for (int wall = 0; wall < 2; ++wall) {
       const unsigned* start = wall ? d.W.start : d.cell_start;
@@ -285,34 +300,29 @@ __device__ __forceinline__ void neighbours_body(const DomainDev& d, unsigned bid
         for (int dy = -1; dy <= 1; ++dy) {
           const int y = c[1] + dy;
           if (y < 0 || y >= g.ny) continue;
+          const int x0 = max(c[0] - 1, 0), x1 = min(c[0] + 1, g.nx - 1);
           const int rb = (z * g.ny + y) * g.nx;
-          const unsigned tag = ((unsigned)((D == 3) ? (dz + 1) * 3 + (dy + 1) : dy + 1) << 27) |
-                               ((unsigned)wall << 31);
-          const float ox = pi.x + cxf * cs;  // r_i.x relative to the grid row origin
+          const unsigned tag = ((unsigned)(dy + 1) << 25) | ((unsigned)(dz + 1) << 27) | ((unsigned)wall << 31);
           const float oy = pi.y - (float)dy * cs;
           const float oz = (D == 3) ? pi.z - (float)dz * cs : 0.f;
           const unsigned j1 = __ldg(start + rb + x1 + 1);
-          for (unsigned j = __ldg(start + rb + x0); j < j1; ++j) {
+          unsigned j = __ldg(start + rb + x0);
+          for (; j < j1; ++j) {
             const float4 p = __ldg(P4 + j);
-            const float rx = ox - (p.x + p.w * cs);
+            const float rx = (pi.x - p.x) - (p.w - cxf) * cs;
             const float ry = oy - p.y;
             const float rz = (D == 3) ? oz - p.z : 0.f;
             const float r2 = rx * rx + ry * ry + rz * rz;
-            const bool in = r2 < two_h_sq && r2 > 0.f;
-            const unsigned ent = j | tag;
-            const int slot = cnt & 3;
-            b0 = (in && slot == 0) ? ent : b0;
-            b1 = (in && slot == 1) ? ent : b1;
-            b2 = (in && slot == 2) ? ent : b2;
-            b3 = (in && slot == 3) ? ent : b3;
-            if (in && slot == 3 && cnt < cap) lst[cnt >> 2] = make_uint4(b0, b1, b2, b3);
-            cnt += in;
+            list_append(t, r2 < two_h_sq && r2 > 0.f, j | tag, lst, cap);
           }
         }
       }
     }
-    if ((cnt & 3) && cnt < cap) lst[cnt >> 2] = make_uint4(b0, b1, b2, b3);
-    d.nb_cnt[i] = (unsigned)cnt;
+    // the last (cnt mod 4) entries are q(4 - r) .. q3
+    const int r = t.cnt & 3;
+    if (r && t.cnt < cap)
+      lst[t.cnt >> 2] = make_uint4(r == 1 ? t.q3 : (r == 2 ? t.q2 : t.q1), r == 2 ? t.q3 : t.q2, t.q3, 0u);
+    d.nb_cnt[i] = (unsigned)t.cnt;
   }
 }
 
@@ -432,9 +442,9 @@ __device__ __forceinline__ void drift_body(const DomainDev& d, unsigned bid, uns
     BODY<D>(sd, (unsigned)m.y, (unsigned)m.z);                                                 \
   }
 
-SPHBUF_PAIR(k_neighbours, neighbours_body, (kThreads, 4))
-SPHBUF_PAIR(k_density, density_body, (kThreads, 3))
-SPHBUF_PAIR(k_force, force_body, (kThreads, 3))
+SPHBUF_PAIR(k_neighbours, neighbours_body, (kThreads, 5))
+SPHBUF_PAIR(k_density, density_body, (kThreads, 5))
+SPHBUF_PAIR(k_force, force_body, (kThreads, 4))
 SPHBUF_PAIR(k_drift, drift_body, (kThreads))
 #undef SPHBUF_PAIR
 

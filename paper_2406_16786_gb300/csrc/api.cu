@@ -432,7 +432,8 @@ sphbuf_status sphbuf_create_domain(const sphbuf_domain_desc* desc, void* cuda_st
     A(dalloc(d, &p->id, C));
     A(dalloc(d, &p->label, C));
   }
-  A(dalloc(d, &v.rho_new, C));
+  A(dalloc(d, &v.vr4, C));
+  A(dalloc(d, &v.deferred, C));
   // neighbour lists of the density pass, reused by the force pass (~80 neighbours in 3-D and
   // ~20 in 2-D at h = 1.3 dp on the lattice; headroom for compression)
   v.nb_cap = D == 3 ? 128 : 48;
@@ -1055,6 +1056,7 @@ static int batch_launch(sphbuf_batch* b, Kern k) {
   switch (k) {
     case K_NEIGHBOURS:
     case K_DENSITY:
+    case K_DENSITY_DEFER:
     case K_FORCE:
     case K_DRIFT:
       return launch_batch_sph(k, b->dim, bd, n, b->stream);
@@ -1075,6 +1077,7 @@ static int batch_enqueue_step(sphbuf_batch* b, unsigned phases, bool timed) {
     k += batch_launch(b, K_NEIGHBOURS);
     if (timed) cudaEventRecord(b->ev[1], s);
     k += batch_launch(b, K_DENSITY);
+    k += batch_launch(b, K_DENSITY_DEFER);
     if (timed) cudaEventRecord(b->ev[2], s);
     k += batch_launch(b, K_FORCE);
   } else {

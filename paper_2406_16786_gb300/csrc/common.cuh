@@ -65,6 +65,7 @@ struct StepState {
   unsigned n_del;      // deletions of the current step
   unsigned next_id;
   unsigned n_occ;      // occupied cells of the current cell-linked list
+  unsigned n_defer;    // particles deferred by the fluid density pass this step
   unsigned long long step;
   int status;          // latched error code (sphbuf_status), 0 = OK
   unsigned long long escaped_total;

@@ -17,7 +17,8 @@ struct DomainDev {
   unsigned* occ_list;     // occupied cells in increasing order (st->n_occ entries)
   unsigned* slot;         // per-particle slot from the histogram, capacity
   unsigned* tmp_id;       // ids scattered to their cell's range, capacity
-  float* rho_new;         // density pass output, capacity
+  float4* vr4;            // density pass output (vx, vy, vz, new rho) in A order, capacity
+  unsigned* deferred;     // particles left by the fluid density pass (buffer or overflowed list)
   float4* pos4;           // A-order copies for the neighbour passes: (fx, fy, fz, cell x)
   float4* vel4;           //   and (vx, vy, vz, rho); written by the rebuild scatter
   const float4* wpos4;    // walls: (fx, fy, fz, cell x)
@@ -51,6 +52,7 @@ struct BatchDev {
 enum Kern : int {
   K_NEIGHBOURS,
   K_DENSITY,
+  K_DENSITY_DEFER,
   K_FORCE,
   K_DRIFT,
   K_BUFFER,
@@ -81,7 +83,7 @@ int batch_threads(Kern k);  // threads per block of each batched kernel
 
 // sph (kernels_sph.cu)
 int launch_neighbours(const DomainDev& d, cudaStream_t s);  // starts the step (step constants)
-int launch_density(const DomainDev& d, cudaStream_t s);
+int launch_density(const DomainDev& d, cudaStream_t s);  // two kernels: fluid, then deferred
 int launch_force(const DomainDev& d, cudaStream_t s);
 int launch_drift(const DomainDev& d, cudaStream_t s);
 // buffer (kernels_buffer.cu)

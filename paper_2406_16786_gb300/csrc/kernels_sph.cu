@@ -28,6 +28,7 @@ __device__ __forceinline__ void begin_step(const DomainDev& d) {
   StepState* st = d.st;
   st->n_inj = 0;
   st->n_del = 0;
+  st->n_defer = 0;
   const double t = (double)st->step * d.P.dt_d;
   for (int k = 0; k < d.nbuf; ++k) {
     const BufDev& b = d.bufs[k];
@@ -196,7 +197,7 @@ __device__ void force_one(const DomainDev& d, unsigned i) {
   const float fi[3] = {d.A.f[0][i], d.A.f[1][i], D == 3 ? d.A.f[2][i] : 0.f};
   const float vi[3] = {d.A.v[0][i], d.A.v[1][i], D == 3 ? d.A.v[2][i] : 0.f};
   const uint8_t lab = d.A.label[i];
-  const float rho_i = d.rho_new[i];
+  const float rho_i = d.vr4[i].w;
   const float p_i = P.c0sq * (rho_i - P.rho0);
   const float pb2 = boundary_pressure2(d, lab, p_i);
   float a[3] = {0.f, 0.f, 0.f};
@@ -206,10 +207,9 @@ __device__ void force_one(const DomainDev& d, unsigned i) {
       float vj[3] = {0.f, 0.f, 0.f};
       float rho_j = rho_i;
       if (!wall) {
-        vj[0] = d.A.v[0][j];
-        vj[1] = d.A.v[1][j];
-        if (D == 3) vj[2] = d.A.v[2][j];
-        rho_j = d.rho_new[j];
+        const float4 v = d.vr4[j];
+        vj[0] = v.x, vj[1] = v.y, vj[2] = v.z;
+        rho_j = v.w;
       }
       force_term(P, wall, rx, ry, rz, r2, vi, rho_i, p_i, pb2, vj, rho_j, a);
     }
@@ -326,15 +326,58 @@ __device__ __forceinline__ void neighbours_body(const DomainDev& d, unsigned bid
   }
 }
 
-// Density pass over the lists: Eq. (9) for fluid particles, the Eq. (4) rate for buffer
-// particles.  A particle whose list overflowed (strong compression) reads its cells directly.
+// Density, Eq. (9), for particle i of the fluid (not in a buffer) from its list; writes
+// vr4[i] = (v_i, rho_i).
+template <int D>
+__device__ __forceinline__ void density_fluid(const DomainDev& d, unsigned i, int cnt) {
+  const Phys& P = d.P;
+  const float4 pi = d.pos4[i];
+  const float fi[3] = {pi.x, pi.y, pi.z};
+  float s = 0.f;
+  for_each_listed<D>(d, i, cnt, pi.w, fi, [&](int, unsigned, float rx, float ry, float rz) {
+    s += kernel_w(sqrtf(rx * rx + ry * ry + rz * rz) * P.inv_h, P);
+  });
+  const float4 v = d.vel4[i];
+  d.vr4[i] = make_float4(v.x, v.y, v.z, P.rho0 * (s + P.w_self) * P.inv_sum_w0);
+}
+
+// Density pass over the lists, Eq. (9), for the fluid particles.  Buffer particles (the
+// Eq. (4) rate) and particles whose list overflowed (strong compression: they read their
+// cells directly) are appended to the deferred list for density_deferred_body, so that this
+// pass keeps few registers and a high occupancy.
 template <int D>
 __device__ __forceinline__ void density_body(const DomainDev& d, unsigned bid, unsigned nblk) {
   if (d.st->status) return;
   const unsigned n = d.st->n;
+  const int cap = d.nb_cap;
+  const int lane = threadIdx.x & 31;
+  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
+    const int cnt = (int)d.nb_cnt[i];
+    const bool defer = d.A.label[i] != 0 || cnt > cap;
+    const unsigned am = __activemask();
+    const unsigned m = __ballot_sync(am, defer);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned base = 0;
+      if (lane == leader) base = atomicAdd(&d.st->n_defer, (unsigned)__popc(m));
+      base = __shfl_sync(am, base, leader);
+      if (defer) d.deferred[base + __popc(m & ((1u << lane) - 1u))] = i;
+    }
+    if (!defer) density_fluid<D>(d, i, cnt);
+  }
+}
+
+// The deferred particles of the density pass: Eq. (4) rate for buffer particles (plain v_j
+// of the neighbours, their start-of-step density), Eq. (9) from the cells for fluid
+// particles with an overflowed list.
+template <int D>
+__device__ __forceinline__ void density_deferred_body(const DomainDev& d, unsigned bid, unsigned nblk) {
+  if (d.st->status) return;
+  const unsigned nd = d.st->n_defer;
   const Phys P = d.P;
   const int cap = d.nb_cap;
-  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
+  for (unsigned e = bid * blockDim.x + threadIdx.x; e < nd; e += nblk * blockDim.x) {
+    const unsigned i = d.deferred[e];
     const int cnt = (int)d.nb_cnt[i];
     const float4 pi = d.pos4[i];
     const float fi[3] = {pi.x, pi.y, pi.z};
@@ -370,10 +413,12 @@ __device__ __forceinline__ void density_body(const DomainDev& d, unsigned bid, u
         if (r2 < P.two_h_sq && r2 > 0.f) term(wall, j, rx, ry, rz);
       });
     }
-    d.rho_new[i] = buf ? rho_i + P.dt * (2.f * rho_i * s) : P.rho0 * (s + P.w_self) * P.inv_sum_w0;
+    d.vr4[i] = make_float4(vi[0], vi[1], vi[2],
+                           buf ? rho_i + P.dt * (2.f * rho_i * s) : P.rho0 * (s + P.w_self) * P.inv_sum_w0);
   }
 }
 
+// Force pass over the lists: Eqs. (5)-(8), (18), then kick, boundary velocity and drift.
 template <int D>
 __device__ __forceinline__ void force_body(const DomainDev& d, unsigned bid, unsigned nblk) {
   if (d.st->status) return;
@@ -388,10 +433,10 @@ __device__ __forceinline__ void force_body(const DomainDev& d, unsigned bid, uns
     }
     const float4 pi = d.pos4[i];
     const float fi[3] = {pi.x, pi.y, pi.z};
-    const float4 vi4 = d.vel4[i];
+    const float4 vi4 = d.vr4[i];
     const float vi[3] = {vi4.x, vi4.y, vi4.z};
     const uint8_t lab = d.A.label[i];
-    const float rho_i = d.rho_new[i];
+    const float rho_i = vi4.w;
     const float p_i = P.c0sq * (rho_i - P.rho0);
     const float pb2 = boundary_pressure2(d, lab, p_i);
     float a[3] = {0.f, 0.f, 0.f};
@@ -400,9 +445,9 @@ __device__ __forceinline__ void force_body(const DomainDev& d, unsigned bid, uns
       float vj[3] = {0.f, 0.f, 0.f};
       float rho_j = rho_i;
       if (!wall) {
-        const float4 v = __ldg(d.vel4 + j);
+        const float4 v = __ldg(d.vr4 + j);
         vj[0] = v.x, vj[1] = v.y, vj[2] = v.z;
-        rho_j = __ldg(d.rho_new + j);
+        rho_j = v.w;
       }
       force_term(P, wall, rx, ry, rz, r2, vi, rho_i, p_i, pb2, vj, rho_j, a);
     });
@@ -443,7 +488,8 @@ __device__ __forceinline__ void drift_body(const DomainDev& d, unsigned bid, uns
   }
 
 SPHBUF_PAIR(k_neighbours, neighbours_body, (kThreads, 5))
-SPHBUF_PAIR(k_density, density_body, (kThreads, 5))
+SPHBUF_PAIR(k_density, density_body, (kThreads, 6))
+SPHBUF_PAIR(k_density_deferred, density_deferred_body, (kThreads, 4))
 SPHBUF_PAIR(k_force, force_body, (kThreads, 4))
 SPHBUF_PAIR(k_drift, drift_body, (kThreads))
 #undef SPHBUF_PAIR
@@ -461,11 +507,14 @@ int launch_neighbours(const DomainDev& d, cudaStream_t s) {
 }
 
 int launch_density(const DomainDev& d, cudaStream_t s) {
-  if (d.g.dim == 2)
+  if (d.g.dim == 2) {
     k_density<2><<<grid_for(d, 8), kThreads, 0, s>>>(d);
-  else
+    k_density_deferred<2><<<grid_for(d, 2), kThreads, 0, s>>>(d);
+  } else {
     k_density<3><<<grid_for(d, 8), kThreads, 0, s>>>(d);
-  return 1;
+    k_density_deferred<3><<<grid_for(d, 2), kThreads, 0, s>>>(d);
+  }
+  return 2;
 }
 
 int launch_force(const DomainDev& d, cudaStream_t s) {
@@ -495,6 +544,7 @@ int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream
   switch (k) {
     SPHBUF_CASE(K_NEIGHBOURS, k_neighbours)
     SPHBUF_CASE(K_DENSITY, k_density)
+    SPHBUF_CASE(K_DENSITY_DEFER, k_density_deferred)
     SPHBUF_CASE(K_FORCE, k_force)
     SPHBUF_CASE(K_DRIFT, k_drift)
     default:

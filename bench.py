@@ -32,10 +32,20 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PIPE_LEN = 5.09
-WORKLOAD = "3-D pipe R0.5 L5.09 dp0.01 along (1,1,1)/sqrt3, 2 bidirectional pressure buffers"
+WORKLOAD = "3-D pipe R0.5 L%g dp0.01 along (1,1,1)/sqrt3, 2 bidirectional pressure buffers"
 METRIC = "particle-steps/s at 4M (3-D pipe, 2 bidirectional pressure buffers); buffer-update us/step alongside"
 UNIT = "particle-steps/s"
 FP32_LANES_PER_SM = 128
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from the ncu
+# captures summarised in profiles/k_neighbours_pipe2M.md and profiles/k_buffer_pipe2M.md (the
+# 2.0 M-particle pipe, L = 2.5 m).  The neighbour pass scales with the particle count; the
+# buffer update with the buffers' candidate cells, which are the same at L = 2.5 and 5.09 m.
+# Set a figure to None when its kernel changes.
+NCU_TRAFFIC = {
+    "k_neighbours": {"bytes_per_particle": (113.67e6 + 636.74e6) / 1965281},
+    "k_buffer": {"bytes_per_launch": 3.50e6 + 0.0},
+}
 
 
 def parse():
@@ -106,6 +116,16 @@ class Clocks:
         mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def traffic_of(kernel, particles):
+    """DRAM bytes of one launch of `kernel` from the committed ncu figures, or None."""
+    t = NCU_TRAFFIC.get(kernel)
+    if not t:
+        return None
+    if "bytes_per_particle" in t:
+        return t["bytes_per_particle"] * particles
+    return t.get("bytes_per_launch")
 
 
 def measured_peaks():
@@ -277,7 +297,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "particles": int(n_mean), "walls": int(case.wall_pos.shape[0]),
+        "config": {"workload": WORKLOAD % args.length, "particles": int(n_mean), "walls": int(case.wall_pos.shape[0]),
                    "cells": int(dom.ncell), "buffers": len(case.buffers), "dt": case.dt,
                    "l2": "state (~%d MB) larger than L2; no flush" % (n_mean * 2 * state_bytes / 1e6),
                    "parallelism": "replicas%d" % world, "graph": True,
@@ -285,14 +305,15 @@ def run_gpu(args):
         "buffer_update_us_per_step": per["buffer"] * 1e3,
         "phase_ms_per_step": per,
         "roofline": {"bound": "alu", "kernel": kern[dom_ph]["kernel"], "achieved": kern[dom_ph]["achieved"],
-                     "peak": alu_peak, "unit": "TFLOP/s", "frac": kern[dom_ph]["frac"], "traffic": None,
+                     "peak": alu_peak, "unit": "TFLOP/s", "frac": kern[dom_ph]["frac"],
+                     "traffic": traffic_of(kern[dom_ph]["kernel"], n_mean),
                      "peak_source": "FP32 lanes x 2 x max SM clock (derived; not measured)",
                      "flops_per_particle": kern[dom_ph]["flops_per_particle"], "pairs_per_particle": pairs,
                      "candidates_per_particle": cands},
         "kernels_alu": kern,
         "roofline_buffer_update": {"bound": "hbm", "kernel": "k_buffer", "achieved": bu_gbs, "peak": hbm,
                                    "unit": "GB/s", "frac": (bu_gbs / hbm) if (bu_gbs and hbm) else None,
-                                   "traffic": None, "bytes_per_step": bu_bytes, "candidate_cells": cells,
+                                   "traffic": traffic_of("k_buffer", n_mean), "bytes_per_step": bu_bytes, "candidate_cells": cells,
                                    "candidate_particles": parts, "injected": len(inj), "deleted": len(dels),
                                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io,
@@ -416,7 +437,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": r, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD + " (bounded oracle sample)", "particles": npart},
+           "config": {"workload": WORKLOAD % args.length + " (bounded oracle sample)", "particles": npart},
            "cpu_baseline": {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": r, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))

@@ -575,6 +575,95 @@ def star_case(*, seed, n_target, arms, width, name="star", umax=1.0, c0=10.0, nu
                 wall_pos=wall, buffers=bufs, capacity=int(capacity_factor * n) + 1024, steps=500)
 
 
+def bent_channel_case(*, dp=0.005, width=1.0, leg_in=5.0, leg_out=3.0, bend_radius=2.0, angle_in_deg=30.0,
+                      angle_out_deg=-15.0, umax=1.5, c0=15.0, nu=1e-2, rho0=1000.0, h_over_dp=1.3,
+                      buffer_layers=4, init_velocity="inlet_profile", speed=0.0, seed=BASE_SEED + 2,
+                      name="bent", capacity_factor=1.4, steps=2000) -> Case:
+    """2-D non-orthogonal bent channel: an inlet leg at ``angle_in_deg``, a circular bend of
+    centre-line radius ``bend_radius``, an outlet leg at ``angle_out_deg``.
+
+    The centre line starts at the origin.  Fluid = a global lattice (jittered) within
+    ``width``/2 of the centre line between its two ends; walls = three lattice layers on both
+    sides, open at the ends.  Inlet: a velocity buffer with the parabolic profile
+    ``umax`` (1 - (Y'/R)^2), R = width/2, normal along the inlet leg; outlet: a pressure buffer
+    (p = 0) with its normal along the outlet leg.  ``init_velocity``: "inlet_profile" (rest,
+    the inlet buffer's particles on their profile), "rest", or "tangent" (every fluid particle
+    moves at ``speed`` along the local centre-line direction).
+    """
+    rng = np.random.default_rng(seed)
+    half = 0.5 * width
+    t1, t2 = math.radians(angle_in_deg), math.radians(angle_out_deg)
+    if not t2 < t1:
+        raise ValueError("the bend turns clockwise: angle_out_deg must be below angle_in_deg")
+    e1, n1 = np.array([math.cos(t1), math.sin(t1)]), np.array([-math.sin(t1), math.cos(t1)])
+    e2, n2 = np.array([math.cos(t2), math.sin(t2)]), np.array([-math.sin(t2), math.cos(t2)])
+    p0 = np.zeros(2)
+    p1 = p0 + leg_in * e1
+    centre = p1 - bend_radius * n1  # clockwise turn: centre on the right of the inlet leg
+    p2 = centre + bend_radius * n2
+    p3 = p2 + leg_out * e2
+    wall_band = 3 * dp
+    pts = np.stack([p0, p1, p2, p3, centre])
+    span_lo = pts.min(axis=0) - half - wall_band - 2 * dp
+    span_hi = pts.max(axis=0) + half + wall_band + 2 * dp
+    ax = np.arange(math.floor(span_lo[0] / dp), math.ceil(span_hi[0] / dp) + 1) * dp + 0.5 * dp
+    ay = np.arange(math.floor(span_lo[1] / dp), math.ceil(span_hi[1] / dp) + 1) * dp + 0.5 * dp
+    X, Y = np.meshgrid(ax, ay, indexing="ij")
+    P = np.stack([X.ravel(), Y.ravel()], axis=1)
+    # (along, across) coordinates of every lattice point against each piece of the centre line
+    s_a = (P - p0) @ e1
+    n_a = (P - p0) @ n1
+    v = P - centre
+    r = np.linalg.norm(v, axis=1)
+    heading = np.arctan2(-v[:, 0], v[:, 1])  # tangent angle whose left normal points at P
+    n_b = r - bend_radius
+    s_c = (P - p2) @ e2
+    n_c = (P - p2) @ n2
+    on_a = (s_a >= 0.0) & (s_a < leg_in)
+    on_b = (heading <= t1) & (heading >= t2) & (r > 0.0)
+    on_c = (s_c >= 0.0) & (s_c <= leg_out)
+    fluid_m = (on_a & (np.abs(n_a) < half)) | (on_b & (np.abs(n_b) < half)) | (on_c & (np.abs(n_c) < half))
+    band = lambda nn: (np.abs(nn) >= half) & (np.abs(nn) < half + wall_band)  # noqa: E731
+    wall_m = (((s_a >= -wall_band) & (s_a < leg_in) & band(n_a)) | (on_b & band(n_b))
+              | ((s_c >= 0.0) & (s_c <= leg_out + wall_band) & band(n_c))) & ~fluid_m
+    fluid = P[fluid_m] + rng.uniform(-0.01 * dp, 0.01 * dp, size=(int(fluid_m.sum()), 2))
+    wall = P[wall_m]
+    h = h_over_dp * dp
+    lo, hi = _grid_box([fluid, wall], margin=2.0 * (2.0 * h))
+    a = buffer_layers * dp
+    bufs = [BufferSpec(origin=np.array([*(p0 + 0.5 * a * e1), 0.0]), rotation=frame_2d(t1),
+                       extent=np.array([a, width, 0.0]), bc=VELOCITY_INLET, umax=umax, half_width=half),
+            BufferSpec(origin=np.array([*(p3 - 0.5 * a * e2), 0.0]), rotation=frame_2d(t2),
+                       extent=np.array([a, width, 0.0]), bc=PRESSURE_OUTLET, p_b=0.0)]
+    vel = np.zeros_like(fluid)
+    if init_velocity == "inlet_profile":
+        sa = (fluid - p0) @ e1
+        na = (fluid - p0) @ n1
+        inb = (sa < a) & (np.abs(na) < half)
+        vel[inb] = (umax * np.clip(1.0 - (na[inb] / half) ** 2, 0.0, None))[:, None] * e1[None, :]
+    elif init_velocity == "tangent":
+        fv = fluid - centre
+        hd = np.arctan2(-fv[:, 0], fv[:, 1])
+        tang = np.stack([np.cos(hd), np.sin(hd)], axis=1)
+        tang[(fluid - p0) @ e1 < leg_in] = e1
+        tang[(fluid - p2) @ e2 >= 0.0] = e2
+        vel = speed * tang
+    elif init_velocity != "rest":
+        raise ValueError("init_velocity must be inlet_profile, rest or tangent")
+    dt = min(0.25 * h / (c0 + umax), 0.125 * h * h / nu)
+    n = fluid.shape[0]
+    return Case(name="%s_dp%g_n%d" % (name, dp, n), dim=2, lo=lo, hi=hi, dp=dp, h_over_dp=h_over_dp, rho0=rho0,
+                c0=c0, nu=nu, dt=dt, fluid_pos=fluid, fluid_vel=vel, fluid_rho=np.full(n, rho0), wall_pos=wall,
+                buffers=bufs, capacity=int(capacity_factor * n) + 1024, steps=steps)
+
+
+def config2(dp=0.005, **kw) -> Case:
+    """2-D channel 1 m wide: inlet leg 5 m at +30 deg, bend of centre-line radius 2 m, outlet leg
+    3 m at -15 deg; parabolic velocity inlet Umax = 1.5 (R = 0.5), pressure outlet p = 0, c0 = 15,
+    nu = 1e-2; dp = 0.005 gives about 0.38 M fluid particles."""
+    return bent_channel_case(dp=dp, name="cfg2_bent", **kw)
+
+
 def config5(ndomains=64, n_lo=10_000, n_hi=500_000, seed=BASE_SEED + 5) -> List[Case]:
     """64 independent 2-D star channels: log-uniform sizes in [10 k, 500 k] particles, 1-6 arms,
     widths 0.2-1 m, seeded angles (the batched workload)."""

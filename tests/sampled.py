@@ -1,0 +1,177 @@
+"""Full-size parity checks shared by the GPU tests (test infrastructure: uses the oracle).
+
+* ``kinematic_bit_exact``: kinematic steps (drift + buffer update + rebuild) of the GPU, in
+  graph replay, against the FP32-mode oracle on every particle: decisions, sorted state,
+  cell_start.
+* ``physics_step_sampled``: one full GPU step from a case's initial state; a random sample of
+  particles is evaluated one by one by the FP64 oracle (neighbours from a k-d tree) and
+  compared with the one-step tolerances; count invariant and sortedness on all particles.
+"""
+import numpy as np
+from scipy.spatial import cKDTree
+
+from oracle import buffer as OB
+from oracle import fp32 as OF
+from oracle import sph
+from paper_2406_16786_gb300 import _ffi
+from paper_2406_16786_gb300 import workloads as wl
+
+KIN = _ffi.PHASE_KINEMATIC | _ffi.PHASE_BUFFER
+
+
+def _bits(a):
+    return np.ascontiguousarray(a, dtype=np.float32).view(np.int32)
+
+
+def _domain(c, cell, frac, vel32, rho32):
+    from paper_2406_16786_gb300.domain import Domain
+
+    dom = Domain(c.dim, c.lo, c.hi, c.dp, c.h_over_dp, c.rho0, c.c0, c.nu, c.dt, c.capacity)
+    dom.set_walls(c.wall_pos)
+    for b in c.buffers:
+        dom.add_buffer(b)
+    dom.write_particles(cell, frac, vel32, rho32)
+    dom.use_graph(True)
+    return dom
+
+
+def kinematic_bit_exact(c, vel, nsteps, full_check_too=False):
+    """Returns the number of decisions taken over the steps (the caller asserts it is > 0)."""
+    cell, frac = wl.encode_positions(c.fluid_pos, c.lo, c.cs, c.grid_dims())
+    vel32 = np.asarray(vel, dtype=np.float32)
+    rho32 = c.fluid_rho.astype(np.float32)
+    dom = _domain(c, cell, frac, vel32, rho32)
+    other = _domain(c, cell, frac, vel32, rho32) if full_check_too else None
+    sim = OF.Fp32Sim(c, cell, frac, vel32, rho32)
+    sim.commit()
+    total = 0
+    for _ in range(nsteps):
+        dom.step(1, KIN)
+        sim.step(1)
+        inj, dels = dom.last_decisions()
+        assert inj == sim.last_inj
+        assert sorted(dels) == sorted(sim.last_del)
+        total += len(inj) + len(dels)
+        g = dom.read()
+        assert np.array_equal(g["id"].astype(np.int64), sim.id)
+        assert np.array_equal(g["cell"].astype(np.int64), sim.cell)
+        assert np.array_equal(_bits(g["frac"]), _bits(sim.f))
+        assert np.array_equal(g["label"].astype(np.int64), sim.label)
+        assert np.array_equal(dom.cell_start().astype(np.int64), sim.cell_start)
+        if other is not None:
+            other.step(1, KIN | _ffi.PHASE_FULL_CHECK)
+            o = other.read()
+            for key in g:
+                assert np.array_equal(g[key], o[key]), key
+            oi, od = other.last_decisions()
+            assert oi == inj and sorted(od) == sorted(dels)
+    dom.close()
+    if other is not None:
+        other.close()
+    return total
+
+
+def physics_step_sampled(c, sample_size=1500, seed=5):
+    cell, frac = wl.encode_positions(c.fluid_pos, c.lo, c.cs, c.grid_dims())
+    vel32 = c.fluid_vel.astype(np.float32)
+    rho32 = c.fluid_rho.astype(np.float32)
+    dom = _domain(c, cell, frac, vel32, rho32)
+    n0 = dom.count()
+    dom.step(1)
+    g = dom.read()
+    gpos = dom.positions()
+    glob = dom.global_counters()
+    nb = len(c.buffers)
+    inj = sum(dom.counters(k)["injected"] for k in range(nb))
+    dele = sum(dom.counters(k)["deleted"] for k in range(nb))
+    assert g["id"].shape[0] == n0 + inj - dele - glob["escaped"]
+    assert glob["escaped"] == 0
+    lin = g["cell"].astype(np.int64)
+    assert np.all(np.diff(lin) >= 0)
+    same = np.diff(lin) == 0
+    assert np.all(np.diff(g["id"].astype(np.int64))[same] > 0)
+
+    # FP64 oracle for a sample of particles, from the same input
+    pos = wl.decode_positions(cell, frac, c.lo, c.cs, c.grid_dims())
+    vel = vel32.astype(np.float64)
+    rho = rho32.astype(np.float64)
+    P = sph.make_params(c.dim, c.dp, c.h_over_dp, c.rho0, c.c0, c.nu, c.dt)
+    bufs = [OB.Buffer(k, s, c.dim) for k, s in enumerate(c.buffers)]
+    # labels as both sides take them at the first step: Algorithms 1-3 identification, FP32
+    g32 = OF.Grid32(c.dim, c.lo, c.hi, c.dp, c.h_over_dp)
+    cc = g32.coords(cell)
+    label = np.zeros(pos.shape[0], dtype=np.int64)
+    for b in bufs:
+        b32 = OF.Buffer32(b, g32)
+        label[OF.in_box32(OF.local32(g32, b32, cc, frac), b32, c.dim)] = b.label
+    rng = np.random.default_rng(seed)
+    sample = rng.choice(pos.shape[0], min(sample_size, pos.shape[0]), replace=False)
+    # every buffer particle of a small buffer population is in the sample too
+    bsel = np.flatnonzero(label != 0)
+    if bsel.size:
+        sample = np.unique(np.concatenate([sample, rng.choice(bsel, min(300, bsel.size), replace=False)]))
+    tf = cKDTree(pos)
+    tw = cKDTree(c.wall_pos)
+    r2h = 2.0 * P.h
+
+    def pairs_for(idx):
+        ii, jj = [], []
+        for i, nbr in zip(idx, tf.query_ball_point(pos[idx], r2h)):
+            nbr = [j for j in nbr if j != i]
+            ii += [i] * len(nbr)
+            jj += nbr
+        ii, jj = np.array(ii, dtype=np.int64), np.array(jj, dtype=np.int64)
+        rij = pos[ii] - pos[jj]
+        ff = sph.Pairs(ii, jj, rij, np.linalg.norm(rij, axis=1))
+        wi, wj = [], []
+        for i, nbr in zip(idx, tw.query_ball_point(pos[idx], r2h)):
+            wi += [i] * len(nbr)
+            wj += nbr
+        wi, wj = np.array(wi, dtype=np.int64), np.array(wj, dtype=np.int64)
+        rw = pos[wi] - c.wall_pos[wj]
+        fw = sph.Pairs(wi, wj, rw, np.linalg.norm(rw, axis=1))
+        return ff, fw
+
+    # densities of the sample and of all their neighbours (needed by the force)
+    ff_s, fw_s = pairs_for(sample)
+    need = np.unique(np.concatenate([sample, ff_s.j]))
+    ff_n, fw_n = pairs_for(need)
+    n = pos.shape[0]
+    rho_sum = sph.density_summation(P, n, ff_n, fw_n)
+    drho = sph.continuity_rate(P, vel, rho, ff_n, fw_n)
+    rho_new = np.where(label != 0, rho + P.dt * drho, rho_sum)
+    p_bc = np.full(n, np.nan)
+    p_eos = sph.eos(rho_new, P)
+    for b in bufs:
+        m = label == b.label
+        p_bc[m] = b.p_b(0.0) if b.bc in OB.PRESSURE_BC else p_eos[m]
+    acc = sph.acceleration(P, vel, rho_new, p_bc, ff_s, fw_s)
+    v_new = vel[sample] + acc[sample] * P.dt
+    for b in bufs:
+        m = label[sample] == b.label
+        if not m.any():
+            continue
+        if b.bc in OB.VELOCITY_BC:
+            prof = b.profile(b.local(pos[sample][m]))
+            v_new[m] = prof[:, None] * b.u[None, :]
+        else:
+            un = v_new[m] @ b.u
+            v_new[m] = un[:, None] * b.u[None, :]
+    r_new = pos[sample] + v_new * P.dt
+
+    gid = g["id"].astype(np.int64)
+    where = {int(i): k for k, i in enumerate(gid)}
+    keep = [k for k, i in enumerate(sample) if int(i) in where]  # sample ids are the input ids
+    gi = np.array([where[int(sample[k])] for k in keep])
+    rho_g = g["rho"][gi].astype(np.float64)
+    rho_o = rho_new[sample][keep]
+    assert np.linalg.norm(rho_g - rho_o) / np.linalg.norm(rho_o) < 1e-5
+    assert np.max(np.abs(rho_g - rho_o)) / P.rho0 < 1e-6
+    vg = g["vel"][gi].astype(np.float64)
+    vo = v_new[keep]
+    assert np.linalg.norm(vg - vo) / max(np.linalg.norm(vo), 1e-30) < 1e-5
+    # recycled particles moved by a u; compare the rest
+    moved = np.linalg.norm(gpos[gi] - r_new[keep], axis=1)
+    assert np.quantile(moved, 0.99) < 1e-6 * c.cs
+    dom.close()
+    return len(keep)

@@ -7,19 +7,12 @@ configuration (graph replays of the whole step).
   same input (neighbours of the sample found with a k-d tree), with the one-step tolerances
   of tests/test_gpu_physics.py; count invariant and sortedness on all particles.
 """
-import numpy as np
 import pytest
-from scipy.spatial import cKDTree
 
-from oracle import buffer as OB
-from oracle import fp32 as OF
-from oracle import sph
-from paper_2406_16786_gb300 import _ffi
 from paper_2406_16786_gb300 import workloads as wl
+from tests import sampled
 
 pytestmark = pytest.mark.gpu
-
-KIN = _ffi.PHASE_KINEMATIC | _ffi.PHASE_BUFFER
 
 
 @pytest.fixture(scope="module")
@@ -27,142 +20,10 @@ def case():
     return wl.config3(length=5.09)
 
 
-def _bits(a):
-    return np.ascontiguousarray(a, dtype=np.float32).view(np.int32)
-
-
 def test_full_size_kinematic_steps_bit_exact(case):
-    from paper_2406_16786_gb300.domain import Domain
-
-    c = case
-    cell, frac = wl.encode_positions(c.fluid_pos, c.lo, c.cs, c.grid_dims())
     # speed the flow up so that both faces see crossings within two steps
-    vel = (c.fluid_vel * 200.0).astype(np.float32)
-    rho = c.fluid_rho.astype(np.float32)
-    dom = Domain(c.dim, c.lo, c.hi, c.dp, c.h_over_dp, c.rho0, c.c0, c.nu, c.dt, c.capacity)
-    dom.set_walls(c.wall_pos)
-    for b in c.buffers:
-        dom.add_buffer(b)
-    dom.write_particles(cell, frac, vel, rho)
-    dom.use_graph(True)
-    sim = OF.Fp32Sim(c, cell, frac, vel, rho)
-    sim.commit()
-    total = 0
-    for _ in range(2):
-        dom.step(1, KIN)
-        sim.step(1)
-        inj, dels = dom.last_decisions()
-        assert inj == sim.last_inj
-        assert sorted(dels) == sorted(sim.last_del)
-        total += len(inj) + len(dels)
-        g = dom.read()
-        assert np.array_equal(g["id"].astype(np.int64), sim.id)
-        assert np.array_equal(g["cell"].astype(np.int64), sim.cell)
-        assert np.array_equal(_bits(g["frac"]), _bits(sim.f))
-        assert np.array_equal(g["label"].astype(np.int64), sim.label)
-        assert np.array_equal(dom.cell_start().astype(np.int64), sim.cell_start)
-    assert total > 0
-    dom.close()
+    assert sampled.kinematic_bit_exact(case, case.fluid_vel * 200.0, 2) > 0
 
 
 def test_full_size_physics_step_sampled(case):
-    from paper_2406_16786_gb300.domain import Domain
-
-    c = case
-    cell, frac = wl.encode_positions(c.fluid_pos, c.lo, c.cs, c.grid_dims())
-    vel32 = c.fluid_vel.astype(np.float32)
-    rho32 = c.fluid_rho.astype(np.float32)
-    dom = Domain(c.dim, c.lo, c.hi, c.dp, c.h_over_dp, c.rho0, c.c0, c.nu, c.dt, c.capacity)
-    dom.set_walls(c.wall_pos)
-    for b in c.buffers:
-        dom.add_buffer(b)
-    dom.write_particles(cell, frac, vel32, rho32)
-    dom.use_graph(True)
-    n0 = dom.count()
-    dom.step(1)
-    g = dom.read()
-    gpos = dom.positions()
-    glob = dom.global_counters()
-    inj = sum(dom.counters(k)["injected"] for k in range(2))
-    dele = sum(dom.counters(k)["deleted"] for k in range(2))
-    assert g["id"].shape[0] == n0 + inj - dele - glob["escaped"]
-    assert glob["escaped"] == 0
-    lin = g["cell"].astype(np.int64)
-    assert np.all(np.diff(lin) >= 0)
-    same = np.diff(lin) == 0
-    assert np.all(np.diff(g["id"].astype(np.int64))[same] > 0)
-
-    # FP64 oracle for a sample of particles, from the same input
-    pos = wl.decode_positions(cell, frac, c.lo, c.cs, c.grid_dims())
-    vel = vel32.astype(np.float64)
-    rho = rho32.astype(np.float64)
-    P = sph.make_params(c.dim, c.dp, c.h_over_dp, c.rho0, c.c0, c.nu, c.dt)
-    bufs = [OB.Buffer(k, s, c.dim) for k, s in enumerate(c.buffers)]
-    # labels as both sides take them: Algorithm 3 identification in the FP32 decision mode
-    g32 = OF.Grid32(c.dim, c.lo, c.hi, c.dp, c.h_over_dp)
-    cc = g32.coords(cell)
-    label = np.zeros(pos.shape[0], dtype=np.int64)
-    for b in bufs:
-        b32 = OF.Buffer32(b, g32)
-        label[OF.in_box32(OF.local32(g32, b32, cc, frac), b32, c.dim)] = b.label
-    rng = np.random.default_rng(5)
-    sample = rng.choice(pos.shape[0], 1500, replace=False)
-    tf = cKDTree(pos)
-    tw = cKDTree(c.wall_pos)
-    r2h = 2.0 * P.h
-
-    def pairs_for(idx):
-        ii, jj = [], []
-        for i, nb in zip(idx, tf.query_ball_point(pos[idx], r2h)):
-            nb = [j for j in nb if j != i]
-            ii += [i] * len(nb)
-            jj += nb
-        ii, jj = np.array(ii, dtype=np.int64), np.array(jj, dtype=np.int64)
-        rij = pos[ii] - pos[jj]
-        ff = sph.Pairs(ii, jj, rij, np.linalg.norm(rij, axis=1))
-        wi, wj = [], []
-        for i, nb in zip(idx, tw.query_ball_point(pos[idx], r2h)):
-            wi += [i] * len(nb)
-            wj += nb
-        wi, wj = np.array(wi, dtype=np.int64), np.array(wj, dtype=np.int64)
-        rw = pos[wi] - c.wall_pos[wj]
-        fw = sph.Pairs(wi, wj, rw, np.linalg.norm(rw, axis=1))
-        return ff, fw
-
-    # densities of the sample and of all their neighbours (needed by the force)
-    ff_s, fw_s = pairs_for(sample)
-    need = np.unique(np.concatenate([sample, ff_s.j]))
-    ff_n, fw_n = pairs_for(need)
-    n = pos.shape[0]
-    rho_sum = sph.density_summation(P, n, ff_n, fw_n)
-    drho = sph.continuity_rate(P, vel, rho, ff_n, fw_n)
-    rho_new = np.where(label != 0, rho + P.dt * drho, rho_sum)
-    p_bc = np.full(n, np.nan)
-    t0 = 0.0
-    for b in bufs:
-        m = label == b.label
-        p_bc[m] = b.p_b(t0)
-    acc = sph.acceleration(P, vel, rho_new, p_bc, ff_s, fw_s)
-    v_new = vel[sample] + acc[sample] * P.dt
-    for b in bufs:
-        m = label[sample] == b.label
-        if m.any():
-            un = v_new[m] @ b.u
-            v_new[m] = un[:, None] * b.u[None, :]
-    r_new = pos[sample] + v_new * P.dt
-
-    gid = g["id"].astype(np.int64)
-    where = {int(i): k for k, i in enumerate(gid)}
-    keep = [k for k, i in enumerate(sample) if int(i) in where]  # sample ids are the input ids
-    gi = np.array([where[int(sample[k])] for k in keep])
-    rho_g = g["rho"][gi].astype(np.float64)
-    rho_o = rho_new[sample][keep]
-    assert np.linalg.norm(rho_g - rho_o) / np.linalg.norm(rho_o) < 1e-5
-    assert np.max(np.abs(rho_g - rho_o)) / P.rho0 < 1e-6
-    vg = g["vel"][gi].astype(np.float64)
-    vo = v_new[keep]
-    assert np.linalg.norm(vg - vo) / np.linalg.norm(vo) < 1e-5
-    # recycled particles moved by a u; compare the rest
-    moved = np.linalg.norm(gpos[gi] - r_new[keep], axis=1)
-    assert np.quantile(moved, 0.99) < 1e-6 * c.cs
-    dom.close()
+    assert sampled.physics_step_sampled(case) > 1000

@@ -174,6 +174,33 @@ def oracle_rate_probe():
     return rate
 
 
+def time_cpu_buffer_update(case, reps=3):
+    """Buffer decisions (Algorithms 1-3) on the CPU, FP64 oracle, one core: every particle
+    against every buffer (the plain definition) vs the paper's local-cell restriction
+    (oracle/local_cell.py), on the initial state of the workload.  Best of ``reps``."""
+    from oracle import buffer as OB
+    from oracle import local_cell as LC
+
+    sim = OB.OracleSim(case)
+    sim.commit()
+    cand = [LC.candidate_cells(b, sim.lo, sim.cs, sim.dims, sim.dim) for b in sim.buffers]
+    t_all, t_loc = [], []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        inj, dels = OB.decide(sim.buffers, sim.pos, sim.label, sim.cs)
+        t_all.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        li, ld = LC.decide_local(sim.buffers, sim.pos, sim.label, sim.cs, sim.cell_start, cand)
+        t_loc.append(time.perf_counter() - t0)
+        if sorted(inj) != li or sorted(dels) != ld:
+            raise RuntimeError("local-cell decisions differ from the all-particle oracle")
+    visited = int(sum(LC.candidates(sim.cell_start, c).size for c in cand))
+    return {"all_particles_us_per_step": min(t_all) * 1e6, "local_cells_us_per_step": min(t_loc) * 1e6,
+            "speedup_local_vs_all": min(t_all) / min(t_loc), "particles": int(sim.n),
+            "candidate_particles": visited, "cores": 1, "kind": "oracle FP64 (numpy) decisions",
+            "sample": "initial state of the workload (all particles), best of %d" % reps}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import torch
@@ -287,11 +314,13 @@ def run_gpu(args):
     tjunction = None if args.no_tjunction else run_restricted_vs_full(args, stream)
 
     cpu = None
+    cpu_bu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate = oracle_rate_probe()
         target = int(min(200000, max(20000, rate * 15.0 / 3)))
         r, per_step, sample, npart = time_oracle(3, 0, target)
         cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        cpu_bu = time_cpu_buffer_update(case)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -321,6 +350,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "cpu_buffer_update": cpu_bu,
         "batched_vs_plain": batched,
         "restricted_vs_full_16M": tjunction,
     }

@@ -143,6 +143,22 @@ sphbuf_status sphbuf_add_inout_buffer(sphbuf_domain_t d, const double origin[3],
                                       sphbuf_bc_type bc, const sphbuf_bc_params *params,
                                       int *out_id);
 
+/* Time-varying frame of inflow buffer buffer_id (Sec. 5.3, the rotating sprinkler: the
+ * buffer turns with the constant angular velocity omega, theta = omega t + theta_0).  After
+ * the particle generation of each step the buffer's particles (positions and velocities) are
+ * rotated by omega dt about pivot (about the z axis in 2-D, about axis in 3-D; axis need not
+ * be unit length and is ignored in 2-D), and the frame is re-established for the next step:
+ * with M the rotation by omega dt and Q_n = M^n, the frame of step n is
+ * O'_n = pivot + Q_n (O'_0 - pivot), R_n = R_0 Q_n^T (FP64 recurrence, the FP32 decision
+ * constants re-derived each step).  Positions move in the FP32 contract: offset from the
+ * pivot D, D' = fl32(M) D row by row, move by D' - D.  The candidate cells are those the
+ * box (dilated by 2 cs) can reach while it turns.  Errors: SPHBUF_ERR_INVALID_ARG (not an
+ * inflow buffer, no axis in 3-D, non-finite input), SPHBUF_ERR_STATE (after the first step or
+ * set twice), SPHBUF_ERR_OVERLAP (the swept region meets another buffer's candidate region).
+ * Only before the first step. */
+sphbuf_status sphbuf_set_buffer_rotation(sphbuf_domain_t d, int buffer_id, const double pivot[3],
+                                         const double axis[3], double omega);
+
 /* Rodrigues frame of Eqs. (12)-(14): R with R n = e_x (reading: I - S sin + S^2 (1 - cos),
  * the transpose of the printed formula, so that X' = R (X - O') has X' along n), followed by
  * a roll about X': R <- Rx(roll) R.  n need not be unit length. */

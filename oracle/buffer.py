@@ -38,7 +38,7 @@ from typing import List
 
 import numpy as np
 
-from . import frames, sph
+from . import frames, moving, sph
 
 VELOCITY_INLET, PRESSURE_OUTLET, PRESSURE_INLET, VELOCITY_OUTLET, BIDIR_PRESSURE, BIDIR_VELOCITY = range(6)
 INFLOW = (VELOCITY_INLET, PRESSURE_INLET)
@@ -67,6 +67,20 @@ class Buffer:
         self.p_amp = float(getattr(spec, "p_amp", 0.0))
         self.p_omega = float(getattr(spec, "p_omega", 0.0))
         self.p_phase = float(getattr(spec, "p_phase", 0.0))
+        self.u = frames.normal(self.R)
+        pivot = getattr(spec, "pivot", None)
+        self.pivot = None if pivot is None else np.asarray(pivot, dtype=np.float64)[:3]
+        axis = getattr(spec, "axis", None)
+        self.axis = (0.0, 0.0, 1.0) if axis is None else np.asarray(axis, dtype=np.float64)[:3]
+        self.omega = float(getattr(spec, "omega", 0.0))
+        if self.pivot is not None and self.bc not in INFLOW:
+            raise ValueError("only inflow buffers may have a time-varying frame")
+
+    def set_frame(self, R3, origin):
+        """Re-establish the local frame (Sec. 5.3): new rotation and origin."""
+        self.R3 = np.asarray(R3, dtype=np.float64)
+        self.R = self.R3[:self.dim, :self.dim]
+        self.origin = np.asarray(origin, dtype=np.float64)[:3]
         self.u = frames.normal(self.R)
 
     def p_b(self, t: float) -> float:
@@ -182,6 +196,13 @@ class OracleSim:
         self.wall = np.array(case.wall_pos, dtype=np.float64)[:, :d].copy()
         self.buffers = [Buffer(k, s, d) for k, s in enumerate(case.buffers)]
         self.step_index = int(step_index)
+        # time-varying frames (Sec. 5.3): the frame of step n is the n-th of the recurrence
+        self.moving = {b.k: moving.MovingFrame(d, b.R3, b.origin, b.pivot, b.axis, b.omega, self.P.dt)
+                       for b in self.buffers if b.pivot is not None}
+        for k, mf in self.moving.items():
+            for _ in range(self.step_index):
+                mf.advance()
+            self.buffers[k].set_frame(*mf.frame())
         K = len(self.buffers)
         self.injected = np.zeros(K, dtype=np.int64)
         self.deleted = np.zeros(K, dtype=np.int64)
@@ -299,6 +320,17 @@ class OracleSim:
             self.rho = np.concatenate([self.rho, np.array(new_rho)])
             self.id = np.concatenate([self.id, np.array(new_id, dtype=np.int64)])
             self.label = np.concatenate([self.label, np.zeros(len(new_pos), dtype=np.int64)])
+        # Sec. 5.3: after the generation, the particles of a rotating buffer turn with it
+        for k, mf in self.moving.items():
+            m = self.label == self.buffers[k].label
+            if m.any():
+                self.pos[m], self.vel[m] = moving.rotate64(self.pos[m], self.vel[m], mf.C, mf.M, self.dim)
+
+    def advance_frames(self):
+        """Re-establish the rotating buffers' frames for the next step (Sec. 5.3)."""
+        for k, mf in self.moving.items():
+            mf.advance()
+            self.buffers[k].set_frame(*mf.frame())
 
     def drop_escaped(self):
         c = cell_coords(self.pos, self.lo, self.cs, self.dims, self.dim)
@@ -320,4 +352,5 @@ class OracleSim:
                 self.last_inj, self.last_del = [], []
             self.rebuild()
             relabel(self.buffers, self.pos, self.label)
+            self.advance_frames()
             self.step_index += 1

@@ -29,6 +29,7 @@ from typing import List
 import numpy as np
 
 from . import buffer as B
+from . import moving as MV
 
 F32 = np.float32
 
@@ -167,8 +168,17 @@ class Fp32Sim:
         self.labels_given = labels is not None
         self.next_id = int(n if next_id is None else next_id)
         self.bufs64 = [B.Buffer(k, s, d) for k, s in enumerate(case.buffers)]
-        self.bufs = [Buffer32(b, self.g) for b in self.bufs64]
         self.step_index = int(step_index)
+        # time-varying frames (Sec. 5.3; oracle/moving.py): FP64 recurrence, FP32 rotation
+        self.moving = {b.k: MV.MovingFrame(d, b.R3, b.origin, b.pivot, b.axis, b.omega, self.dt)
+                       for b in self.bufs64 if b.pivot is not None}
+        self.pivot32 = {k: MV.encode_point(self.g, mf.C) for k, mf in self.moving.items()}
+        self.M32 = {k: np.array(mf.M, dtype=F32) for k, mf in self.moving.items()}
+        for k, mf in self.moving.items():
+            for _ in range(self.step_index):
+                mf.advance()
+            self.bufs64[k].set_frame(*mf.frame())
+        self.bufs = [Buffer32(b, self.g) for b in self.bufs64]
         K = len(self.bufs)
         self.injected = np.zeros(K, dtype=np.int64)
         self.deleted = np.zeros(K, dtype=np.int64)
@@ -262,6 +272,20 @@ class Fp32Sim:
             self.rho = np.concatenate([self.rho, nr])
             self.id = np.concatenate([self.id, nid])
             self.label = np.concatenate([self.label, np.zeros(n_new, dtype=np.int64)])
+        # Sec. 5.3: the particles of a rotating buffer turn with it after the generation
+        for k in self.moving:
+            m = np.nonzero(self.label == self.bufs[k].label)[0]
+            if m.size:
+                cc, ff, vv = self.c[m].copy(), self.f[m].copy(), self.vel[m].copy()
+                cC, fC = self.pivot32[k]
+                MV.rotate32(self.g, cc, ff, vv, cC, fC, self.M32[k])
+                self.c[m], self.f[m], self.vel[m] = cc, ff, vv
+
+    def advance_frames(self):
+        for k, mf in self.moving.items():
+            mf.advance()
+            self.bufs64[k].set_frame(*mf.frame())
+            self.bufs[k] = Buffer32(self.bufs64[k], self.g)
 
     def step(self, nsteps=1, buffer=True):
         for _ in range(nsteps):
@@ -272,4 +296,5 @@ class Fp32Sim:
                 self.last_inj, self.last_del = [], []
             self.rebuild()
             self.relabel()
+            self.advance_frames()
             self.step_index += 1

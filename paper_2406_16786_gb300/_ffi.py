@@ -35,6 +35,7 @@ SIGNATURES = {
     "sphbuf_write_particles": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, c_u64, c_u32]),
     "sphbuf_add_inout_buffer": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int, P(BcParams), P(ctypes.c_int)]),
     "sphbuf_rotation_from_normal": (ctypes.c_int, [vp, c_dbl, vp]),
+    "sphbuf_set_buffer_rotation": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, c_dbl]),
     "sphbuf_step": (ctypes.c_int, [vp, ctypes.c_int]),
     "sphbuf_step_phases": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_uint]),
     "sphbuf_use_graph": (ctypes.c_int, [vp, ctypes.c_int]),

@@ -24,6 +24,9 @@ struct BufHost {
   double origin[3], R[9], extent[3];
   int bc;
   sphbuf_bc_params prm;
+  bool rotating = false;
+  RotDev rot{};
+  double r_min = 0, r_max = 0;  // distances from the pivot swept by the dilated box
 };
 
 }  // namespace
@@ -165,9 +168,45 @@ bool obb_overlap(int dim, const double c1[3], const double R1[9], const double h
   return true;
 }
 
+// Distances from a point C to the nearest and farthest points of an oriented box (centre O,
+// frame rows R, half extents h).
+void box_distances(int dim, const double C[3], const double O[3], const double R[9], const double h[3],
+                   double* dmin, double* dmax) {
+  double s2 = 0;
+  for (int r = 0; r < dim; ++r) {
+    double q = 0;
+    for (int x = 0; x < dim; ++x) q += R[3 * r + x] * (C[x] - O[x]);
+    const double e = std::max(std::fabs(q) - h[r], 0.0);
+    s2 += e * e;
+  }
+  *dmin = std::sqrt(s2);
+  double best = 0;
+  const int ncorner = 1 << dim;
+  for (int m = 0; m < ncorner; ++m) {
+    double p2 = 0;
+    for (int x = 0; x < dim; ++x) {
+      double cx = O[x] - C[x];
+      for (int r = 0; r < dim; ++r) cx += ((m >> r) & 1 ? h[r] : -h[r]) * R[3 * r + x];
+      p2 += cx * cx;
+    }
+    best = std::max(best, p2);
+  }
+  *dmax = std::sqrt(best);
+}
+
+// Does the region swept by rotating buffer b (a shell about its pivot) meet the box?
+bool swept_overlaps_box(int dim, const BufHost& b, const double O[3], const double R[9], const double h[3]) {
+  double dmin = 0, dmax = 0;
+  box_distances(dim, b.rot.C, O, R, h, &dmin, &dmax);
+  return dmin <= b.r_max && dmax >= b.r_min;
+}
+
 sphbuf_status upload_buffers(sphbuf_domain* d) {
   CK(cudaMemcpy(const_cast<BufDev*>(d->dev.bufs), d->bufs_dev.data(), d->bufs_dev.size() * sizeof(BufDev),
                 cudaMemcpyHostToDevice));
+  std::vector<RotDev> rot(d->bufs.size());
+  for (size_t k = 0; k < d->bufs.size(); ++k) rot[k] = d->bufs[k].rot;
+  if (!rot.empty()) CK(cudaMemcpy(d->dev.rot, rot.data(), rot.size() * sizeof(RotDev), cudaMemcpyHostToDevice));
   std::vector<int> rel;
   for (size_t k = 0; k < d->bufs_dev.size(); ++k)
     if (d->bufs_dev[k].kind != KIND_INFLOW) rel.push_back((int)k);
@@ -191,6 +230,33 @@ sphbuf_status build_segments(sphbuf_domain* d) {
   std::vector<int> segbuf;
   for (size_t k = 0; k < d->bufs.size(); ++k) {
     const BufHost& b = d->bufs[k];
+    if (b.rotating) {
+      // Sec. 5.3: every cell the dilated box can reach while it turns about the pivot, i.e.
+      // cells whose centre lies within [r_min - rad, r_max + rad] of the pivot
+      const double rad = 0.5 * cs * std::sqrt((double)D);
+      int lo_c[3] = {0, 0, 0}, hi_c[3] = {0, 0, 0};
+      for (int x = 0; x < D; ++x) {
+        lo_c[x] = std::max(0, (int)std::floor((b.rot.C[x] - b.r_max - rad - d->desc.lo[x]) / cs));
+        hi_c[x] = std::min(d->dims[x] - 1, (int)std::floor((b.rot.C[x] + b.r_max + rad - d->desc.lo[x]) / cs));
+      }
+      for (int cz = lo_c[2]; cz <= hi_c[2]; ++cz)
+        for (int cy = lo_c[1]; cy <= hi_c[1]; ++cy)
+          for (int cx = lo_c[0]; cx <= hi_c[0]; ++cx) {
+            const int cc[3] = {cx, cy, cz};
+            double r2 = 0;
+            for (int x = 0; x < D; ++x) {
+              const double e = d->desc.lo[x] + (cc[x] + 0.5) * cs - b.rot.C[x];
+              r2 += e * e;
+            }
+            const double r = std::sqrt(r2);
+            if (r > b.r_max + rad || r < b.r_min - rad) continue;
+            const int lin = (cz * d->dims[1] + cy) * d->dims[0] + cx;
+            seg.push_back(lin);
+            seg.push_back(lin + 1);
+            segbuf.push_back((int)k);
+          }
+      continue;
+    }
     const double dil = (d->bufs_dev[k].kind == KIND_OUTFLOW) ? 2.0 * cs : cs;
     double half[3] = {0.5 * b.extent[0] + dil, 0.5 * b.extent[1] + dil, D == 3 ? 0.5 * b.extent[2] + dil : 0.0};
     // AABB of the dilated box in cell coordinates
@@ -409,6 +475,8 @@ sphbuf_status sphbuf_create_domain(const sphbuf_domain_desc* desc, void* cuda_st
   P.rho0_d = desc->rho0;
   P.c0sq_d = desc->c0 * desc->c0;
   P.dt_d = desc->dt;
+  for (int x = 0; x < 3; ++x) P.lo_d[x] = desc->lo[x];
+  P.cs_d = d->cs;
   P.capacity = (unsigned)desc->capacity;
   P.list_cap = (unsigned)std::max<uint64_t>(1024, std::min<uint64_t>(desc->capacity, 1ull << 22));
   const size_t C = desc->capacity;
@@ -454,6 +522,7 @@ sphbuf_status sphbuf_create_domain(const sphbuf_domain_desc* desc, void* cuda_st
   BufDev* bd = nullptr;
   A(dalloc(d, &bd, kMaxBuffers));
   v.bufs = bd;
+  A(dalloc(d, &v.rot, kMaxBuffers));
   int* rel = nullptr;
   A(dalloc(d, &rel, kMaxBuffers));
   v.relabel_ids = rel;
@@ -694,7 +763,7 @@ sphbuf_status sphbuf_add_inout_buffer(sphbuf_domain_t d, const double origin[3],
   const double h1[3] = {0.5 * b.extent[0] + dil, 0.5 * b.extent[1] + dil, D == 3 ? 0.5 * b.extent[2] + dil : 0};
   for (const BufHost& o : d->bufs) {
     const double h2[3] = {0.5 * o.extent[0] + dil, 0.5 * o.extent[1] + dil, D == 3 ? 0.5 * o.extent[2] + dil : 0};
-    if (obb_overlap(D, b.origin, b.R, h1, o.origin, o.R, h2))
+    if (obb_overlap(D, b.origin, b.R, h1, o.origin, o.R, h2) || (o.rotating && swept_overlaps_box(D, o, b.origin, b.R, h1)))
       return fail(d, SPHBUF_ERR_OVERLAP, "candidate regions of two buffers overlap");
   }
   const int k = (int)d->bufs.size();
@@ -750,6 +819,80 @@ sphbuf_status sphbuf_add_inout_buffer(sphbuf_domain_t d, const double origin[3],
   d->bufs.push_back(b);
   d->bufs_dev.push_back(v);
   if (out_id) *out_id = k;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_set_buffer_rotation(sphbuf_domain_t d, int buffer_id, const double pivot[3], const double axis[3],
+                                         double omega) {
+  if (!d || !pivot) return SPHBUF_ERR_INVALID_ARG;
+  if (d->stepped || d->committed) return fail(d, SPHBUF_ERR_STATE, "rotation must be set before the first step");
+  if (buffer_id < 0 || buffer_id >= (int)d->bufs.size()) return fail(d, SPHBUF_ERR_INVALID_ARG, "no such buffer");
+  BufHost& b = d->bufs[buffer_id];
+  BufDev& v = d->bufs_dev[buffer_id];
+  if (v.kind != KIND_INFLOW) return fail(d, SPHBUF_ERR_INVALID_ARG, "only inflow buffers may rotate");
+  if (b.rotating) return fail(d, SPHBUF_ERR_STATE, "rotation already set");
+  if (!std::isfinite(omega)) return fail(d, SPHBUF_ERR_INVALID_ARG, "omega must be finite");
+  const int D = d->desc.dim;
+  const double C[3] = {pivot[0], pivot[1], D == 3 ? pivot[2] : 0.0};
+  for (int x = 0; x < 3; ++x)
+    if (!std::isfinite(C[x])) return fail(d, SPHBUF_ERR_INVALID_ARG, "pivot must be finite");
+  // M: rotation by omega dt (about z in 2-D; about the unit axis in 3-D), FP64 in the order
+  // the oracle states
+  const double phi = omega * d->desc.dt;
+  const double s = std::sin(phi), c = std::cos(phi);
+  double M[9];
+  if (D == 2) {
+    const double m2[9] = {c, -s, 0.0, s, c, 0.0, 0.0, 0.0, 1.0};
+    std::memcpy(M, m2, sizeof(M));
+  } else {
+    if (!axis) return fail(d, SPHBUF_ERR_INVALID_ARG, "a 3-D rotation needs an axis");
+    const double nn = std::sqrt((axis[0] * axis[0] + axis[1] * axis[1]) + axis[2] * axis[2]);
+    if (!(nn > 0) || !std::isfinite(nn)) return fail(d, SPHBUF_ERR_INVALID_ARG, "rotation axis must be non-zero");
+    const double n0 = axis[0] / nn, n1 = axis[1] / nn, n2 = axis[2] / nn, t = 1.0 - c;
+    const double m3[9] = {(t * n0) * n0 + c,      (t * n0) * n1 - s * n2, (t * n0) * n2 + s * n1,
+                          (t * n0) * n1 + s * n2, (t * n1) * n1 + c,      (t * n1) * n2 - s * n0,
+                          (t * n0) * n2 - s * n1, (t * n1) * n2 + s * n0, (t * n2) * n2 + c};
+    std::memcpy(M, m3, sizeof(M));
+  }
+  BufHost nb = b;
+  RotDev& q = nb.rot;
+  std::memcpy(q.M, M, sizeof(M));
+  for (int e = 0; e < 9; ++e) q.Q[e] = (e % 4 == 0) ? 1.0 : 0.0;
+  std::memcpy(q.C, C, sizeof(C));
+  std::memcpy(q.O0, b.origin, sizeof(q.O0));
+  std::memcpy(q.R0, b.R, sizeof(q.R0));
+  q.a = b.extent[0];
+  // distances from the pivot swept by the box dilated by 2 cs
+  const double dil = 2.0 * d->cs;
+  const double hd[3] = {0.5 * b.extent[0] + dil, 0.5 * b.extent[1] + dil, D == 3 ? 0.5 * b.extent[2] + dil : 0.0};
+  box_distances(D, C, b.origin, b.R, hd, &nb.r_min, &nb.r_max);
+  nb.rotating = true;
+  for (size_t o = 0; o < d->bufs.size(); ++o) {
+    if ((int)o == buffer_id) continue;
+    const BufHost& ob = d->bufs[o];
+    const double ho[3] = {0.5 * ob.extent[0] + dil, 0.5 * ob.extent[1] + dil, D == 3 ? 0.5 * ob.extent[2] + dil : 0.0};
+    bool hit = swept_overlaps_box(D, nb, ob.origin, ob.R, ho);
+    if (ob.rotating) {
+      double dd = 0;
+      for (int x = 0; x < D; ++x) dd += (C[x] - ob.rot.C[x]) * (C[x] - ob.rot.C[x]);
+      hit = hit || std::sqrt(dd) <= nb.r_max + ob.r_max;
+    }
+    if (hit) return fail(d, SPHBUF_ERR_OVERLAP, "the rotating buffer's swept region meets another buffer's");
+  }
+  b = nb;
+  v.rotating = 1;
+  for (int x = 0; x < 3; ++x) {
+    v.cC[x] = 0;
+    v.fC[x] = 0.f;
+    if (x < D) {
+      const double t = C[x] - d->desc.lo[x];
+      const double cc = std::floor(t / d->cs);
+      v.cC[x] = (int)cc;
+      v.fC[x] = (float)(t - cc * d->cs);
+    }
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int cc = 0; cc < 3; ++cc) v.M32[r][cc] = (float)M[3 * r + cc];
   return SPHBUF_OK;
 }
 

@@ -42,7 +42,83 @@ struct BufDev {
   float flux_scale;    // dp^d / a
   int box_lo[3], box_hi[3];  // cell-coordinate bounds containing the box (relabel prefilter)
   double p_b0, p_amp, p_omega, p_phase;
+  // time-varying frame (Sec. 5.3): the buffer's particles turn by M32 about the pivot
+  // (cC, fC) after each buffer update; the frame fields above are re-derived every step
+  int rotating;
+  int cC[3];
+  float fC[3];
+  float M32[3][3];
 };
+
+// FP64 state of a rotating buffer's frame (Sec. 5.3): Q_n = M Q_{n-1}, R_n = R_0 Q_n^T,
+// O'_n = C + Q_n (O'_0 - C).
+struct RotDev {
+  double M[9];   // rotation by omega dt (row-major)
+  double Q[9];   // accumulated rotation of the current step
+  double C[3];   // pivot
+  double O0[3];  // origin at step 0
+  double R0[9];  // frame at step 0
+  double a;      // extent along X' (recycling shift)
+};
+
+// FP64 arithmetic without contraction, identical on host and device (the host code is
+// compiled with -ffp-contract=off; device code uses the round-to-nearest intrinsics).
+#ifdef __CUDA_ARCH__
+#define SPHBUF_DMUL(a, b) __dmul_rn((a), (b))
+#define SPHBUF_DADD(a, b) __dadd_rn((a), (b))
+#define SPHBUF_DSUB(a, b) __dsub_rn((a), (b))
+#define SPHBUF_DDIV(a, b) __ddiv_rn((a), (b))
+#else
+#define SPHBUF_DMUL(a, b) ((a) * (b))
+#define SPHBUF_DADD(a, b) ((a) + (b))
+#define SPHBUF_DSUB(a, b) ((a) - (b))
+#define SPHBUF_DDIV(a, b) ((a) / (b))
+#endif
+
+// The frame-dependent FP32 constants of the decision contract from an FP64 frame (origin O,
+// row-major R): cO = floor((O - lo) / cs), fO = fl((O - lo) - cO cs), R32 = fl(R),
+// shift = fl(-a R[0][x]), u = fl(R[0][x]).
+__host__ __device__ inline void frame_constants(BufDev& v, const double O[3], const double R[9], double a,
+                                                const double lo[3], double cs, int D) {
+  for (int x = 0; x < 3; ++x) {
+    v.cO[x] = 0;
+    v.fO[x] = 0.f;
+    if (x < D) {
+      const double t = SPHBUF_DSUB(O[x], lo[x]);
+      const double c = floor(SPHBUF_DDIV(t, cs));
+      v.cO[x] = (int)c;
+      v.fO[x] = (float)SPHBUF_DSUB(t, SPHBUF_DMUL(c, cs));
+    }
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) v.R[r][c] = (float)R[3 * r + c];
+  for (int x = 0; x < 3; ++x) {
+    v.shift[x] = x < D ? (float)SPHBUF_DMUL(-a, R[x]) : 0.f;
+    v.u[x] = x < D ? (float)R[x] : 0.f;
+  }
+}
+
+// Frame of the current step from the rotation state (module header order).
+__host__ __device__ inline void rotated_frame(const RotDev& q, double O[3], double R[9]) {
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      R[3 * r + c] = SPHBUF_DADD(SPHBUF_DADD(SPHBUF_DMUL(q.R0[3 * r], q.Q[3 * c]), SPHBUF_DMUL(q.R0[3 * r + 1], q.Q[3 * c + 1])),
+                                 SPHBUF_DMUL(q.R0[3 * r + 2], q.Q[3 * c + 2]));
+  const double d0 = SPHBUF_DSUB(q.O0[0], q.C[0]), d1 = SPHBUF_DSUB(q.O0[1], q.C[1]), d2 = SPHBUF_DSUB(q.O0[2], q.C[2]);
+  for (int x = 0; x < 3; ++x)
+    O[x] = SPHBUF_DADD(q.C[x], SPHBUF_DADD(SPHBUF_DADD(SPHBUF_DMUL(q.Q[3 * x], d0), SPHBUF_DMUL(q.Q[3 * x + 1], d1)),
+                                           SPHBUF_DMUL(q.Q[3 * x + 2], d2)));
+}
+
+// Q <- M Q (module header order).
+__host__ __device__ inline void advance_rotation(RotDev& q) {
+  double T[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      T[3 * r + c] = SPHBUF_DADD(SPHBUF_DADD(SPHBUF_DMUL(q.M[3 * r], q.Q[c]), SPHBUF_DMUL(q.M[3 * r + 1], q.Q[3 + c])),
+                                 SPHBUF_DMUL(q.M[3 * r + 2], q.Q[6 + c]));
+  for (int e = 0; e < 9; ++e) q.Q[e] = T[e];
+}
 
 struct Grid {
   int dim;
@@ -54,6 +130,7 @@ struct Grid {
 struct Phys {
   float h, inv_h, two_h_sq, alpha, rho0, c0, c0sq, eta, mass, dt, inv_sum_w0, w_self;
   double rho0_d, c0sq_d, dt_d;
+  double lo_d[3], cs_d;  // grid origin and cell size in FP64 (frames of rotating buffers)
   unsigned capacity;
   unsigned list_cap;
 };

@@ -28,7 +28,8 @@ struct DomainDev {
   Decision* inj;          // decisions of the current step, list_cap each
   Decision* del;
   InjRecord* inj_sorted;  // injections in (buffer, parent id) order
-  const BufDev* bufs;     // nbuf entries
+  const BufDev* bufs;     // nbuf entries (frame fields of rotating buffers rewritten per step)
+  RotDev* rot;            // kMaxBuffers entries: frame state of rotating buffers
   int nbuf;
   const int* relabel_ids; // buffers that relabel (outflow, bidirectional)
   int nrelabel;

@@ -107,7 +107,10 @@ __device__ __forceinline__ void stage(const DomainDev& d, Staged& sm, bool flag,
 
 // Algorithms 1-3 for particle i of B (test state p) against buffer k; the warp stages the
 // decisions.  (lin_c, c_c, cp_c): a cell, its coordinates and its cell part for buffer k,
-// used when the particle is still in that cell (the cell it was sorted into).
+// used when the particle is still in that cell (the cell it was sorted into).  A particle of
+// a rotating inflow buffer then turns with the buffer about its pivot (Sec. 5.3), after any
+// recycling: positions in the FP32 contract (offset from the pivot, rotated row by row, moved
+// by the difference), velocities rotated row by row.
 template <int D>
 __device__ __forceinline__ void decide(const DomainDev& d, Staged& sm, int k, unsigned i, const Cand& p, int lin_c,
                                        const int c_c[3], const float cp_c[3]) {
@@ -137,7 +140,8 @@ __device__ __forceinline__ void decide(const DomainDev& d, Staged& sm, int k, un
       if (b.kind == KIND_BIDIR) del = X[0] < -b.ha;
     }
   }
-  if (!__any_sync(kFull, inj || del)) return;
+  const bool rot = test && b.rotating;
+  if (!__any_sync(kFull, inj || del || rot)) return;
   Decision rec;
   rec.k = (unsigned)k;
   rec.idx = i;
@@ -150,22 +154,47 @@ __device__ __forceinline__ void decide(const DomainDev& d, Staged& sm, int k, un
     rec.v[x] = 0.f;
   }
   if (inj || del) rec.id = d.B.id[i];
-  if (inj) {
+  if (inj || rot) {
 #pragma unroll
     for (int x = 0; x < D; ++x) rec.v[x] = d.B.v[x][i];
-    rec.rho = d.B.rho[i];
   }
+  if (inj) rec.rho = d.B.rho[i];
   stage<D, true>(d, sm, inj, rec);
+  float fw[3] = {p.f[0], p.f[1], p.f[2]};
+  bool ok = true;
   if (inj) {
     // recycle the parent: r' - [a, 0, 0]^T mapped back, i.e. r - a u (after the record
     // captured the duplicate's state)
-    bool ok = true;
+#pragma unroll
+    for (int x = 0; x < D; ++x) ok &= move_fold(fw[x], c[x], b.shift[x], g.cs);
+  }
+  if (rot) {
+    float Dv[3] = {0.f, 0.f, 0.f}, Dn[3], vn[3];
+#pragma unroll
+    for (int x = 0; x < D; ++x)
+      Dv[x] = __fadd_rn(__fmul_rn(__int2float_rn(c[x] - b.cC[x]), g.cs), __fadd_rn(fw[x], -b.fC[x]));
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      float acc = __fmul_rn(b.M32[r][0], Dv[0]);
+      float vac = __fmul_rn(b.M32[r][0], rec.v[0]);
+      acc = __fadd_rn(acc, __fmul_rn(b.M32[r][1], Dv[1]));
+      vac = __fadd_rn(vac, __fmul_rn(b.M32[r][1], rec.v[1]));
+      if (D == 3) {
+        acc = __fadd_rn(acc, __fmul_rn(b.M32[r][2], Dv[2]));
+        vac = __fadd_rn(vac, __fmul_rn(b.M32[r][2], rec.v[2]));
+      }
+      Dn[r] = acc;
+      vn[r] = vac;
+    }
 #pragma unroll
     for (int x = 0; x < D; ++x) {
-      float fx = p.f[x];
-      ok &= move_fold(fx, c[x], b.shift[x], g.cs);
-      d.B.f[x][i] = fx;
+      ok &= move_fold(fw[x], c[x], __fadd_rn(Dn[x], -Dv[x]), g.cs);
+      d.B.v[x][i] = vn[x];
     }
+  }
+  if (inj || rot) {
+#pragma unroll
+    for (int x = 0; x < D; ++x) d.B.f[x][i] = fw[x];
     const bool inside = ok && c[0] >= 0 && c[0] < g.nx && c[1] >= 0 && c[1] < g.ny && c[2] >= 0 && c[2] < g.nz;
     if (inside) {
       d.B.cell[i] = (c[2] * g.ny + c[1]) * g.nx + c[0];
@@ -173,8 +202,8 @@ __device__ __forceinline__ void decide(const DomainDev& d, Staged& sm, int k, un
       d.B.label[i] = kDead;
       atomicAdd(&d.st->escaped_total, 1ull);
     }
-    if (!b.vel_bc) d.B.rho[i] = sm.rho_pb[k];  // Eq. (22)
   }
+  if (inj && !b.vel_bc) d.B.rho[i] = sm.rho_pb[k];  // Eq. (22)
   if (del) d.B.label[i] = kDead;
   stage<D, false>(d, sm, del, rec);
 }

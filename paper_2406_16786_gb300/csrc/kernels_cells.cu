@@ -320,7 +320,20 @@ __device__ __forceinline__ void finalize_body(const DomainDev& d, int count_step
   if (bid == 0 && threadIdx.x == 0) {
     st->n = d.cell_start[d.g.ncell];
     st->next_id += min(st->n_inj, d.P.list_cap);
-    if (count_step) st->step += 1;
+    if (count_step) {
+      st->step += 1;
+      // Sec. 5.3: re-establish the frames of rotating buffers for the next step (their
+      // particles turned in this step's buffer update)
+      for (int k = 0; k < d.nbuf; ++k) {
+        BufDev* b = const_cast<BufDev*>(d.bufs) + k;
+        if (!b->rotating) continue;
+        RotDev& q = d.rot[k];
+        advance_rotation(q);
+        double O[3], R[9];
+        rotated_frame(q, O, R);
+        frame_constants(*b, O, R, q.a, d.P.lo_d, d.P.cs_d, d.g.dim);
+      }
+    }
   }
   // (first particle, end, cell, buffer) of the candidate cell segments
   for (unsigned s = bid * blockDim.x + threadIdx.x; s < (unsigned)d.nseg; s += nblk * blockDim.x) {

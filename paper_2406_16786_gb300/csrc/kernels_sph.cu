@@ -288,6 +288,10 @@ __device__ __forceinline__ void neighbours_body(const DomainDev& d, unsigned bid
     const float cxf = pi.w;
     uint4* lst = reinterpret_cast<uint4*>(d.nb + (size_t)i * cap);
     ListTail t{0u, 0u, 0u, 0u, 0};
+    // x of particle i from its grid row's origin: enough for the inclusion test (its rounding,
+    // ~1e-7 of the row length, moves only pairs at q = 2 - O(1e-5), where W and dW vanish);
+    // the density and force passes recompute r_ij from the cell offsets
+    const float ox = pi.x + cxf * cs;
 #pragma unroll 1
     for (int wall = 0; wall < 2; ++wall) {
       const unsigned* start = wall ? d.W.start : d.cell_start;
@@ -309,7 +313,7 @@ __device__ __forceinline__ void neighbours_body(const DomainDev& d, unsigned bid
           unsigned j = __ldg(start + rb + x0);
           for (; j < j1; ++j) {
             const float4 p = __ldg(P4 + j);
-            const float rx = (pi.x - p.x) - (p.w - cxf) * cs;
+            const float rx = ox - (p.x + p.w * cs);
             const float ry = oy - p.y;
             const float rz = (D == 3) ? oz - p.z : 0.f;
             const float r2 = rx * rx + ry * ry + rz * rz;

@@ -199,7 +199,18 @@ class Domain:
         self._check(self.lib.sphbuf_add_inout_buffer(self.h, _ptr(o), _ptr(R), _ptr(e), int(spec.bc), ctypes.byref(prm),
                                                      ctypes.byref(k)), "add_inout_buffer")
         self.nbuf += 1
+        pivot = getattr(spec, "pivot", None)
+        if pivot is not None:
+            self.set_buffer_rotation(k.value, pivot, getattr(spec, "axis", None), float(getattr(spec, "omega", 0.0)))
         return k.value
+
+    def set_buffer_rotation(self, k: int, pivot, axis, omega: float):
+        """Time-varying frame of inflow buffer k (Sec. 5.3): turns by omega about the pivot."""
+        pv = np.zeros(3, dtype=np.float64)
+        pv[:len(pivot)] = np.asarray(pivot, dtype=np.float64)
+        ax = np.array([0.0, 0.0, 1.0]) if axis is None else np.ascontiguousarray(axis, dtype=np.float64)
+        self._check(self.lib.sphbuf_set_buffer_rotation(self.h, int(k), _ptr(pv), _ptr(ax), float(omega)),
+                    "set_buffer_rotation")
 
     def step(self, nsteps=1, phases=_ffi.STEP_DEFAULT):
         self._check(self.lib.sphbuf_step_phases(self.h, int(nsteps), int(phases)), "step")

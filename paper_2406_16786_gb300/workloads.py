@@ -60,6 +60,11 @@ class BufferSpec:
     p_amp: float = 0.0
     p_omega: float = 0.0
     p_phase: float = 0.0
+    # time-varying frame of an inflow buffer (Sec. 5.3): turned by omega per second about the
+    # pivot (about z in 2-D, about ``axis`` in 3-D); None = fixed frame
+    pivot: Optional[np.ndarray] = None
+    axis: Optional[np.ndarray] = None
+    omega: float = 0.0
 
 
 @dataclasses.dataclass
@@ -662,6 +667,81 @@ def config2(dp=0.005, **kw) -> Case:
     3 m at -15 deg; parabolic velocity inlet Umax = 1.5 (R = 0.5), pressure outlet p = 0, c0 = 15,
     nu = 1e-2; dp = 0.005 gives about 0.38 M fluid particles."""
     return bent_channel_case(dp=dp, name="cfg2_bent", **kw)
+
+
+def sprinkler_case(*, dim=2, dp=0.002, r_nozzle=0.1, width=0.04, umax=1.0, omega=2.0, theta0=0.0,
+                   axis=(0.0, 0.0, 1.0), domain_radius=0.3, ambient=False, c0=10.0, nu=1e-2, rho0=1000.0,
+                   h_over_dp=1.3, buffer_layers=4, seed=BASE_SEED + 53, name="sprinkler") -> Case:
+    """Rotating sprinkler (Sec. 5.3): a velocity-inlet nozzle that turns about a pivot.
+
+    The pivot is the origin; the nozzle box (``buffer_layers`` dp along its normal, ``width``
+    across) sits at distance ``r_nozzle`` along its own normal, a radial jet (the paper does
+    not fix the nozzle's orientation; reading), at the angle ``theta0`` (2-D) or perpendicular
+    to ``axis`` (3-D, square cross-section).  Its profile is U (1 - (Y'/R)^2), R = width/2 (the
+    paper's 2500 (0.02^2 - y'^2) is U = 1, R = 0.02); it turns at ``omega`` rad/s about the
+    z axis (2-D) or ``axis`` (3-D).  Fluid: the nozzle's lattice (its buffer particles, on the
+    profile) and, with ``ambient``, fluid at rest on a lattice outside the disc (ball) the
+    nozzle sweeps.  No walls; the grid covers ``domain_radius`` around the pivot.
+    """
+    rng = np.random.default_rng(seed)
+    a = buffer_layers * dp
+    half = 0.5 * width
+    if dim == 2:
+        e = np.array([math.cos(theta0), math.sin(theta0), 0.0])
+        R = frame_2d(theta0)
+    else:
+        ax = np.asarray(axis, dtype=np.float64)
+        ax = ax / np.linalg.norm(ax)
+        k = int(np.argmin(np.abs(ax)))
+        helper = np.zeros(3)
+        helper[k] = 1.0
+        e = helper - np.dot(helper, ax) * ax
+        e /= np.linalg.norm(e)
+        R = frame_3d(e, roll=float(rng.uniform(0.0, 2.0 * math.pi)))
+    origin = r_nozzle * e
+    # the nozzle's lattice in its own frame, rotated into place
+    nx = int(round(a / dp))
+    ny = int(round(width / dp))
+    lx = (np.arange(nx) + 0.5) * dp - 0.5 * a
+    ly = (np.arange(ny) + 0.5) * dp - half
+    if dim == 2:
+        X, Y = np.meshgrid(lx, ly, indexing="ij")
+        loc = np.stack([X.ravel(), Y.ravel(), np.zeros(X.size)], axis=1)
+    else:
+        X, Y, Z = np.meshgrid(lx, ly, ly, indexing="ij")
+        loc = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    glob = loc @ R + origin
+    rr = loc[:, 1] ** 2 + (loc[:, 2] ** 2 if dim == 3 else 0.0)
+    prof = umax * np.clip(1.0 - rr / half ** 2, 0.0, None)
+    fluid = glob[:, :dim]
+    vel = (prof[:, None] * e[None, :])[:, :dim]
+    if ambient:
+        reach = r_nozzle + 0.5 * a + 4 * dp
+        ext = domain_radius - 4 * dp
+        g1 = (np.arange(-int(ext / dp), int(ext / dp) + 1) + 0.5) * dp
+        grids = np.meshgrid(*([g1] * dim), indexing="ij")
+        P = np.stack([q.ravel() for q in grids], axis=1)
+        r = np.linalg.norm(P, axis=1)
+        P = P[(r > reach) & (r < ext)]
+        fluid = np.concatenate([fluid, P])
+        vel = np.concatenate([vel, np.zeros_like(P)])
+    fluid = fluid + rng.uniform(-0.01 * dp, 0.01 * dp, size=fluid.shape)
+    lo = np.zeros(3)
+    hi = np.zeros(3)
+    lo[:dim] = -domain_radius
+    hi[:dim] = domain_radius
+    if dim == 2:
+        lo[2], hi[2] = 0.0, 1.0
+    h = h_over_dp * dp
+    dt = min(0.25 * h / (c0 + umax), 0.125 * h * h / nu)
+    ext3 = np.array([a, width, width if dim == 3 else 0.0])
+    buf = BufferSpec(origin=origin, rotation=R, extent=ext3, bc=VELOCITY_INLET, umax=umax, half_width=half,
+                     pivot=np.zeros(3), axis=np.array([0.0, 0.0, 1.0]) if dim == 2 else np.asarray(axis, float),
+                     omega=omega)
+    n = fluid.shape[0]
+    return Case(name="%s%dd_dp%g_n%d" % (name, dim, dp, n), dim=dim, lo=lo, hi=hi, dp=dp, h_over_dp=h_over_dp,
+                rho0=rho0, c0=c0, nu=nu, dt=dt, fluid_pos=fluid, fluid_vel=vel, fluid_rho=np.full(n, rho0),
+                wall_pos=np.zeros((0, dim)), buffers=[buf], capacity=4 * n + 4096, steps=500)
 
 
 def config5(ndomains=64, n_lo=10_000, n_hi=500_000, seed=BASE_SEED + 5) -> List[Case]:

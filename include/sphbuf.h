@@ -159,6 +159,25 @@ sphbuf_status sphbuf_add_inout_buffer(sphbuf_domain_t d, const double origin[3],
 sphbuf_status sphbuf_set_buffer_rotation(sphbuf_domain_t d, int buffer_id, const double pivot[3],
                                          const double axis[3], double omega);
 
+/* RCR Windkessel outlet (Eq. (31), the aorta outlets of Sec. 6.2) for pressure buffer
+ * buffer_id: its boundary pressure is computed each step from the volume flux Q through the
+ * buffer instead of p_b(t).  Eq. (31) is taken as P = P_d + R_p Q with C dP_d/dt = Q - P_d / R_d
+ * (the same model), integrated explicitly once per step with the flux of the previous step:
+ * P_d(n) = P_d(n-1) + dt ((Q(n-1) - P_d(n-1) / R_d) / C) (n >= 1, FP64 in this order; P_d(0) =
+ * p_d0, Q(-1) = 0) and p_b(t_n) = P_d(n) + R_p Q(n-1).  Q is the flux the force pass measures:
+ * sum over the buffer's particles of (v . u) dp^dim / a, positive along u (outward for an
+ * outlet), m^dim/s.  Units SI: r_p, r_d in Pa s / m^dim, compliance in m^dim / Pa.  Errors:
+ * SPHBUF_ERR_INVALID_ARG (velocity buffer, r_p < 0, compliance or r_d <= 0, non-finite),
+ * SPHBUF_ERR_STATE (after the first step).  Only before the first step. */
+sphbuf_status sphbuf_set_windkessel(sphbuf_domain_t d, int buffer_id, double r_p, double compliance,
+                                    double r_d, double p_d0);
+
+/* Boundary pressure of buffer buffer_id for the current (last begun) step: p_b (FP64), the
+ * Windkessel distal pressure P_d (0 without a Windkessel) and the flux Q of the step before,
+ * which p_b was computed from.  Any pointer may be NULL.  Synchronises the domain's stream. */
+sphbuf_status sphbuf_read_boundary_pressure(sphbuf_domain_t d, int buffer_id, double *p_b, double *p_d,
+                                            double *q_prev);
+
 /* Rodrigues frame of Eqs. (12)-(14): R with R n = e_x (reading: I - S sin + S^2 (1 - cos),
  * the transpose of the printed formula, so that X' = R (X - O') has X' along n), followed by
  * a roll about X': R <- Rx(roll) R.  n need not be unit length. */

@@ -75,6 +75,24 @@ class Buffer:
         self.omega = float(getattr(spec, "omega", 0.0))
         if self.pivot is not None and self.bc not in INFLOW:
             raise ValueError("only inflow buffers may have a time-varying frame")
+        # RCR Windkessel (Eq. (31)): p_b from the flux instead of p_b(t); see windkessel_step
+        wk_c = getattr(spec, "wk_c", None)
+        self.wk = wk_c is not None
+        if self.wk and self.bc not in PRESSURE_BC:
+            raise ValueError("a Windkessel drives a pressure buffer")
+        self.wk_rp = float(getattr(spec, "wk_rp", 0.0))
+        self.wk_c = float(wk_c) if self.wk else 0.0
+        self.wk_rd = float(getattr(spec, "wk_rd", 0.0))
+        self.wk_pd = float(getattr(spec, "wk_pd0", 0.0))
+        self.pb_now = self.wk_pd  # p_b of the current step (Windkessel buffers)
+
+    def windkessel_step(self, q_prev: float, dt: float, first: bool):
+        """Eq. (31) as P = P_d + R_p Q, C dP_d/dt = Q - P_d / R_d (the same RCR model), one
+        explicit Euler step with the flux of the previous step (reading):
+        P_d <- P_d + dt ((Q - P_d / R_d) / C) (not at the first step); p_b = P_d + R_p Q."""
+        if not first:
+            self.wk_pd = self.wk_pd + dt * ((q_prev - self.wk_pd / self.wk_rd) / self.wk_c)
+        self.pb_now = self.wk_pd + self.wk_rp * q_prev
 
     def set_frame(self, R3, origin):
         """Re-establish the local frame (Sec. 5.3): new rotation and origin."""
@@ -84,7 +102,14 @@ class Buffer:
         self.u = frames.normal(self.R)
 
     def p_b(self, t: float) -> float:
+        if self.wk:
+            return self.pb_now
         return self.p_b0 + self.p_amp * math.sin(self.p_omega * t + self.p_phase)
+
+    def flux(self, vel, label, dp: float) -> float:
+        """Volume flux through the buffer: sum over its particles of (v . u) dp^d / a."""
+        m = label == self.label
+        return float(np.sum(vel[m] @ self.u) * dp ** self.dim / self.extent[0])
 
     def local(self, pos: np.ndarray) -> np.ndarray:
         return frames.to_local(self.R, self.origin, pos)
@@ -204,6 +229,8 @@ class OracleSim:
                 mf.advance()
             self.buffers[k].set_frame(*mf.frame())
         K = len(self.buffers)
+        self.flux = np.zeros(K)  # volume flux of the last step per buffer (0 before the first)
+        self.dp = float(case.dp)
         self.injected = np.zeros(K, dtype=np.int64)
         self.deleted = np.zeros(K, dtype=np.int64)
         self.escaped = 0
@@ -279,6 +306,8 @@ class OracleSim:
             else:
                 un = v[m] @ b.u
                 v[m] = un[:, None] * b.u[None, :]
+        for b in self.buffers:
+            self.flux[b.k] = b.flux(v, self.label, self.dp)
         self.acc = acc
         self.vel = v
         self.pos = self.pos + v * P.dt
@@ -339,8 +368,16 @@ class OracleSim:
             self.escaped += int((~ok).sum())
             self._take(np.nonzero(ok)[0])
 
+    def begin_step(self):
+        """Boundary pressures of the step: Windkessel buffers from the last step's flux."""
+        for b in self.buffers:
+            if b.wk:
+                b.windkessel_step(float(self.flux[b.k]), self.P.dt, self.step_index == 0)
+        self.flux[:] = 0.0
+
     def step(self, nsteps=1, physics=True, buffer=True):
         for _ in range(nsteps):
+            self.begin_step()
             if physics:
                 self.physics()
             else:

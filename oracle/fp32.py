@@ -289,6 +289,10 @@ class Fp32Sim:
 
     def step(self, nsteps=1, buffer=True):
         for _ in range(nsteps):
+            # kinematic steps measure no flux: Windkessel buffers see Q = 0
+            for b in self.bufs64:
+                if b.wk:
+                    b.windkessel_step(0.0, self.dt, self.step_index == 0)
             self.drift()
             if buffer:
                 self.buffer_update()

@@ -26,6 +26,7 @@ struct BufHost {
   sphbuf_bc_params prm;
   bool rotating = false;
   RotDev rot{};
+  double wk_pd0 = 0;  // initial Windkessel distal pressure
   double r_min = 0, r_max = 0;  // distances from the pivot swept by the dilated box
 };
 
@@ -204,6 +205,11 @@ bool swept_overlaps_box(int dim, const BufHost& b, const double O[3], const doub
 sphbuf_status upload_buffers(sphbuf_domain* d) {
   CK(cudaMemcpy(const_cast<BufDev*>(d->dev.bufs), d->bufs_dev.data(), d->bufs_dev.size() * sizeof(BufDev),
                 cudaMemcpyHostToDevice));
+  std::vector<double> pd(d->bufs.size(), 0.0);
+  for (size_t k = 0; k < d->bufs.size(); ++k) pd[k] = d->bufs[k].wk_pd0;
+  if (!pd.empty())
+    CK(cudaMemcpy(reinterpret_cast<char*>(d->dev.st) + offsetof(StepState, wk_pd), pd.data(), pd.size() * sizeof(double),
+                  cudaMemcpyHostToDevice));
   std::vector<RotDev> rot(d->bufs.size());
   for (size_t k = 0; k < d->bufs.size(); ++k) rot[k] = d->bufs[k].rot;
   if (!rot.empty()) CK(cudaMemcpy(d->dev.rot, rot.data(), rot.size() * sizeof(RotDev), cudaMemcpyHostToDevice));
@@ -896,6 +902,36 @@ sphbuf_status sphbuf_set_buffer_rotation(sphbuf_domain_t d, int buffer_id, const
   return SPHBUF_OK;
 }
 
+sphbuf_status sphbuf_set_windkessel(sphbuf_domain_t d, int buffer_id, double r_p, double compliance, double r_d,
+                                    double p_d0) {
+  if (!d) return SPHBUF_ERR_INVALID_ARG;
+  if (d->stepped || d->committed) return fail(d, SPHBUF_ERR_STATE, "the Windkessel must be set before the first step");
+  if (buffer_id < 0 || buffer_id >= (int)d->bufs.size()) return fail(d, SPHBUF_ERR_INVALID_ARG, "no such buffer");
+  BufDev& v = d->bufs_dev[buffer_id];
+  if (v.vel_bc) return fail(d, SPHBUF_ERR_INVALID_ARG, "a Windkessel drives a pressure buffer");
+  if (!(r_p >= 0) || !(compliance > 0) || !(r_d > 0) || !std::isfinite(r_p) || !std::isfinite(compliance) ||
+      !std::isfinite(r_d) || !std::isfinite(p_d0))
+    return fail(d, SPHBUF_ERR_INVALID_ARG, "Windkessel parameters: R_p >= 0, C > 0, R_d > 0, finite");
+  v.wk = 1;
+  v.wk_rp = r_p;
+  v.wk_c = compliance;
+  v.wk_rd = r_d;
+  d->bufs[buffer_id].wk_pd0 = p_d0;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_read_boundary_pressure(sphbuf_domain_t d, int buffer_id, double* p_b, double* p_d, double* q_prev) {
+  if (!d) return SPHBUF_ERR_INVALID_ARG;
+  if (buffer_id < 0 || buffer_id >= (int)d->bufs.size()) return fail(d, SPHBUF_ERR_INVALID_ARG, "no such buffer");
+  StepState st;
+  sphbuf_status s = read_state(d, &st);
+  if (s != SPHBUF_OK) return s;
+  if (p_b) *p_b = st.pb_d[buffer_id];
+  if (p_d) *p_d = st.wk_pd[buffer_id];
+  if (q_prev) *q_prev = st.flux_last[buffer_id];
+  return SPHBUF_OK;
+}
+
 sphbuf_status sphbuf_step_phases(sphbuf_domain_t d, int nsteps, unsigned phases) {
   if (!d || nsteps < 0) return SPHBUF_ERR_INVALID_ARG;
   const bool phys = phases & SPHBUF_PHASE_PHYSICS, kin = phases & SPHBUF_PHASE_KINEMATIC;
@@ -1049,7 +1085,7 @@ sphbuf_status sphbuf_read_counters(sphbuf_domain_t d, int k, uint64_t* injected,
   if (deleted) *deleted = st.deleted[k];
   if (mass_in) *mass_in = (double)st.injected[k] * d->mass_d;
   if (mass_out) *mass_out = (double)st.deleted[k] * d->mass_d;
-  if (flux_q) *flux_q = st.flux[k];
+  if (flux_q) *flux_q = (double)st.flux_fx[k] * kFluxUnit;
   return SPHBUF_OK;
 }
 

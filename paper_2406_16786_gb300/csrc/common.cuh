@@ -48,7 +48,15 @@ struct BufDev {
   int cC[3];
   float fC[3];
   float M32[3][3];
+  // RCR Windkessel pressure (Eq. (31)) instead of p_b(t): parameters R_p, C, R_d
+  int wk;
+  double wk_rp, wk_c, wk_rd;
 };
+
+// Volume fluxes are summed as 64-bit fixed-point integers (unit 2^-50 m^d/s): integer
+// atomics make the sum independent of the order of the additions.
+constexpr double kFluxScale = 1125899906842624.0;     // 2^50
+constexpr double kFluxUnit = 1.0 / 1125899906842624.0;  // 2^-50
 
 // FP64 state of a rotating buffer's frame (Sec. 5.3): Q_n = M Q_{n-1}, R_n = R_0 Q_n^T,
 // O'_n = C + Q_n (O'_0 - C).
@@ -150,7 +158,10 @@ struct StepState {
   unsigned long long deleted[kMaxBuffers];
   float pb[kMaxBuffers];      // p_b(t_n)
   float rho_pb[kMaxBuffers];  // fl32(rho0 + p_b(t_n) / c0^2)
-  double flux[kMaxBuffers];   // volume flux of the last step
+  long long flux_fx[kMaxBuffers];  // volume flux through buffer k in the current step (fixed point)
+  double flux_last[kMaxBuffers];   // flux of the previous step (the one p_b(t_n) used)
+  double pb_d[kMaxBuffers];        // p_b(t_n) in FP64
+  double wk_pd[kMaxBuffers];       // Windkessel distal pressure P_d (Eq. (31) split)
 };
 
 struct Particles {

@@ -32,10 +32,24 @@ __device__ __forceinline__ void begin_step(const DomainDev& d) {
   const double t = (double)st->step * d.P.dt_d;
   for (int k = 0; k < d.nbuf; ++k) {
     const BufDev& b = d.bufs[k];
-    const double pb = b.p_b0 + b.p_amp * sin(b.p_omega * t + b.p_phase);
+    const double q = (double)st->flux_fx[k] * kFluxUnit;  // flux of the previous step
+    st->flux_last[k] = q;
+    st->flux_fx[k] = 0;
+    double pb;
+    if (b.wk) {
+      // Eq. (31) as P = P_d + R_p Q, C dP_d/dt = Q - P_d / R_d; explicit Euler with the
+      // flux of the previous step: P_d <- P_d + dt ((Q - P_d / R_d) / C)
+      double pd = st->wk_pd[k];
+      if (st->step > 0)
+        pd = SPHBUF_DADD(pd, SPHBUF_DMUL(d.P.dt_d, SPHBUF_DDIV(SPHBUF_DSUB(q, SPHBUF_DDIV(pd, b.wk_rd)), b.wk_c)));
+      st->wk_pd[k] = pd;
+      pb = SPHBUF_DADD(pd, SPHBUF_DMUL(b.wk_rp, q));
+    } else {
+      pb = b.p_b0 + b.p_amp * sin(b.p_omega * t + b.p_phase);
+    }
+    st->pb_d[k] = pb;
     st->pb[k] = (float)pb;
     st->rho_pb[k] = (float)(d.P.rho0_d + pb / d.P.c0sq_d);
-    st->flux[k] = 0.0;
   }
 }
 
@@ -176,7 +190,8 @@ __device__ __forceinline__ void finish_force(const DomainDev& d, unsigned i, con
     }
     float vn = v[0] * b.u[0] + v[1] * b.u[1];
     if (D == 3) vn += v[2] * b.u[2];
-    atomicAdd(&d.st->flux[k], (double)(vn * b.flux_scale));
+    atomicAdd(reinterpret_cast<unsigned long long*>(&d.st->flux_fx[k]),
+              (unsigned long long)__double2ll_rn((double)(vn * b.flux_scale) * kFluxScale));
   }
   drift_store<D>(d, i, c, fi, v, rho_i, lab);
 }

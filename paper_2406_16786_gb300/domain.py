@@ -199,10 +199,24 @@ class Domain:
         self._check(self.lib.sphbuf_add_inout_buffer(self.h, _ptr(o), _ptr(R), _ptr(e), int(spec.bc), ctypes.byref(prm),
                                                      ctypes.byref(k)), "add_inout_buffer")
         self.nbuf += 1
+        if getattr(spec, "wk_c", None) is not None:
+            self.set_windkessel(k.value, spec.wk_rp, spec.wk_c, spec.wk_rd, getattr(spec, "wk_pd0", 0.0))
         pivot = getattr(spec, "pivot", None)
         if pivot is not None:
             self.set_buffer_rotation(k.value, pivot, getattr(spec, "axis", None), float(getattr(spec, "omega", 0.0)))
         return k.value
+
+    def set_windkessel(self, k: int, r_p: float, compliance: float, r_d: float, p_d0: float = 0.0):
+        """RCR Windkessel boundary pressure (Eq. (31)) for pressure buffer k."""
+        self._check(self.lib.sphbuf_set_windkessel(self.h, int(k), float(r_p), float(compliance), float(r_d),
+                                                   float(p_d0)), "set_windkessel")
+
+    def boundary_pressure(self, k: int):
+        """(p_b of the last begun step, Windkessel P_d, flux Q of the step before)."""
+        pb, pd, q = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.sphbuf_read_boundary_pressure(self.h, int(k), ctypes.byref(pb), ctypes.byref(pd),
+                                                           ctypes.byref(q)), "read_boundary_pressure")
+        return pb.value, pd.value, q.value
 
     def set_buffer_rotation(self, k: int, pivot, axis, omega: float):
         """Time-varying frame of inflow buffer k (Sec. 5.3): turns by omega about the pivot."""

@@ -65,6 +65,12 @@ class BufferSpec:
     pivot: Optional[np.ndarray] = None
     axis: Optional[np.ndarray] = None
     omega: float = 0.0
+    # RCR Windkessel outlet (Eq. (31)) of a pressure buffer: R_p, C, R_d (SI), initial P_d;
+    # wk_c None = p_b(t) as above
+    wk_rp: float = 0.0
+    wk_c: Optional[float] = None
+    wk_rd: float = 0.0
+    wk_pd0: float = 0.0
 
 
 @dataclasses.dataclass

@@ -159,6 +159,25 @@ sphbuf_status sphbuf_add_inout_buffer(sphbuf_domain_t d, const double origin[3],
 sphbuf_status sphbuf_set_buffer_rotation(sphbuf_domain_t d, int buffer_id, const double pivot[3],
                                          const double axis[3], double omega);
 
+/* Background pressure of the equation of state: p = c0^2 (rho - rho0) + p_bg (Eq. (3) plus
+ * a constant, default 0).  Only pressure differences and the open-boundary term of Eq. (18)
+ * act on the flow, so a p_bg above the largest expected suction keeps every pressure
+ * positive and avoids the tensile instability of plain WCSPH where the gauge pressure goes
+ * negative (the regularisation the paper obtains from its transport-velocity formulation,
+ * Eq. (10)).  Prescribed buffer pressures p_b are absolute (include p_bg); a recycled
+ * pressure-buffer particle gets rho = rho0 + (p_b - p_bg) / c0^2 (Eq. (22)).  Errors:
+ * SPHBUF_ERR_INVALID_ARG (non-finite), SPHBUF_ERR_STATE (after the first step). */
+sphbuf_status sphbuf_set_background_pressure(sphbuf_domain_t d, double p_bg);
+
+/* Transport-velocity formulation (Eq. (10)): fluid particles (label 0) are advected with
+ * v - dt p_max sum_j 2 m/(rho_i rho_j) dW/dr_ij e_ij instead of v, p_max = lambda rho0 v_max^2
+ * with v_max the largest particle speed of the previous step's force pass (0 at the first
+ * step); their momentum velocity stays v.  The buffer particles (the in-/outlet layers) are
+ * advected with v.  lambda = 0 (the default) turns it off; the paper takes 5 to 10.
+ * Errors: SPHBUF_ERR_INVALID_ARG (negative or non-finite), SPHBUF_ERR_STATE (after the first
+ * step). */
+sphbuf_status sphbuf_set_transport_velocity(sphbuf_domain_t d, double lambda);
+
 /* RCR Windkessel outlet (Eq. (31), the aorta outlets of Sec. 6.2) for pressure buffer
  * buffer_id: its boundary pressure is computed each step from the volume flux Q through the
  * buffer instead of p_b(t).  Eq. (31) is taken as P = P_d + R_p Q with C dP_d/dt = Q - P_d / R_d

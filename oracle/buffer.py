@@ -201,7 +201,9 @@ class OracleSim:
     def __init__(self, case, pos=None, vel=None, rho=None, ids=None, labels=None, next_id=None,
                  step_index=0):
         self.dim = int(case.dim)
-        self.P = sph.make_params(case.dim, case.dp, case.h_over_dp, case.rho0, case.c0, case.nu, case.dt)
+        self.P = sph.make_params(case.dim, case.dp, case.h_over_dp, case.rho0, case.c0, case.nu, case.dt,
+                                 getattr(case, "p_bg", 0.0), getattr(case, "tvf_lambda", 0.0))
+        self.vmax = 0.0  # largest particle speed after the last force pass (Eq. (10)'s v_max)
         self.lo = np.asarray(case.lo, dtype=np.float64)
         self.hi = np.asarray(case.hi, dtype=np.float64)
         self.cs = 2.0 * (float(case.h_over_dp) * float(case.dp))
@@ -309,8 +311,18 @@ class OracleSim:
         for b in self.buffers:
             self.flux[b.k] = b.flux(v, self.label, self.dp)
         self.acc = acc
+        adv = v
+        if P.tvf_lambda > 0.0:
+            # Eq. (10): advect the fluid away from the in-/outlets with the transport velocity
+            # v - dt p_max sum_j 2 m/(rho_i rho_j) dW/dr e_ij, p_max = lambda rho0 v_max^2 with
+            # v_max of the previous step; the buffer particles (the boundary layers at the in-/
+            # outlets, reading A23) keep v
+            p_max = P.tvf_lambda * P.rho0 * self.vmax * self.vmax
+            shift = P.dt * p_max * sph.transport_sum(P, rho_new, ff, fw)
+            adv = np.where((self.label == 0)[:, None], v - shift, v)
+        self.vmax = float(np.linalg.norm(v, axis=1).max()) if v.shape[0] else 0.0
         self.vel = v
-        self.pos = self.pos + v * P.dt
+        self.pos = self.pos + adv * P.dt
         self.rho = rho_new
 
     def kinematic(self):
@@ -334,7 +346,7 @@ class OracleSim:
             self.last_inj.append((k, int(self.id[i]), nid))
             self.pos[i] = self.pos[i] - b.extent[0] * b.u
             if b.bc in PRESSURE_BC:
-                self.rho[i] = self.P.rho0 + b.p_b(t) / (self.P.c0 * self.P.c0)
+                self.rho[i] = self.P.rho0 + (b.p_b(t) - self.P.p_bg) / (self.P.c0 * self.P.c0)
             self.injected[k] += 1
         self.next_id += len(inj)
         self.last_del = [(k, int(self.id[i])) for k, i in dels]

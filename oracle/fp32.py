@@ -158,6 +158,7 @@ class Fp32Sim:
         self.dt32 = F32(case.dt)
         self.rho0 = float(case.rho0)
         self.c0 = float(case.c0)
+        self.p_bg = float(getattr(case, "p_bg", 0.0))
         self.c = self.g.coords(cell)
         self.f = np.array(frac, dtype=F32)[:, :d].copy()
         self.vel = np.array(vel, dtype=F32)[:, :d].copy()
@@ -256,7 +257,7 @@ class Fp32Sim:
             for k, i in inj:
                 b64 = self.bufs64[k]
                 if b64.bc in B.PRESSURE_BC:
-                    self.rho[i] = F32(self.rho0 + b64.p_b(t) / (self.c0 * self.c0))
+                    self.rho[i] = F32(self.rho0 + (b64.p_b(t) - self.p_bg) / (self.c0 * self.c0))
                 self.injected[k] += 1
             self.next_id += n_new
         self.last_del = [(k, int(self.id[i])) for k, i in dels]

@@ -40,6 +40,8 @@ class Params:
     c0: float
     nu: float
     dt: float
+    p_bg: float = 0.0  # background pressure of the EoS (reading A22; 0 = Eq. (3) as printed)
+    tvf_lambda: float = 0.0  # transport velocity, Eq. (10): p_max = lambda rho0 v_max^2 (0 = off)
 
     @property
     def eta(self) -> float:
@@ -54,14 +56,16 @@ class Params:
         return kernel.lattice_sum_w0(self.dim, self.dp, self.h)
 
 
-def make_params(dim, dp, h_over_dp, rho0, c0, nu, dt) -> Params:
+def make_params(dim, dp, h_over_dp, rho0, c0, nu, dt, p_bg=0.0, tvf_lambda=0.0) -> Params:
     return Params(dim=int(dim), dp=float(dp), h=float(h_over_dp) * float(dp), rho0=float(rho0),
-                  c0=float(c0), nu=float(nu), dt=float(dt))
+                  c0=float(c0), nu=float(nu), dt=float(dt), p_bg=float(p_bg), tvf_lambda=float(tvf_lambda))
 
 
 def eos(rho, P: Params):
-    """Eq. (3): p = c0^2 (rho - rho0)."""
-    return P.c0 * P.c0 * (np.asarray(rho) - P.rho0)
+    """Eq. (3): p = c0^2 (rho - rho0), plus the constant background pressure p_bg (reading
+    A22: keeps the pressure positive where the flow would put it below zero; only pressure
+    differences and the open-boundary term of Eq. (18), which carries p_bg in p_b, act)."""
+    return P.c0 * P.c0 * (np.asarray(rho) - P.rho0) + P.p_bg
 
 
 @dataclasses.dataclass
@@ -156,6 +160,23 @@ def _riemann_p_star(vi, vj, rho_i, rho_j, p_i, p_j, e, c0):
     UR = -np.sum(vj * e, axis=1)
     beta = np.minimum(3.0 * np.maximum(UL - UR, 0.0), c0)
     return 0.5 * (p_i + p_j) + 0.5 * beta * 0.5 * (rho_i + rho_j) * (UL - UR)
+
+
+def transport_sum(P: Params, rho, ff: Pairs, fw: Pairs) -> np.ndarray:
+    """The sum of Eq. (10): sum_j 2 m_j / (rho_i rho_j) dW_ij/dr_ij e_ij (fluid and wall
+    neighbours; a wall neighbour takes rho_j = rho_i as in the force)."""
+    n = rho.shape[0]
+    d = ff.rij.shape[1] if ff.i.size else fw.rij.shape[1]
+    out = np.zeros((n, d))
+    for pairs, wall in ((ff, False), (fw, True)):
+        if pairs.i.size == 0:
+            continue
+        i = pairs.i
+        e = pairs.rij / pairs.r[:, None]
+        rho_j = rho[i] if wall else rho[pairs.j]
+        coef = 2.0 * P.mass / (rho[i] * rho_j) * kernel.dW(pairs.r, P.h, P.dim)
+        out += _scatter(i, coef[:, None] * e, n)
+    return out
 
 
 def acceleration(P: Params, vel, rho, p_bc, ff: Pairs, fw: Pairs) -> np.ndarray:

@@ -902,6 +902,23 @@ sphbuf_status sphbuf_set_buffer_rotation(sphbuf_domain_t d, int buffer_id, const
   return SPHBUF_OK;
 }
 
+sphbuf_status sphbuf_set_background_pressure(sphbuf_domain_t d, double p_bg) {
+  if (!d) return SPHBUF_ERR_INVALID_ARG;
+  if (d->stepped || d->committed) return fail(d, SPHBUF_ERR_STATE, "the background pressure must be set before the first step");
+  if (!std::isfinite(p_bg)) return fail(d, SPHBUF_ERR_INVALID_ARG, "background pressure must be finite");
+  d->dev.P.p_bg = (float)p_bg;
+  d->dev.P.p_bg_d = p_bg;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_set_transport_velocity(sphbuf_domain_t d, double lambda) {
+  if (!d) return SPHBUF_ERR_INVALID_ARG;
+  if (d->stepped || d->committed) return fail(d, SPHBUF_ERR_STATE, "the transport velocity must be set before the first step");
+  if (!(lambda >= 0) || !std::isfinite(lambda)) return fail(d, SPHBUF_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+  d->dev.P.tvf_lambda = (float)lambda;
+  return SPHBUF_OK;
+}
+
 sphbuf_status sphbuf_set_windkessel(sphbuf_domain_t d, int buffer_id, double r_p, double compliance, double r_d,
                                     double p_d0) {
   if (!d) return SPHBUF_ERR_INVALID_ARG;
@@ -1152,6 +1169,7 @@ sphbuf_status sphbuf_read_phase_times(sphbuf_domain_t d, double ms[5], uint64_t*
 // ---------------------------------------------------------------- batched domains
 struct sphbuf_batch {
   std::vector<sphbuf_domain*> doms;
+  bool tvf = false;  // some domain advects with the transport velocity (Eq. (10))
   std::vector<uint64_t> n0;  // particles per domain when the batch was made (block shares)
   int dim = 0;
   int sm_count = 1;
@@ -1238,7 +1256,7 @@ static int batch_launch(sphbuf_batch* b, Kern k) {
     case K_DENSITY_DEFER:
     case K_FORCE:
     case K_DRIFT:
-      return launch_batch_sph(k, b->dim, bd, n, b->stream);
+      return launch_batch_sph(k, b->dim, bd, n, b->stream, b->tvf);
     case K_BUFFER:
     case K_BUFFER_FULL:
       return launch_batch_buffer(k, b->dim, bd, n, b->stream);
@@ -1352,6 +1370,7 @@ sphbuf_status sphbuf_batch_create(sphbuf_domain_t* domains, int n, void* cuda_st
     }
     b->doms.push_back(d);
     b->n0.push_back(st.n);
+    if (d->dev.P.tvf_lambda > 0.f) b->tvf = true;
   }
   b->sm_count = b->doms[0]->dev.sm_count;
   if (cuda_stream) {

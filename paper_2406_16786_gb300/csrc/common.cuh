@@ -137,7 +137,9 @@ struct Grid {
 
 struct Phys {
   float h, inv_h, two_h_sq, alpha, rho0, c0, c0sq, eta, mass, dt, inv_sum_w0, w_self;
-  double rho0_d, c0sq_d, dt_d;
+  float p_bg;  // background pressure of the EoS: p = c0^2 (rho - rho0) + p_bg
+  float tvf_lambda;  // transport velocity (Eq. (10)): p_max = lambda rho0 v_max^2; 0 = off
+  double rho0_d, c0sq_d, dt_d, p_bg_d;
   double lo_d[3], cs_d;  // grid origin and cell size in FP64 (frames of rotating buffers)
   unsigned capacity;
   unsigned list_cap;
@@ -162,6 +164,8 @@ struct StepState {
   double flux_last[kMaxBuffers];   // flux of the previous step (the one p_b(t_n) used)
   double pb_d[kMaxBuffers];        // p_b(t_n) in FP64
   double wk_pd[kMaxBuffers];       // Windkessel distal pressure P_d (Eq. (31) split)
+  unsigned vmax_bits;              // largest particle speed of the current force pass (float bits)
+  float p_max;                     // Eq. (10) background pressure of the current step
 };
 
 struct Particles {

@@ -77,7 +77,7 @@ __device__ __forceinline__ void load_domain(DomainDev& dst, const DomainDev* src
   __syncthreads();
 }
 
-int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s);
+int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s, bool tvf);
 int launch_batch_buffer(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s);
 int launch_batch_cells(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s);
 int batch_threads(Kern k);  // threads per block of each batched kernel

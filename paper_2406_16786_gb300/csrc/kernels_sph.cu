@@ -29,6 +29,10 @@ __device__ __forceinline__ void begin_step(const DomainDev& d) {
   st->n_inj = 0;
   st->n_del = 0;
   st->n_defer = 0;
+  // Eq. (10): p_max = lambda rho0 v_max^2 with v_max of the last force pass (0 at the start)
+  const double vmax = (double)__uint_as_float(st->vmax_bits);
+  st->p_max = (float)((double)d.P.tvf_lambda * d.P.rho0_d * vmax * vmax);
+  st->vmax_bits = 0u;
   const double t = (double)st->step * d.P.dt_d;
   for (int k = 0; k < d.nbuf; ++k) {
     const BufDev& b = d.bufs[k];
@@ -49,7 +53,7 @@ __device__ __forceinline__ void begin_step(const DomainDev& d) {
     }
     st->pb_d[k] = pb;
     st->pb[k] = (float)pb;
-    st->rho_pb[k] = (float)(d.P.rho0_d + pb / d.P.c0sq_d);
+    st->rho_pb[k] = (float)(d.P.rho0_d + (pb - d.P.p_bg_d) / d.P.c0sq_d);
   }
 }
 
@@ -68,17 +72,19 @@ __device__ __forceinline__ float density_term(const Phys& P, bool buffer_i, bool
     p_j = p_i;
   } else {
     vx = vi[0] - vj[0], vy = vi[1] - vj[1], vz = vi[2] - vj[2];
-    p_j = P.c0sq * (rho_j - P.rho0);
+    p_j = P.c0sq * (rho_j - P.rho0) + P.p_bg;
   }
   const float vij_e = (vx * rx + vy * ry + vz * rz) * inv_r;
   const float term = 0.5f * vij_e + (p_i - p_j) / ((rho_i + rho_j) * P.c0);
   return P.mass / rho_j * term * kernel_dw(r * P.inv_h, P);
 }
 
-// Eq. (5) / (18) pair term added to a.  pb2 = 2 p_b (0 for non-buffer particles).
+// Eq. (5) / (18) pair term added to a.  pb2 = 2 p_b (0 for non-buffer particles).  With TVF
+// the pair's term of Eq. (10)'s sum, 2 m/(rho_i rho_j) dW/dr e_ij, is added to tb.
+template <bool TVF>
 __device__ __forceinline__ void force_term(const Phys& P, bool wall, float rx, float ry, float rz, float r2,
                                            const float vi[3], float rho_i, float p_i, float pb2, const float vj[3],
-                                           float rho_j, float a[3]) {
+                                           float rho_j, float a[3], float tb[3]) {
   const float r = sqrtf(r2), inv_r = 1.f / r;
   float vx, vy, vz, p_j;
   if (wall) {
@@ -88,7 +94,7 @@ __device__ __forceinline__ void force_term(const Phys& P, bool wall, float rx, f
     p_j = p_i;
   } else {
     vx = vi[0] - vj[0], vy = vi[1] - vj[1], vz = vi[2] - vj[2];
-    p_j = P.c0sq * (rho_j - P.rho0);
+    p_j = P.c0sq * (rho_j - P.rho0) + P.p_bg;
   }
   const float dU = -(vx * rx + vy * ry + vz * rz) * inv_r;  // U_L - U_R
   const float beta = fminf(3.f * fmaxf(dU, 0.f), P.c0);
@@ -99,6 +105,12 @@ __device__ __forceinline__ void force_term(const Phys& P, bool wall, float rx, f
   a[0] += ce * rx + cv * vx;
   a[1] += ce * ry + cv * vy;
   a[2] += ce * rz + cv * vz;
+  if (TVF) {
+    const float ct = 2.f * m_rr * inv_r;
+    tb[0] += ct * rx;
+    tb[1] += ct * ry;
+    tb[2] += ct * rz;
+  }
 }
 
 // Calls fn(wall, j, rx, ry, rz) for every particle of the 3^d cells around cell c (global
@@ -135,13 +147,13 @@ __device__ __forceinline__ void for_each_near(const DomainDev& d, const int c[3]
 // Drift + fold + escape check of the force/drift epilogue; writes B[i].
 template <int D>
 __device__ __forceinline__ void drift_store(const DomainDev& d, unsigned i, const int c[3], const float fi[3],
-                                            const float v[3], float rho, uint8_t lab) {
+                                            const float v[3], const float adv[3], float rho, uint8_t lab) {
   const Grid& g = d.g;
   int cn[3] = {c[0], c[1], c[2]};
   float fn[3] = {fi[0], fi[1], fi[2]};
   bool finite = true;
 #pragma unroll
-  for (int x = 0; x < D; ++x) finite &= move_fold(fn[x], cn[x], __fmul_rn(v[x], d.P.dt), g.cs);
+  for (int x = 0; x < D; ++x) finite &= move_fold(fn[x], cn[x], __fmul_rn(adv[x], d.P.dt), g.cs);
   bool inside = cn[0] >= 0 && cn[0] < g.nx && cn[1] >= 0 && cn[1] < g.ny && cn[2] >= 0 && cn[2] < g.nz;
   if (!finite) {
     latch(d.st, 6 /* SPHBUF_ERR_NAN */);
@@ -163,10 +175,13 @@ __device__ __forceinline__ void drift_store(const DomainDev& d, unsigned i, cons
   d.B.label[i] = lab;
 }
 
-// Kick, boundary velocity, flux, drift for centre particle i with acceleration a.
-template <int D>
+// Kick, boundary velocity, flux, drift for centre particle i with acceleration a.  With TVF
+// (Eq. (10)) a fluid particle (label 0) drifts with v - dt p_max tb, the buffer particles (the
+// in-/outlet boundary layers, reading A23) with v; v_max of the pass is recorded.
+template <int D, bool TVF>
 __device__ __forceinline__ void finish_force(const DomainDev& d, unsigned i, const int c[3], const float fi[3],
-                                             const float vi[3], float rho_i, uint8_t lab, const float a[3]) {
+                                             const float vi[3], float rho_i, uint8_t lab, const float a[3],
+                                             const float tb[3]) {
   const Phys& P = d.P;
   float v[3] = {vi[0] + a[0] * P.dt, vi[1] + a[1] * P.dt, D == 3 ? vi[2] + a[2] * P.dt : 0.f};
   if (lab != 0) {
@@ -193,7 +208,23 @@ __device__ __forceinline__ void finish_force(const DomainDev& d, unsigned i, con
     atomicAdd(reinterpret_cast<unsigned long long*>(&d.st->flux_fx[k]),
               (unsigned long long)__double2ll_rn((double)(vn * b.flux_scale) * kFluxScale));
   }
-  drift_store<D>(d, i, c, fi, v, rho_i, lab);
+  if (TVF) {
+    float adv[3] = {v[0], v[1], v[2]};
+    if (lab == 0) {
+      const float s = P.dt * d.st->p_max;
+#pragma unroll
+      for (int x = 0; x < D; ++x) adv[x] = v[x] - s * tb[x];
+    }
+    float sp = v[0] * v[0] + v[1] * v[1];
+    if (D == 3) sp += v[2] * v[2];
+    const unsigned bits = __float_as_uint(sqrtf(sp));  // non-negative: bits order like values
+    const unsigned am = __activemask();
+    const unsigned wmax = __reduce_max_sync(am, bits);
+    if ((threadIdx.x & 31) == __ffs(am) - 1) atomicMax(&d.st->vmax_bits, wmax);
+    drift_store<D>(d, i, c, fi, v, adv, rho_i, lab);
+  } else {
+    drift_store<D>(d, i, c, fi, v, v, rho_i, lab);
+  }
 }
 
 __device__ __forceinline__ float boundary_pressure2(const DomainDev& d, uint8_t lab, float p_i) {
@@ -204,7 +235,7 @@ __device__ __forceinline__ float boundary_pressure2(const DomainDev& d, uint8_t 
 }
 
 // ---------------------------------------------------------------- fallback: one particle from the cells
-template <int D>
+template <int D, bool TVF>
 __device__ void force_one(const DomainDev& d, unsigned i) {
   const Phys& P = d.P;
   int c[3];
@@ -213,9 +244,9 @@ __device__ void force_one(const DomainDev& d, unsigned i) {
   const float vi[3] = {d.A.v[0][i], d.A.v[1][i], D == 3 ? d.A.v[2][i] : 0.f};
   const uint8_t lab = d.A.label[i];
   const float rho_i = d.vr4[i].w;
-  const float p_i = P.c0sq * (rho_i - P.rho0);
+  const float p_i = P.c0sq * (rho_i - P.rho0) + P.p_bg;
   const float pb2 = boundary_pressure2(d, lab, p_i);
-  float a[3] = {0.f, 0.f, 0.f};
+  float a[3] = {0.f, 0.f, 0.f}, tb[3] = {0.f, 0.f, 0.f};
   for_each_near<D>(d, c, fi, [&](int wall, unsigned j, float rx, float ry, float rz) {
     const float r2 = rx * rx + ry * ry + rz * rz;
     if (r2 < P.two_h_sq && r2 > 0.f) {
@@ -226,10 +257,10 @@ __device__ void force_one(const DomainDev& d, unsigned i) {
         vj[0] = v.x, vj[1] = v.y, vj[2] = v.z;
         rho_j = v.w;
       }
-      force_term(P, wall, rx, ry, rz, r2, vi, rho_i, p_i, pb2, vj, rho_j, a);
+      force_term<TVF>(P, wall, rx, ry, rz, r2, vi, rho_i, p_i, pb2, vj, rho_j, a, tb);
     }
   });
-  finish_force<D>(d, i, c, fi, vi, rho_i, lab, a);
+  finish_force<D, TVF>(d, i, c, fi, vi, rho_i, lab, a, tb);
 }
 
 // ---------------------------------------------------------------- neighbour lists
@@ -404,7 +435,7 @@ __device__ __forceinline__ void density_deferred_body(const DomainDev& d, unsign
     const bool buf = lab != 0;
     const float4 vi4 = d.vel4[i];
     const float rho_i = vi4.w;
-    const float p_i = P.c0sq * (rho_i - P.rho0);
+    const float p_i = P.c0sq * (rho_i - P.rho0) + P.p_bg;
     const float vi[3] = {vi4.x, vi4.y, vi4.z};
     float s = 0.f;
     auto term = [&](int wall, unsigned j, float rx, float ry, float rz) {
@@ -437,8 +468,9 @@ __device__ __forceinline__ void density_deferred_body(const DomainDev& d, unsign
   }
 }
 
-// Force pass over the lists: Eqs. (5)-(8), (18), then kick, boundary velocity and drift.
-template <int D>
+// Force pass over the lists: Eqs. (5)-(8), (18), then kick, boundary velocity and drift
+// (with the transport velocity of Eq. (10) when TVF).
+template <int D, bool TVF>
 __device__ __forceinline__ void force_body(const DomainDev& d, unsigned bid, unsigned nblk) {
   if (d.st->status) return;
   const unsigned n = d.st->n;
@@ -447,7 +479,7 @@ __device__ __forceinline__ void force_body(const DomainDev& d, unsigned bid, uns
   for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
     const int cnt = (int)d.nb_cnt[i];
     if (cnt > cap) {
-      force_one<D>(d, i);
+      force_one<D, TVF>(d, i);
       continue;
     }
     const float4 pi = d.pos4[i];
@@ -456,9 +488,9 @@ __device__ __forceinline__ void force_body(const DomainDev& d, unsigned bid, uns
     const float vi[3] = {vi4.x, vi4.y, vi4.z};
     const uint8_t lab = d.A.label[i];
     const float rho_i = vi4.w;
-    const float p_i = P.c0sq * (rho_i - P.rho0);
+    const float p_i = P.c0sq * (rho_i - P.rho0) + P.p_bg;
     const float pb2 = boundary_pressure2(d, lab, p_i);
-    float a[3] = {0.f, 0.f, 0.f};
+    float a[3] = {0.f, 0.f, 0.f}, tb[3] = {0.f, 0.f, 0.f};
     for_each_listed<D>(d, i, cnt, pi.w, fi, [&](int wall, unsigned j, float rx, float ry, float rz) {
       const float r2 = rx * rx + ry * ry + rz * rz;
       float vj[3] = {0.f, 0.f, 0.f};
@@ -468,11 +500,11 @@ __device__ __forceinline__ void force_body(const DomainDev& d, unsigned bid, uns
         vj[0] = v.x, vj[1] = v.y, vj[2] = v.z;
         rho_j = v.w;
       }
-      force_term(P, wall, rx, ry, rz, r2, vi, rho_i, p_i, pb2, vj, rho_j, a);
+      force_term<TVF>(P, wall, rx, ry, rz, r2, vi, rho_i, p_i, pb2, vj, rho_j, a, tb);
     });
     int c[3];
     cell_coords(d.A.cell[i], d.g, c);
-    finish_force<D>(d, i, c, fi, vi, rho_i, lab, a);
+    finish_force<D, TVF>(d, i, c, fi, vi, rho_i, lab, a, tb);
   }
 }
 
@@ -486,7 +518,7 @@ __device__ __forceinline__ void drift_body(const DomainDev& d, unsigned bid, uns
     cell_coords(d.A.cell[i], d.g, c);
     const float fi[3] = {d.A.f[0][i], d.A.f[1][i], D == 3 ? d.A.f[2][i] : 0.f};
     const float v[3] = {d.A.v[0][i], d.A.v[1][i], D == 3 ? d.A.v[2][i] : 0.f};
-    drift_store<D>(d, i, c, fi, v, d.A.rho[i], d.A.label[i]);
+    drift_store<D>(d, i, c, fi, v, v, d.A.rho[i], d.A.label[i]);
   }
 }
 
@@ -509,7 +541,17 @@ __device__ __forceinline__ void drift_body(const DomainDev& d, unsigned bid, uns
 SPHBUF_PAIR(k_neighbours, neighbours_body, (kThreads, 5))
 SPHBUF_PAIR(k_density, density_body, (kThreads, 6))
 SPHBUF_PAIR(k_density_deferred, density_deferred_body, (kThreads, 4))
-SPHBUF_PAIR(k_force, force_body, (kThreads, 4))
+template <int D, bool TVF>
+__global__ void __launch_bounds__(kThreads, 4) k_force(DomainDev d) {
+  force_body<D, TVF>(d, blockIdx.x, gridDim.x);
+}
+template <int D, bool TVF>
+__global__ void __launch_bounds__(kThreads, 4) k_force_batch(BatchDev b) {
+  __shared__ DomainDev sd;
+  const int4 m = b.map[blockIdx.x];
+  load_domain(sd, b.doms + m.x);
+  force_body<D, TVF>(sd, (unsigned)m.y, (unsigned)m.z);
+}
 SPHBUF_PAIR(k_drift, drift_body, (kThreads))
 #undef SPHBUF_PAIR
 
@@ -537,10 +579,18 @@ int launch_density(const DomainDev& d, cudaStream_t s) {
 }
 
 int launch_force(const DomainDev& d, cudaStream_t s) {
-  if (d.g.dim == 2)
-    k_force<2><<<grid_for(d, 8), kThreads, 0, s>>>(d);
-  else
-    k_force<3><<<grid_for(d, 8), kThreads, 0, s>>>(d);
+  const bool tvf = d.P.tvf_lambda > 0.f;
+  if (d.g.dim == 2) {
+    if (tvf)
+      k_force<2, true><<<grid_for(d, 8), kThreads, 0, s>>>(d);
+    else
+      k_force<2, false><<<grid_for(d, 8), kThreads, 0, s>>>(d);
+  } else {
+    if (tvf)
+      k_force<3, true><<<grid_for(d, 8), kThreads, 0, s>>>(d);
+    else
+      k_force<3, false><<<grid_for(d, 8), kThreads, 0, s>>>(d);
+  }
   return 1;
 }
 
@@ -552,7 +602,22 @@ int launch_drift(const DomainDev& d, cudaStream_t s) {
   return 1;
 }
 
-int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s) {
+int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s, bool tvf) {
+  if (k == K_FORCE) {
+    // the transport-velocity kernel also serves domains with lambda = 0 (p_max stays 0)
+    if (dim == 2) {
+      if (tvf)
+        k_force_batch<2, true><<<nblocks, kThreads, 0, s>>>(b);
+      else
+        k_force_batch<2, false><<<nblocks, kThreads, 0, s>>>(b);
+    } else {
+      if (tvf)
+        k_force_batch<3, true><<<nblocks, kThreads, 0, s>>>(b);
+      else
+        k_force_batch<3, false><<<nblocks, kThreads, 0, s>>>(b);
+    }
+    return 1;
+  }
 #define SPHBUF_CASE(KID, NAME)                                             \
   case KID:                                                                \
     if (dim == 2)                                                          \
@@ -564,7 +629,6 @@ int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream
     SPHBUF_CASE(K_NEIGHBOURS, k_neighbours)
     SPHBUF_CASE(K_DENSITY, k_density)
     SPHBUF_CASE(K_DENSITY_DEFER, k_density_deferred)
-    SPHBUF_CASE(K_FORCE, k_force)
     SPHBUF_CASE(K_DRIFT, k_drift)
     default:
       return 0;

@@ -157,6 +157,10 @@ class Domain:
         d = cls(case.dim, case.lo, case.hi, case.dp, case.h_over_dp, case.rho0, case.c0, case.nu, case.dt,
                 capacity or case.capacity, stream=stream)
         d.set_walls(case.wall_pos)
+        if getattr(case, "p_bg", 0.0):
+            d.set_background_pressure(case.p_bg)
+        if getattr(case, "tvf_lambda", 0.0):
+            d.set_transport_velocity(case.tvf_lambda)
         for b in case.buffers:
             d.add_buffer(b)
         if native:
@@ -205,6 +209,14 @@ class Domain:
         if pivot is not None:
             self.set_buffer_rotation(k.value, pivot, getattr(spec, "axis", None), float(getattr(spec, "omega", 0.0)))
         return k.value
+
+    def set_background_pressure(self, p_bg: float):
+        """Background pressure of the EoS, p = c0^2 (rho - rho0) + p_bg (before the first step)."""
+        self._check(self.lib.sphbuf_set_background_pressure(self.h, float(p_bg)), "set_background_pressure")
+
+    def set_transport_velocity(self, lam: float):
+        """Transport velocity of Eq. (10) with coefficient lambda (before the first step)."""
+        self._check(self.lib.sphbuf_set_transport_velocity(self.h, float(lam)), "set_transport_velocity")
 
     def set_windkessel(self, k: int, r_p: float, compliance: float, r_d: float, p_d0: float = 0.0):
         """RCR Windkessel boundary pressure (Eq. (31)) for pressure buffer k."""

@@ -94,6 +94,8 @@ class Case:
     buffers: List[BufferSpec]
     capacity: int
     steps: int = 1
+    p_bg: float = 0.0  # background pressure of the EoS (Pa); buffer p_b values include it
+    tvf_lambda: float = 0.0  # transport velocity (Eq. (10)) coefficient, 5-10 in the paper; 0 = off
 
     @property
     def n(self) -> int:

@@ -28,6 +28,10 @@ def _domain(c, cell, frac, vel32, rho32):
 
     dom = Domain(c.dim, c.lo, c.hi, c.dp, c.h_over_dp, c.rho0, c.c0, c.nu, c.dt, c.capacity)
     dom.set_walls(c.wall_pos)
+    if c.p_bg:
+        dom.set_background_pressure(c.p_bg)
+    if c.tvf_lambda:
+        dom.set_transport_velocity(c.tvf_lambda)
     for b in c.buffers:
         dom.add_buffer(b)
     dom.write_particles(cell, frac, vel32, rho32)
@@ -95,7 +99,7 @@ def physics_step_sampled(c, sample_size=1500, seed=5):
     pos = wl.decode_positions(cell, frac, c.lo, c.cs, c.grid_dims())
     vel = vel32.astype(np.float64)
     rho = rho32.astype(np.float64)
-    P = sph.make_params(c.dim, c.dp, c.h_over_dp, c.rho0, c.c0, c.nu, c.dt)
+    P = sph.make_params(c.dim, c.dp, c.h_over_dp, c.rho0, c.c0, c.nu, c.dt, c.p_bg)
     bufs = [OB.Buffer(k, s, c.dim) for k, s in enumerate(c.buffers)]
     # labels as both sides take them at the first step: Algorithms 1-3 identification, FP32
     g32 = OF.Grid32(c.dim, c.lo, c.hi, c.dp, c.h_over_dp)

@@ -312,7 +312,7 @@ def run_gpu(args):
     del back
 
     dom.close()
-    batched = None if args.no_batched else run_batched(args, stream)
+    batched = None if args.no_batched else run_batched(args, stream, rank, world)
     tjunction = None if args.no_tjunction else run_restricted_vs_full(args, stream)
     rotating = None if args.no_rotating else run_rotating(args, stream)
 
@@ -365,14 +365,18 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def run_batched(args, stream):
-    """64 independent 2-D star channels: one batch vs 64 sequential plain runs, same GPU."""
+def run_batched(args, stream, rank=0, world=1):
+    """64 independent 2-D star channels: one batch vs 64 sequential plain runs, same GPU.
+    Under torchrun the domains are shared out by longest processing time (no data exchange);
+    every rank runs its share both ways and the times are the slowest rank's."""
     import torch
 
-    from paper_2406_16786_gb300 import workloads
+    from paper_2406_16786_gb300 import sharding, workloads
     from paper_2406_16786_gb300.domain import Batch, Domain
 
-    cases = workloads.config5()
+    all_cases = workloads.config5()
+    mine = sharding.assign_lpt([c.n for c in all_cases], world)[rank]
+    cases = [all_cases[q] for q in mine]
     K, W = args.batch_steps, 3
     # plain: each domain alone (graph replays), one after another
     plain = [Domain.from_case(c, stream=stream) for c in cases]
@@ -386,8 +390,8 @@ def run_batched(args, stream):
         d.step(K)
     e1.record(stream)
     torch.cuda.synchronize()
-    t_plain = e0.elapsed_time(e1)
-    n_plain = sum(d.count() for d in plain)
+    t_plain = sharding.max_over_ranks(e0.elapsed_time(e1))
+    n_plain = sum(sharding.gather_counters({q: d.count() for q, d in zip(mine, plain)}).values())
     for d in plain:
         d.close()
     # batched: the same 64 domains in one batch (grid multiplier from the autotuner)
@@ -401,15 +405,17 @@ def run_batched(args, stream):
     b.step(K)
     e1.record(stream)
     torch.cuda.synchronize()
-    t_batch = e0.elapsed_time(e1)
+    t_batch = sharding.max_over_ranks(e0.elapsed_time(e1))
     b.sync()
-    n_batch = sum(d.count() for d in doms)
+    counts = sharding.gather_counters({q: {"particles": d.count(), "steps": d.global_counters()["steps"]}
+                                       for q, d in zip(mine, doms)})
+    n_batch = sum(v["particles"] for v in counts.values())
     b.close()
     for d in doms:
         d.close()
-    nd = len(cases)
+    nd = len(all_cases)
     return {"workload": "64 2-D star channels (1-6 arms, 10k-500k particles log-uniform, mixed BCs)",
-            "domains": nd, "particles": n_batch, "steps": K,
+            "domains": nd, "ranks": world, "domains_per_rank": len(mine), "particles": n_batch, "steps": K,
             "plain_domain_steps_per_s": nd * K / (t_plain / 1e3),
             "batched_domain_steps_per_s": nd * K / (t_batch / 1e3),
             "speedup": t_plain / t_batch, "plain_ms": t_plain, "batched_ms": t_batch,

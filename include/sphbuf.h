@@ -169,6 +169,19 @@ sphbuf_status sphbuf_set_buffer_rotation(sphbuf_domain_t d, int buffer_id, const
  * SPHBUF_ERR_INVALID_ARG (non-finite), SPHBUF_ERR_STATE (after the first step). */
 sphbuf_status sphbuf_set_background_pressure(sphbuf_domain_t d, double p_bg);
 
+/* Dual-criteria time stepping (Sec. 2.2): each step (of the descriptor's dt, the advection
+ * step) fixes the neighbour configuration, re-initialises the density of the fluid particles
+ * by Eq. (9) (buffer particles keep theirs), evaluates the viscous acceleration once, then
+ * runs n_acoustic acoustic steps of dt / n_acoustic: continuity (Eq. (4)) for every particle
+ * and the pressure part of Eq. (5) with Eq. (18) from the current state, kick, boundary
+ * velocity, density and position update.  The buffer update and the cell-list rebuild run
+ * once per step.  A buffer's flux is the mean over the acoustic steps.  n_acoustic = 0 (the
+ * default) is the single-rate kick-drift step.  A particle whose neighbour list overflowed
+ * (strong compression) latches SPHBUF_ERR_CAPACITY in this mode.  Batches need the same
+ * n_acoustic in every domain.  Errors: SPHBUF_ERR_INVALID_ARG (outside [0, 4096]),
+ * SPHBUF_ERR_STATE (after the first step), SPHBUF_ERR_CUDA (allocation). */
+sphbuf_status sphbuf_set_dual_time_stepping(sphbuf_domain_t d, int n_acoustic);
+
 /* Transport-velocity formulation (Eq. (10)): fluid particles (label 0) are advected with
  * v - dt p_max sum_j 2 m/(rho_i rho_j) dW/dr_ij e_ij instead of v, p_max = lambda rho0 v_max^2
  * with v_max the largest particle speed of the previous step's force pass (0 at the first

@@ -325,6 +325,50 @@ class OracleSim:
         self.pos = self.pos + adv * P.dt
         self.rho = rho_new
 
+    def dual_physics(self, n_ac: int):
+        """Dual-criteria time stepping (Sec. 2.2, the cited dual-criteria scheme; reading A26):
+        one advection step of dt = P.dt made of n_ac acoustic steps of dt / n_ac.
+
+        At the advection step the configuration (the neighbour pairs) is fixed and the
+        density of the fluid particles is re-initialised by Eq. (9) (buffer particles keep
+        theirs); the viscous acceleration is evaluated once.  Each acoustic step then takes,
+        from the current state with the pairs' distances recomputed: the continuity rate of
+        Eq. (4) for every particle and the pressure part of Eq. (5) with Eq. (18); v += dt_ac
+        (a_p + a_v), the boundary velocity of the buffer particles (Eqs. (19), (23)-(26), from
+        the acoustic step's start position), rho += dt_ac drho/dt, r += dt_ac v.  The flux of
+        a buffer is the mean over the acoustic steps."""
+        P = self.P
+        ff, fw = sph.neighbor_pairs(self.pos, self.wall, P.h)
+        is_buf = self.label != 0
+        rho = np.where(is_buf, self.rho, sph.density_summation(P, self.n, ff, fw))
+        nan = np.full(self.n, np.nan)
+        a_v = sph.acceleration(P, self.vel, rho, nan, ff, fw, pressure=False)
+        dt = P.dt / n_ac
+        v, pos = self.vel.copy(), self.pos.copy()
+        flux = np.zeros(len(self.buffers))
+        for _ in range(n_ac):
+            ffs, fws = sph.moved(ff, pos, pos), sph.moved(fw, pos, self.wall)
+            drho = sph.continuity_rate(P, v, rho, ffs, fws)
+            a_p = sph.acceleration(P, v, rho, self.p_bc(rho), ffs, fws, viscous=False)
+            vn = v + dt * (a_p + a_v)
+            for b in self.buffers:
+                m = self.label == b.label
+                if not np.any(m):
+                    continue
+                if b.bc in VELOCITY_BC:
+                    prof = b.profile(b.local(pos[m]))
+                    vn[m] = prof[:, None] * b.u[None, :]
+                else:
+                    un = vn[m] @ b.u
+                    vn[m] = un[:, None] * b.u[None, :]
+            for b in self.buffers:
+                flux[b.k] += b.flux(vn, self.label, self.dp) / n_ac
+            rho = rho + dt * drho
+            pos = pos + dt * vn
+            v = vn
+        self.flux[:] = flux
+        self.vel, self.pos, self.rho = v, pos, rho
+
     def kinematic(self):
         """Drift only with the current velocity (used by the lockstep tests)."""
         self.pos = self.pos + self.vel * self.P.dt
@@ -387,10 +431,12 @@ class OracleSim:
                 b.windkessel_step(float(self.flux[b.k]), self.P.dt, self.step_index == 0)
         self.flux[:] = 0.0
 
-    def step(self, nsteps=1, physics=True, buffer=True):
+    def step(self, nsteps=1, physics=True, buffer=True, dual=0):
         for _ in range(nsteps):
             self.begin_step()
-            if physics:
+            if physics and dual:
+                self.dual_physics(dual)
+            elif physics:
                 self.physics()
             else:
                 self.kinematic()

@@ -179,12 +179,19 @@ def transport_sum(P: Params, rho, ff: Pairs, fw: Pairs) -> np.ndarray:
     return out
 
 
-def acceleration(P: Params, vel, rho, p_bc, ff: Pairs, fw: Pairs) -> np.ndarray:
+def moved(pairs: Pairs, fpos, other) -> Pairs:
+    """The same pairs with r_ij recomputed from new positions (fixed configuration)."""
+    rij = fpos[pairs.i] - other[pairs.j]
+    return Pairs(pairs.i, pairs.j, rij, np.sqrt(np.sum(rij * rij, axis=1)))
+
+
+def acceleration(P: Params, vel, rho, p_bc, ff: Pairs, fw: Pairs, pressure=True, viscous=True) -> np.ndarray:
     """Eq. (5), and Eq. (18) for particles with a finite boundary pressure ``p_bc[i]``.
 
     dv_i/dt = -2 sum_j m P*_ij/(rho_i rho_j) grad W_ij + 2 sum_j m eta v_ij/(rho_i rho_j r_ij) dW_ij
               [+ 2 p_b sum_j m/(rho_i rho_j) grad W_ij   for buffer particles]
-    ``p_bc`` is NaN for particles without the boundary term.
+    ``p_bc`` is NaN for particles without the boundary term.  ``pressure`` / ``viscous``
+    select the terms (the pressure part includes Eq. (18)).
     """
     n = rho.shape[0]
     d = vel.shape[1]
@@ -210,10 +217,13 @@ def acceleration(P: Params, vel, rho, p_bc, ff: Pairs, fw: Pairs) -> np.ndarray:
             rho_j = rho[pairs.j]
             p_j = p[pairs.j]
         rho_i = rho[i]
-        pstar = _riemann_p_star(vi, vj, rho_i, rho_j, p[i], p_j, e, P.c0)
         inv = m / (rho_i * rho_j)
-        term = -2.0 * (inv * pstar)[:, None] * gradW
-        term += 2.0 * (inv * P.eta * dw / pairs.r)[:, None] * (vi - vj)
-        term += 2.0 * (pb[i] * inv)[:, None] * gradW * has_bc[i][:, None]
+        term = np.zeros_like(gradW)
+        if pressure:
+            pstar = _riemann_p_star(vi, vj, rho_i, rho_j, p[i], p_j, e, P.c0)
+            term += -2.0 * (inv * pstar)[:, None] * gradW
+            term += 2.0 * (pb[i] * inv)[:, None] * gradW * has_bc[i][:, None]
+        if viscous:
+            term += 2.0 * (inv * P.eta * dw / pairs.r)[:, None] * (vi - vj)
         acc += _scatter(i, term, n)
     return acc

@@ -39,6 +39,7 @@ SIGNATURES = {
     "sphbuf_set_windkessel": (ctypes.c_int, [vp, ctypes.c_int, c_dbl, c_dbl, c_dbl, c_dbl]),
     "sphbuf_set_background_pressure": (ctypes.c_int, [vp, c_dbl]),
     "sphbuf_set_transport_velocity": (ctypes.c_int, [vp, c_dbl]),
+    "sphbuf_set_dual_time_stepping": (ctypes.c_int, [vp, ctypes.c_int]),
     "sphbuf_read_boundary_pressure": (ctypes.c_int, [vp, ctypes.c_int, P(c_dbl), P(c_dbl), P(c_dbl)]),
     "sphbuf_step": (ctypes.c_int, [vp, ctypes.c_int]),
     "sphbuf_step_phases": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_uint]),

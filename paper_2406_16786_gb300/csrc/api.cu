@@ -378,7 +378,7 @@ int enqueue_step(sphbuf_domain* d, unsigned phases, bool timed) {
     if (timed) cudaEventRecord(d->ev[1], s);
     k += launch_density(v, s);
     if (timed) cudaEventRecord(d->ev[2], s);
-    k += launch_force(v, s);
+    k += v.P.dual_n > 0 ? launch_dual(v, s) : launch_force(v, s);
   } else {
     if (timed) cudaEventRecord(d->ev[1], s);
     if (timed) cudaEventRecord(d->ev[2], s);
@@ -911,6 +911,22 @@ sphbuf_status sphbuf_set_background_pressure(sphbuf_domain_t d, double p_bg) {
   return SPHBUF_OK;
 }
 
+sphbuf_status sphbuf_set_dual_time_stepping(sphbuf_domain_t d, int n_acoustic) {
+  if (!d) return SPHBUF_ERR_INVALID_ARG;
+  if (d->stepped || d->committed) return fail(d, SPHBUF_ERR_STATE, "the time stepping must be set before the first step");
+  if (n_acoustic < 0 || n_acoustic > 4096) return fail(d, SPHBUF_ERR_INVALID_ARG, "n_acoustic must be in [0, 4096]");
+  DomainDev& v = d->dev;
+  if (n_acoustic > 0 && !v.pos_b) {
+    const size_t C = d->desc.capacity;
+    CK(dalloc(d, &v.pos_b, C));
+    CK(dalloc(d, &v.vr_b, C));
+    CK(dalloc(d, &v.av, C));
+  }
+  v.P.dual_n = n_acoustic;
+  v.P.dt_ac = n_acoustic > 0 ? (float)(d->desc.dt / n_acoustic) : 0.f;
+  return SPHBUF_OK;
+}
+
 sphbuf_status sphbuf_set_transport_velocity(sphbuf_domain_t d, double lambda) {
   if (!d) return SPHBUF_ERR_INVALID_ARG;
   if (d->stepped || d->committed) return fail(d, SPHBUF_ERR_STATE, "the transport velocity must be set before the first step");
@@ -1169,6 +1185,7 @@ sphbuf_status sphbuf_read_phase_times(sphbuf_domain_t d, double ms[5], uint64_t*
 // ---------------------------------------------------------------- batched domains
 struct sphbuf_batch {
   std::vector<sphbuf_domain*> doms;
+  int dual_n = 0;    // acoustic steps per step (the same for every domain of the batch)
   bool tvf = false;  // some domain advects with the transport velocity (Eq. (10))
   std::vector<uint64_t> n0;  // particles per domain when the batch was made (block shares)
   int dim = 0;
@@ -1256,6 +1273,8 @@ static int batch_launch(sphbuf_batch* b, Kern k) {
     case K_DENSITY_DEFER:
     case K_FORCE:
     case K_DRIFT:
+    case K_VISCOUS:
+    case K_DUAL_FINISH:
       return launch_batch_sph(k, b->dim, bd, n, b->stream, b->tvf);
     case K_BUFFER:
     case K_BUFFER_FULL:
@@ -1276,7 +1295,16 @@ static int batch_enqueue_step(sphbuf_batch* b, unsigned phases, bool timed) {
     k += batch_launch(b, K_DENSITY);
     k += batch_launch(b, K_DENSITY_DEFER);
     if (timed) cudaEventRecord(b->ev[2], s);
-    k += batch_launch(b, K_FORCE);
+    if (b->dual_n > 0) {
+      k += batch_launch(b, K_VISCOUS);
+      for (int q = 0; q < b->dual_n; ++q) {
+        const BatchDev bd{b->d_doms, b->d_maps[K_ACOUSTIC]};
+        k += launch_batch_sph(K_ACOUSTIC, b->dim, bd, b->nblocks[K_ACOUSTIC], s, false, q);
+      }
+      k += batch_launch(b, K_DUAL_FINISH);
+    } else {
+      k += batch_launch(b, K_FORCE);
+    }
   } else {
     if (timed) cudaEventRecord(b->ev[1], s);
     if (timed) cudaEventRecord(b->ev[2], s);
@@ -1367,6 +1395,11 @@ sphbuf_status sphbuf_batch_create(sphbuf_domain_t* domains, int n, void* cuda_st
     if (s != SPHBUF_OK) {
       delete b;
       return s;
+    }
+    if (q == 0) b->dual_n = d->dev.P.dual_n;
+    if (d->dev.P.dual_n != b->dual_n) {
+      delete b;
+      return SPHBUF_ERR_INVALID_ARG;
     }
     b->doms.push_back(d);
     b->n0.push_back(st.n);

@@ -139,6 +139,8 @@ struct Phys {
   float h, inv_h, two_h_sq, alpha, rho0, c0, c0sq, eta, mass, dt, inv_sum_w0, w_self;
   float p_bg;  // background pressure of the EoS: p = c0^2 (rho - rho0) + p_bg
   float tvf_lambda;  // transport velocity (Eq. (10)): p_max = lambda rho0 v_max^2; 0 = off
+  float dt_ac;       // acoustic step of the dual-criteria scheme (dt / dual_n)
+  int dual_n;        // acoustic steps per advection step; 0 = single-rate kick-drift
   double rho0_d, c0sq_d, dt_d, p_bg_d;
   double lo_d[3], cs_d;  // grid origin and cell size in FP64 (frames of rotating buffers)
   unsigned capacity;

@@ -18,6 +18,9 @@ struct DomainDev {
   unsigned* slot;         // per-particle slot from the histogram, capacity
   unsigned* tmp_id;       // ids scattered to their cell's range, capacity
   float4* vr4;            // density pass output (vx, vy, vz, new rho) in A order, capacity
+  float4* pos_b;          // dual-criteria scheme: second copy of pos4 and vr4 (acoustic steps
+  float4* vr_b;           //   alternate between the two), and the viscous acceleration of
+  float4* av;             //   the advection step
   unsigned* deferred;     // particles left by the fluid density pass (buffer or overflowed list)
   float4* pos4;           // A-order copies for the neighbour passes: (fx, fy, fz, cell x)
   float4* vel4;           //   and (vx, vy, vz, rho); written by the rebuild scatter
@@ -56,6 +59,9 @@ enum Kern : int {
   K_DENSITY_DEFER,
   K_FORCE,
   K_DRIFT,
+  K_VISCOUS,
+  K_ACOUSTIC,
+  K_DUAL_FINISH,
   K_BUFFER,
   K_BUFFER_FULL,
   K_HIST,
@@ -77,7 +83,7 @@ __device__ __forceinline__ void load_domain(DomainDev& dst, const DomainDev* src
   __syncthreads();
 }
 
-int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s, bool tvf);
+int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s, bool tvf, int sub = 0);
 int launch_batch_buffer(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s);
 int launch_batch_cells(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s);
 int batch_threads(Kern k);  // threads per block of each batched kernel
@@ -87,6 +93,7 @@ int launch_neighbours(const DomainDev& d, cudaStream_t s);  // starts the step (
 int launch_density(const DomainDev& d, cudaStream_t s);  // two kernels: fluid, then deferred
 int launch_force(const DomainDev& d, cudaStream_t s);
 int launch_drift(const DomainDev& d, cudaStream_t s);
+int launch_dual(const DomainDev& d, cudaStream_t s);  // viscous, acoustic steps, fold (dual_n > 0)
 // buffer (kernels_buffer.cu)
 int launch_identify(const DomainDev& d, cudaStream_t s);
 int launch_decide(const DomainDev& d, bool full_domain, cudaStream_t s);

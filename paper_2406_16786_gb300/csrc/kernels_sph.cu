@@ -463,8 +463,10 @@ __device__ __forceinline__ void density_deferred_body(const DomainDev& d, unsign
         if (r2 < P.two_h_sq && r2 > 0.f) term(wall, j, rx, ry, rz);
       });
     }
-    d.vr4[i] = make_float4(vi[0], vi[1], vi[2],
-                           buf ? rho_i + P.dt * (2.f * rho_i * s) : P.rho0 * (s + P.w_self) * P.inv_sum_w0);
+    // (in the dual-criteria scheme the buffer particles keep their density here; their
+    // continuity is integrated by the acoustic steps)
+    const float rb = P.dual_n > 0 ? rho_i : rho_i + P.dt * (2.f * rho_i * s);
+    d.vr4[i] = make_float4(vi[0], vi[1], vi[2], buf ? rb : P.rho0 * (s + P.w_self) * P.inv_sum_w0);
   }
 }
 
@@ -522,6 +524,189 @@ __device__ __forceinline__ void drift_body(const DomainDev& d, unsigned bid, uns
   }
 }
 
+// ---------------------------------------------------------------- dual-criteria time stepping
+// One advection step = the neighbour lists and the density re-initialisation (Eq. (9)) of the
+// step, the viscous acceleration once (viscous_body), dual_n acoustic steps (acoustic_body:
+// continuity, Eq. (4), and the pressure part of Eq. (5) with Eq. (18) from the current state;
+// kick, boundary velocity, density and position update), then the positions are folded back
+// into their cells and written to B (dual_finish_body).  During the acoustic steps the
+// configuration of the lists is fixed and the offsets stay relative to the cells of the
+// advection step (they may leave [0, cs)); pos4/vr4 and pos_b/vr_b alternate.
+
+// Viscous part of Eq. (5) for the pair (walls: v_ij = 2 v_i, rho_j = rho_i).
+__device__ __forceinline__ void viscous_term(const Phys& P, bool wall, float rx, float ry, float rz, float r2,
+                                             const float vi[3], float rho_i, const float vj[3], float rho_j,
+                                             float a[3]) {
+  const float r = sqrtf(r2), inv_r = 1.f / r;
+  float vx, vy, vz;
+  if (wall) {
+    vx = 2.f * vi[0], vy = 2.f * vi[1], vz = 2.f * vi[2];
+    rho_j = rho_i;
+  } else {
+    vx = vi[0] - vj[0], vy = vi[1] - vj[1], vz = vi[2] - vj[2];
+  }
+  const float cv = P.mass / (rho_i * rho_j) * kernel_dw(r * P.inv_h, P) * 2.f * P.eta * inv_r;
+  a[0] += cv * vx;
+  a[1] += cv * vy;
+  a[2] += cv * vz;
+}
+
+template <int D>
+__device__ __forceinline__ void viscous_body(const DomainDev& d, unsigned bid, unsigned nblk) {
+  if (d.st->status) return;
+  const unsigned n = d.st->n;
+  const Phys P = d.P;
+  const int cap = d.nb_cap;
+  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
+    const int cnt = (int)d.nb_cnt[i];
+    const float4 pi = d.pos4[i];
+    const float fi[3] = {pi.x, pi.y, pi.z};
+    const float4 vi4 = d.vr4[i];
+    const float vi[3] = {vi4.x, vi4.y, vi4.z};
+    const float rho_i = vi4.w;
+    float a[3] = {0.f, 0.f, 0.f};
+    auto fn = [&](int wall, unsigned j, float rx, float ry, float rz) {
+      const float r2 = rx * rx + ry * ry + rz * rz;
+      float vj[3] = {0.f, 0.f, 0.f};
+      float rho_j = rho_i;
+      if (!wall) {
+        const float4 v = __ldg(d.vr4 + j);
+        vj[0] = v.x, vj[1] = v.y, vj[2] = v.z;
+        rho_j = v.w;
+      }
+      viscous_term(P, wall, rx, ry, rz, r2, vi, rho_i, vj, rho_j, a);
+    };
+    if (cnt <= cap) {
+      for_each_listed<D>(d, i, cnt, pi.w, fi, fn);
+    } else {
+      int c[3];
+      cell_coords(d.A.cell[i], d.g, c);
+      for_each_near<D>(d, c, fi, [&](int wall, unsigned j, float rx, float ry, float rz) {
+        const float r2 = rx * rx + ry * ry + rz * rz;
+        if (r2 < P.two_h_sq && r2 > 0.f) fn(wall, j, rx, ry, rz);
+      });
+    }
+    d.av[i] = make_float4(a[0], a[1], a[2], 0.f);
+  }
+}
+
+// Acoustic step sub (0-based) of the advection step: reads state sub % 2, writes the other.
+template <int D>
+__device__ __forceinline__ void acoustic_body(const DomainDev& d, unsigned bid, unsigned nblk, int sub) {
+  if (d.st->status) return;
+  const unsigned n = d.st->n;
+  const Phys P = d.P;
+  Phys Pp = P;
+  Pp.eta = 0.f;  // pressure part only (the viscous one is in av)
+  const float4* pc = (sub & 1) ? d.pos_b : d.pos4;
+  const float4* sc = (sub & 1) ? d.vr_b : d.vr4;
+  float4* pn = (sub & 1) ? d.pos4 : d.pos_b;
+  float4* sn = (sub & 1) ? d.vr4 : d.vr_b;
+  const float dt = P.dt_ac;
+  const float inv_n = 1.f / (float)P.dual_n;
+  const Grid& g = d.g;
+  const int cap = d.nb_cap;
+  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
+    int cnt = (int)d.nb_cnt[i];
+    if (cnt > cap) {
+      // an overflowed list has no fixed configuration for the acoustic steps
+      latch(d.st, 2 /* SPHBUF_ERR_CAPACITY */);
+      cnt = cap;
+    }
+    const float4 pi = pc[i];
+    const float fi[3] = {pi.x, pi.y, pi.z};
+    const float cxf = pi.w;
+    const float4 si = sc[i];
+    const float vi[3] = {si.x, si.y, si.z};
+    const float rho_i = si.w;
+    const float p_i = P.c0sq * (rho_i - P.rho0) + P.p_bg;
+    const uint8_t lab = d.A.label[i];
+    const float pb2 = boundary_pressure2(d, lab, p_i);
+    float a[3] = {0.f, 0.f, 0.f}, tb[3] = {0.f, 0.f, 0.f};
+    float srho = 0.f;
+    const uint4* lst = reinterpret_cast<const uint4*>(d.nb + (size_t)i * d.nb_cap);
+    auto one = [&](unsigned ent) {
+      const unsigned j = ent & 0x1FFFFFFu;
+      const int wall = (int)(ent >> 31);
+      const int dy = (int)((ent >> 25) & 3u) - 1;
+      const int dz = (D == 3) ? (int)((ent >> 27) & 3u) - 1 : 0;
+      const float4 p = wall ? __ldg(d.wpos4 + j) : pc[j];
+      const float rx = fi[0] - p.x - (p.w - cxf) * g.cs;
+      const float ry = fi[1] - (float)dy * g.cs - p.y;
+      const float rz = (D == 3) ? fi[2] - (float)dz * g.cs - p.z : 0.f;
+      const float r2 = rx * rx + ry * ry + rz * rz;
+      float vj[3] = {0.f, 0.f, 0.f};
+      float rho_j = rho_i;
+      if (!wall) {
+        const float4 v = sc[j];
+        vj[0] = v.x, vj[1] = v.y, vj[2] = v.z;
+        rho_j = v.w;
+      }
+      force_term<false>(Pp, wall, rx, ry, rz, r2, vi, rho_i, p_i, pb2, vj, rho_j, a, tb);
+      srho += density_term<D>(P, true, wall, rx, ry, rz, sqrtf(r2), vi, rho_i, p_i, vj, rho_j);
+    };
+    for (int e = 0; e < cnt; e += 4) {
+      const uint4 q = __ldg(lst + (e >> 2));
+      one(q.x);
+      if (e + 1 < cnt) one(q.y);
+      if (e + 2 < cnt) one(q.z);
+      if (e + 3 < cnt) one(q.w);
+    }
+    const float4 av = d.av[i];
+    float v[3] = {vi[0] + dt * (a[0] + av.x), vi[1] + dt * (a[1] + av.y), D == 3 ? vi[2] + dt * (a[2] + av.z) : 0.f};
+    if (lab != 0) {
+      const int k = (int)lab - 1;
+      const BufDev& b = d.bufs[k];
+      int c[3];
+      cell_coords(d.A.cell[i], g, c);
+      if (b.vel_bc) {
+        float X[3];
+        local_coords<D>(b, c, fi, g.cs, X, D);
+        float rr = X[1] * X[1];
+        if (D == 3) rr += X[2] * X[2];
+        const float prof = b.inv_hw2 > 0.f ? b.umax * fmaxf(1.f - rr * b.inv_hw2, 0.f) : b.umax;
+#pragma unroll
+        for (int x = 0; x < D; ++x) v[x] = prof * b.u[x];
+      } else {
+        float vn = v[0] * b.u[0] + v[1] * b.u[1];
+        if (D == 3) vn += v[2] * b.u[2];
+#pragma unroll
+        for (int x = 0; x < D; ++x) v[x] = vn * b.u[x];
+      }
+      float vn = v[0] * b.u[0] + v[1] * b.u[1];
+      if (D == 3) vn += v[2] * b.u[2];
+      atomicAdd(reinterpret_cast<unsigned long long*>(&d.st->flux_fx[k]),
+                (unsigned long long)__double2ll_rn((double)(vn * b.flux_scale * inv_n) * kFluxScale));
+    }
+    const float rho_n = rho_i + dt * (2.f * rho_i * srho);
+    float f[3];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) f[x] = x < D ? __fadd_rn(fi[x], __fmul_rn(v[x], dt)) : 0.f;
+    pn[i] = make_float4(f[0], f[1], f[2], cxf);
+    sn[i] = make_float4(v[0], v[1], v[2], rho_n);
+  }
+}
+
+// After the acoustic steps: offsets folded back into [0, cs), the particles written to B.
+template <int D>
+__device__ __forceinline__ void dual_finish_body(const DomainDev& d, unsigned bid, unsigned nblk) {
+  if (d.st->status) return;
+  const unsigned n = d.st->n;
+  const bool odd = d.P.dual_n & 1;
+  const float4* pc = odd ? d.pos_b : d.pos4;
+  const float4* sc = odd ? d.vr_b : d.vr4;
+  const float zero[3] = {0.f, 0.f, 0.f};
+  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
+    int c[3];
+    cell_coords(d.A.cell[i], d.g, c);
+    const float4 p = pc[i];
+    const float4 s = sc[i];
+    const float f[3] = {p.x, p.y, p.z};
+    const float v[3] = {s.x, s.y, s.z};
+    drift_store<D>(d, i, c, f, v, zero, s.w, d.A.label[i]);
+  }
+}
+
 // Single-domain kernels and their multi-domain (batched) twins: block b of a batched launch
 // works for domain map[b].x as its block map[b].y of map[b].z; the domain's descriptor is
 // copied to shared memory first.
@@ -553,6 +738,20 @@ __global__ void __launch_bounds__(kThreads, 4) k_force_batch(BatchDev b) {
   force_body<D, TVF>(sd, (unsigned)m.y, (unsigned)m.z);
 }
 SPHBUF_PAIR(k_drift, drift_body, (kThreads))
+SPHBUF_PAIR(k_viscous, viscous_body, (kThreads, 4))
+SPHBUF_PAIR(k_dual_finish, dual_finish_body, (kThreads))
+
+template <int D>
+__global__ void __launch_bounds__(kThreads, 4) k_acoustic(DomainDev d, int sub) {
+  acoustic_body<D>(d, blockIdx.x, gridDim.x, sub);
+}
+template <int D>
+__global__ void __launch_bounds__(kThreads, 4) k_acoustic_batch(BatchDev b, int sub) {
+  __shared__ DomainDev sd;
+  const int4 m = b.map[blockIdx.x];
+  load_domain(sd, b.doms + m.x);
+  acoustic_body<D>(sd, (unsigned)m.y, (unsigned)m.z, sub);
+}
 #undef SPHBUF_PAIR
 
 int grid_for(const DomainDev& d, int per_sm) { return d.sm_count * per_sm; }
@@ -602,7 +801,28 @@ int launch_drift(const DomainDev& d, cudaStream_t s) {
   return 1;
 }
 
-int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s, bool tvf) {
+int launch_dual(const DomainDev& d, cudaStream_t s) {
+  const int grid = grid_for(d, 8);
+  if (d.g.dim == 2) {
+    k_viscous<2><<<grid, kThreads, 0, s>>>(d);
+    for (int q = 0; q < d.P.dual_n; ++q) k_acoustic<2><<<grid, kThreads, 0, s>>>(d, q);
+    k_dual_finish<2><<<grid, kThreads, 0, s>>>(d);
+  } else {
+    k_viscous<3><<<grid, kThreads, 0, s>>>(d);
+    for (int q = 0; q < d.P.dual_n; ++q) k_acoustic<3><<<grid, kThreads, 0, s>>>(d, q);
+    k_dual_finish<3><<<grid, kThreads, 0, s>>>(d);
+  }
+  return d.P.dual_n + 2;
+}
+
+int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s, bool tvf, int sub) {
+  if (k == K_ACOUSTIC) {
+    if (dim == 2)
+      k_acoustic_batch<2><<<nblocks, kThreads, 0, s>>>(b, sub);
+    else
+      k_acoustic_batch<3><<<nblocks, kThreads, 0, s>>>(b, sub);
+    return 1;
+  }
   if (k == K_FORCE) {
     // the transport-velocity kernel also serves domains with lambda = 0 (p_max stays 0)
     if (dim == 2) {
@@ -629,6 +849,8 @@ int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream
     SPHBUF_CASE(K_NEIGHBOURS, k_neighbours)
     SPHBUF_CASE(K_DENSITY, k_density)
     SPHBUF_CASE(K_DENSITY_DEFER, k_density_deferred)
+    SPHBUF_CASE(K_VISCOUS, k_viscous)
+    SPHBUF_CASE(K_DUAL_FINISH, k_dual_finish)
     SPHBUF_CASE(K_DRIFT, k_drift)
     default:
       return 0;

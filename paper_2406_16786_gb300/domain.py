@@ -161,6 +161,8 @@ class Domain:
             d.set_background_pressure(case.p_bg)
         if getattr(case, "tvf_lambda", 0.0):
             d.set_transport_velocity(case.tvf_lambda)
+        if getattr(case, "dual_substeps", 0):
+            d.set_dual_time_stepping(case.dual_substeps)
         for b in case.buffers:
             d.add_buffer(b)
         if native:
@@ -213,6 +215,10 @@ class Domain:
     def set_background_pressure(self, p_bg: float):
         """Background pressure of the EoS, p = c0^2 (rho - rho0) + p_bg (before the first step)."""
         self._check(self.lib.sphbuf_set_background_pressure(self.h, float(p_bg)), "set_background_pressure")
+
+    def set_dual_time_stepping(self, n_acoustic: int):
+        """Dual-criteria steps: dt is the advection step, made of n_acoustic acoustic steps."""
+        self._check(self.lib.sphbuf_set_dual_time_stepping(self.h, int(n_acoustic)), "set_dual_time_stepping")
 
     def set_transport_velocity(self, lam: float):
         """Transport velocity of Eq. (10) with coefficient lambda (before the first step)."""

@@ -96,6 +96,7 @@ class Case:
     steps: int = 1
     p_bg: float = 0.0  # background pressure of the EoS (Pa); buffer p_b values include it
     tvf_lambda: float = 0.0  # transport velocity (Eq. (10)) coefficient, 5-10 in the paper; 0 = off
+    dual_substeps: int = 0  # dual-criteria time stepping: acoustic steps per dt (0 = single-rate)
 
     @property
     def n(self) -> int:

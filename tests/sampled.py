@@ -32,6 +32,8 @@ def _domain(c, cell, frac, vel32, rho32):
         dom.set_background_pressure(c.p_bg)
     if c.tvf_lambda:
         dom.set_transport_velocity(c.tvf_lambda)
+    if c.dual_substeps:
+        dom.set_dual_time_stepping(c.dual_substeps)
     for b in c.buffers:
         dom.add_buffer(b)
     dom.write_particles(cell, frac, vel32, rho32)

@@ -53,3 +53,35 @@ def test_vipo_converges_to_poiseuille():
     assert acc_p / nsamp == pytest.approx(dP * (1 - a / L), rel=0.1)
     assert sim.escaped == 0
     assert sim.n == sim.n0 + sim.injected.sum() - sim.deleted.sum()
+
+
+@pytest.mark.slow
+def test_vipo_converges_to_poiseuille_dual_time_stepping():
+    # the same channel with the dual-criteria scheme (reading A26): advection step four times
+    # the single-rate step (viscous limit 0.25 h^2/nu), two acoustic steps of CFL 0.5 each
+    case = vipo_case()
+    case.dt = 4.0 * case.dt
+    case.dual_substeps = 2
+    eta = RHO0 * NU
+    dP = 8.0 * eta * L * U / D ** 2
+    sim = OB.OracleSim(case)
+    sim.commit()
+    b0 = sim.buffers[0]
+    a = b0.extent[0]
+    ys = (np.arange(20) + 0.5) * case.dp - 0.5 * D
+    acc_v, nsamp = np.zeros(20), 0
+    for s in range(550):
+        sim.step(1, dual=case.dual_substeps)
+        if s >= 400 and s % 12 == 0:
+            loc = b0.local(sim.pos)
+            mid = np.abs(loc[:, 0] - (0.5 * L - 0.5 * a)) < 2 * case.dp
+            lane = np.clip(np.round((loc[mid, 1] + 0.5 * D) / case.dp - 0.5).astype(int), 0, 19)
+            vx = sim.vel[mid] @ b0.u
+            acc_v += np.bincount(lane, weights=vx, minlength=20) / np.maximum(np.bincount(lane, minlength=20), 1)
+            nsamp += 1
+    v = acc_v / nsamp
+    exact = analytic.poiseuille_plane(ys, dP, eta, L, D)
+    keep = np.abs(ys) <= 0.5 * D - case.dp
+    assert analytic.rmsep(exact[keep], v[keep]) < 0.02
+    assert sim.escaped == 0
+    assert sim.n == sim.n0 + sim.injected.sum() - sim.deleted.sum()

@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--tj-steps", type=int, default=10)
     ap.add_argument("--rot-steps", type=int, default=20)
     ap.add_argument("--no-rotating", action="store_true")
+    ap.add_argument("--no-dual", action="store_true")
     ap.add_argument("--no-tjunction", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -315,6 +316,7 @@ def run_gpu(args):
     batched = None if args.no_batched else run_batched(args, stream, rank, world)
     tjunction = None if args.no_tjunction else run_restricted_vs_full(args, stream)
     rotating = None if args.no_rotating else run_rotating(args, stream)
+    dual = None if args.no_dual else run_dual(args, stream, ms_max / args.steps)
 
     cpu = None
     cpu_bu = None
@@ -357,6 +359,7 @@ def run_gpu(args):
         "batched_vs_plain": batched,
         "restricted_vs_full_16M": tjunction,
         "rotating_buffer_3d": rotating,
+        "dual_time_stepping": dual,
     }
     if rank == 0:
         print(json.dumps(out))
@@ -464,6 +467,46 @@ def run_restricted_vs_full(args, stream):
     res["particle_steps_per_s"] = res["particles"] / (res["restricted_ms_per_step"] / 1e3)
     dom.close()
     return res
+
+
+def run_dual(args, stream, single_ms):
+    """The bench workload with the dual-criteria time stepping (reading A26): advection step
+    0.25 min(h/U, h^2/nu) made of acoustic steps of CFL <= 0.6, against the single-rate step
+    of the main measurement: simulated time per wall-clock second."""
+    import math
+
+    import torch
+
+    from paper_2406_16786_gb300 import workloads
+    from paper_2406_16786_gb300.domain import Domain
+
+    case = workloads.config3(length=args.length)
+    h = case.h_over_dp * case.dp
+    umax = 0.06
+    dt_single = case.dt
+    dt_adv = 0.25 * min(h / umax, h * h / case.nu)
+    n_ac = int(math.ceil(dt_adv / (0.6 * h / (case.c0 + umax))))
+    case.dt = dt_adv
+    case.dual_substeps = n_ac
+    dom = Domain.from_case(case, stream=stream)
+    dom.use_graph(True)
+    dom.step(args.warmup)
+    K = max(5, args.steps // 2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    dom.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    n = dom.count()
+    dom.close()
+    return {"workload": "the bench pipe with dual-criteria time stepping", "particles": n,
+            "advection_dt": dt_adv, "acoustic_steps": n_ac, "ms_per_advection_step": ms,
+            "simulated_s_per_wall_s": dt_adv / (ms / 1e3),
+            "single_rate_dt": dt_single, "single_rate_ms_per_step": single_ms,
+            "single_rate_simulated_s_per_wall_s": dt_single / (single_ms / 1e3),
+            "speedup_in_simulated_time": (dt_adv / ms) / (dt_single / single_ms), "steps": K}
 
 
 def run_rotating(args, stream):

@@ -129,7 +129,11 @@ sphbuf_status sphbuf_set_fluid(sphbuf_domain_t d, const double *pos, const float
 /* Fluid particles in the native cell-relative encoding (see Conventions).  id NULL means
  * 0..n-1.  label NULL means 0 everywhere and Algorithm 1's identification runs at the next
  * step; a non-NULL label array is taken as is (restart).  next_id: first id for new
- * particles (>= every id).  Allowed before the first step and between steps (restart). */
+ * particles (>= every id).  Allowed before the first step and between steps (restart).
+ * The arrays are copied to the device as they are and checked there (cell inside the grid,
+ * offsets in [0, cs32), labels naming a buffer, next_id above every id); a check that fails
+ * returns SPHBUF_ERR_INVALID_ARG and leaves the domain with no particles.  Pinned host
+ * arrays make the copies direct. */
 sphbuf_status sphbuf_write_particles(sphbuf_domain_t d, const int32_t *cell, const float *frac,
                                      const float *vel, const float *rho, const uint32_t *id,
                                      const uint8_t *label, uint64_t n, uint32_t next_id);
@@ -234,7 +238,8 @@ sphbuf_status sphbuf_count(sphbuf_domain_t d, uint64_t *n);
 sphbuf_status sphbuf_grid_info(sphbuf_domain_t d, int32_t dims[3], double *cs, uint64_t *ncell);
 
 /* Copies the sorted particle state to host arrays of capacity cap (synchronises).  Any
- * pointer may be NULL.  Order: by (cell, id). */
+ * pointer may be NULL.  Order: by (cell, id).  frac / vel are gathered into n x dim rows on
+ * the device and copied once each. */
 sphbuf_status sphbuf_read_particles(sphbuf_domain_t d, int32_t *cell, float *frac, float *vel,
                                     float *rho, uint32_t *id, uint8_t *label, uint64_t cap,
                                     uint64_t *n_out);

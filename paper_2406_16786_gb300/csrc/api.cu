@@ -533,6 +533,7 @@ sphbuf_status sphbuf_create_domain(const sphbuf_domain_desc* desc, void* cuda_st
   A(dalloc(d, &rel, kMaxBuffers));
   v.relabel_ids = rel;
   A(dalloc(d, &v.st, 1));
+  A(dalloc(d, &v.io, 4));
   if (e == cudaSuccess) {
     A(cudaMemset(v.cnt, 0, (size_t)v.ncell_pad * sizeof(unsigned)));
     A(cudaMemset(v.cell_start, 0, ((size_t)v.ncell_pad + 1) * sizeof(unsigned)));
@@ -626,46 +627,43 @@ sphbuf_status sphbuf_write_particles(sphbuf_domain_t d, const int32_t* cell, con
   if (!d || (n && (!cell || !frac || !vel || !rho))) return SPHBUF_ERR_INVALID_ARG;
   if (n > d->desc.capacity) return fail(d, SPHBUF_ERR_CAPACITY, "more particles than the domain capacity");
   const int D = d->desc.dim;
-  std::vector<float> tf[3], tv[3];
-  for (int x = 0; x < D; ++x) {
-    tf[x].resize(n);
-    tv[x].resize(n);
-  }
-  uint32_t max_id = 0;
-  for (uint64_t i = 0; i < n; ++i) {
-    if (cell[i] < 0 || (long long)cell[i] >= d->ncell)
-      return fail(d, SPHBUF_ERR_INVALID_ARG, "cell index outside the grid");
-    for (int x = 0; x < D; ++x) {
-      const float f = frac[i * D + x];
-      if (!(f >= 0.f && f < d->cs32)) return fail(d, SPHBUF_ERR_INVALID_ARG, "in-cell offset outside [0, cs)");
-      tf[x][i] = f;
-      tv[x][i] = vel[i * D + x];
-    }
-    if (label && label[i] != 0 && (label[i] == kDead || (size_t)label[i] > d->bufs.size()))
-      return fail(d, SPHBUF_ERR_INVALID_ARG, "label names no buffer");
-    max_id = std::max(max_id, id ? id[i] : (uint32_t)i);
-  }
-  if (n && next_id <= max_id) return fail(d, SPHBUF_ERR_INVALID_ARG, "next_id must exceed every id");
   CK(cudaStreamSynchronize(d->stream));
   Particles& B = d->dev.B;
+  cudaStream_t s = d->stream;
   if (n) {
-    CK(cudaMemcpy(B.cell, cell, n * sizeof(int), cudaMemcpyHostToDevice));
-    for (int x = 0; x < D; ++x) {
-      CK(cudaMemcpy(B.f[x], tf[x].data(), n * sizeof(float), cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(B.v[x], tv[x].data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    // copy the arrays as they are (the AoS frac / vel into the neighbour-list storage, which
+    // the next step rewrites), then check and transpose them on the device
+    float* sf = reinterpret_cast<float*>(d->dev.nb);
+    float* sv = sf + (size_t)n * D;
+    CK(cudaMemcpyAsync(B.cell, cell, n * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(sf, frac, n * D * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(sv, vel, n * D * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.rho, rho, n * sizeof(float), cudaMemcpyHostToDevice, s));
+    if (id) CK(cudaMemcpyAsync(B.id, id, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    if (label) CK(cudaMemcpyAsync(B.label, label, n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(d->dev.io, 0, 4 * sizeof(unsigned), s));
+    launch_ingest(d->dev, sf, sv, (unsigned)n, id != nullptr, label != nullptr, (int)d->bufs.size(), s);
+    CK(cudaGetLastError());
+    unsigned io[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(io, d->dev.io, sizeof(io), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const char* why = (io[0] & 1u)         ? "cell index outside the grid"
+                      : (io[0] & 2u)       ? "in-cell offset outside [0, cs)"
+                      : (io[0] & 4u)       ? "label names no buffer"
+                      : (next_id <= io[1]) ? "next_id must exceed every id"
+                                           : nullptr;
+    if (why) {
+      // the arrays were checked after they were copied: leave the domain empty
+      StepState st;
+      CK(cudaMemcpy(&st, d->dev.st, sizeof(StepState), cudaMemcpyDeviceToHost));
+      st.n = 0;
+      st.n_inj = 0;
+      st.n_del = 0;
+      CK(cudaMemcpy(d->dev.st, &st, sizeof(StepState), cudaMemcpyHostToDevice));
+      d->labels_given = true;
+      d->need_rebuild = true;
+      return fail(d, SPHBUF_ERR_INVALID_ARG, why);
     }
-    CK(cudaMemcpy(B.rho, rho, n * sizeof(float), cudaMemcpyHostToDevice));
-    if (id) {
-      CK(cudaMemcpy(B.id, id, n * sizeof(uint32_t), cudaMemcpyHostToDevice));
-    } else {
-      std::vector<uint32_t> ids(n);
-      std::iota(ids.begin(), ids.end(), 0u);
-      CK(cudaMemcpy(B.id, ids.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice));
-    }
-    if (label)
-      CK(cudaMemcpy(B.label, label, n, cudaMemcpyHostToDevice));
-    else
-      CK(cudaMemset(B.label, 0, n));
   }
   StepState st;
   CK(cudaMemcpy(&st, d->dev.st, sizeof(StepState), cudaMemcpyDeviceToHost));
@@ -887,6 +885,7 @@ sphbuf_status sphbuf_set_buffer_rotation(sphbuf_domain_t d, int buffer_id, const
   }
   b = nb;
   v.rotating = 1;
+  d->dev.any_rot = 1;
   for (int x = 0; x < 3; ++x) {
     v.cC[x] = 0;
     v.fC[x] = 0.f;
@@ -1061,21 +1060,22 @@ sphbuf_status sphbuf_read_particles(sphbuf_domain_t d, int32_t* cell, float* fra
   const int D = d->desc.dim;
   const Particles& A = d->dev.A;
   if (!n) return SPHBUF_OK;
-  if (cell) CK(cudaMemcpy(cell, A.cell, n * sizeof(int), cudaMemcpyDeviceToHost));
-  std::vector<float> tmp(n);
-  for (int x = 0; x < D; ++x) {
-    if (frac) {
-      CK(cudaMemcpy(tmp.data(), A.f[x], n * sizeof(float), cudaMemcpyDeviceToHost));
-      for (uint64_t i = 0; i < n; ++i) frac[i * D + x] = tmp[i];
-    }
-    if (vel) {
-      CK(cudaMemcpy(tmp.data(), A.v[x], n * sizeof(float), cudaMemcpyDeviceToHost));
-      for (uint64_t i = 0; i < n; ++i) vel[i * D + x] = tmp[i];
-    }
+  cudaStream_t st_ = d->stream;
+  if (frac || vel) {
+    // gather the AoS arrays on the device (into the neighbour-list storage, which the next
+    // step rewrites), then copy each array once
+    float* sf = reinterpret_cast<float*>(d->dev.nb);
+    float* sv = sf + (size_t)n * D;
+    launch_egest(d->dev, frac ? sf : nullptr, vel ? sv : nullptr, (unsigned)n, st_);
+    CK(cudaGetLastError());
+    if (frac) CK(cudaMemcpyAsync(frac, sf, n * D * sizeof(float), cudaMemcpyDeviceToHost, st_));
+    if (vel) CK(cudaMemcpyAsync(vel, sv, n * D * sizeof(float), cudaMemcpyDeviceToHost, st_));
   }
-  if (rho) CK(cudaMemcpy(rho, A.rho, n * sizeof(float), cudaMemcpyDeviceToHost));
-  if (id) CK(cudaMemcpy(id, A.id, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
-  if (label) CK(cudaMemcpy(label, A.label, n, cudaMemcpyDeviceToHost));
+  if (cell) CK(cudaMemcpyAsync(cell, A.cell, n * sizeof(int), cudaMemcpyDeviceToHost, st_));
+  if (rho) CK(cudaMemcpyAsync(rho, A.rho, n * sizeof(float), cudaMemcpyDeviceToHost, st_));
+  if (id) CK(cudaMemcpyAsync(id, A.id, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st_));
+  if (label) CK(cudaMemcpyAsync(label, A.label, n, cudaMemcpyDeviceToHost, st_));
+  CK(cudaStreamSynchronize(st_));
   return SPHBUF_OK;
 }
 
@@ -1187,6 +1187,7 @@ struct sphbuf_batch {
   std::vector<sphbuf_domain*> doms;
   int dual_n = 0;    // acoustic steps per step (the same for every domain of the batch)
   bool tvf = false;  // some domain advects with the transport velocity (Eq. (10))
+  bool rot = false;  // some domain has a rotating buffer
   std::vector<uint64_t> n0;  // particles per domain when the batch was made (block shares)
   int dim = 0;
   int sm_count = 1;
@@ -1278,7 +1279,7 @@ static int batch_launch(sphbuf_batch* b, Kern k) {
       return launch_batch_sph(k, b->dim, bd, n, b->stream, b->tvf);
     case K_BUFFER:
     case K_BUFFER_FULL:
-      return launch_batch_buffer(k, b->dim, bd, n, b->stream);
+      return launch_batch_buffer(k, b->dim, bd, n, b->rot, b->stream);
     default:
       return launch_batch_cells(k, b->dim, bd, n, b->stream);
   }
@@ -1404,6 +1405,7 @@ sphbuf_status sphbuf_batch_create(sphbuf_domain_t* domains, int n, void* cuda_st
     b->doms.push_back(d);
     b->n0.push_back(st.n);
     if (d->dev.P.tvf_lambda > 0.f) b->tvf = true;
+    if (d->dev.any_rot) b->rot = true;
   }
   b->sm_count = b->doms[0]->dev.sm_count;
   if (cuda_stream) {

@@ -21,6 +21,7 @@ struct DomainDev {
   float4* pos_b;          // dual-criteria scheme: second copy of pos4 and vr4 (acoustic steps
   float4* vr_b;           //   alternate between the two), and the viscous acceleration of
   float4* av;             //   the advection step
+  unsigned* io;           // 4 words: host-transfer checks (error bits, largest id)
   unsigned* deferred;     // particles left by the fluid density pass (buffer or overflowed list)
   float4* pos4;           // A-order copies for the neighbour passes: (fx, fy, fz, cell x)
   float4* vel4;           //   and (vx, vy, vz, rho); written by the rebuild scatter
@@ -33,6 +34,7 @@ struct DomainDev {
   InjRecord* inj_sorted;  // injections in (buffer, parent id) order
   const BufDev* bufs;     // nbuf entries (frame fields of rotating buffers rewritten per step)
   RotDev* rot;            // kMaxBuffers entries: frame state of rotating buffers
+  int any_rot;            // some buffer rotates (selects the buffer kernel with the turn)
   int nbuf;
   const int* relabel_ids; // buffers that relabel (outflow, bidirectional)
   int nrelabel;
@@ -84,7 +86,7 @@ __device__ __forceinline__ void load_domain(DomainDev& dst, const DomainDev* src
 }
 
 int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s, bool tvf, int sub = 0);
-int launch_batch_buffer(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s);
+int launch_batch_buffer(Kern k, int dim, const BatchDev& b, int nblocks, bool rot, cudaStream_t s);
 int launch_batch_cells(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s);
 int batch_threads(Kern k);  // threads per block of each batched kernel
 
@@ -101,6 +103,13 @@ int launch_apply(const DomainDev& d, cudaStream_t s);
 // cells (kernels_cells.cu)
 int launch_rebuild(const DomainDev& d, bool count_step, cudaStream_t s);
 int finalize_blocks(const DomainDev& d);  // blocks of the finalize pass (candidate segments / 256)
+// Host transfers: the AoS frac / vel arrays staged in device memory <-> the SoA state.
+// ingest: B <- staged arrays (cell, rho, id, label already copied), with the checks of
+// sphbuf_write_particles (io[0] bits: 1 cell, 2 offset, 4 label; io[1] = largest id).
+void launch_ingest(const DomainDev& d, const float* frac, const float* vel, unsigned n, int ids_given,
+                   int labels_given, int nbuf, cudaStream_t s);
+// egest: staged AoS arrays <- A (the sorted state).
+void launch_egest(const DomainDev& d, float* frac, float* vel, unsigned n, cudaStream_t s);
 void launch_decode_positions(const DomainDev& d, double* pos_out, const double lo[3], double cs,
                              cudaStream_t s);
 cudaError_t cell_list_build(const int32_t* cell, const uint32_t* id, const uint8_t* label,

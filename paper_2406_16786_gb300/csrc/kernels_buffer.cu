@@ -110,8 +110,9 @@ __device__ __forceinline__ void stage(const DomainDev& d, Staged& sm, bool flag,
 // used when the particle is still in that cell (the cell it was sorted into).  A particle of
 // a rotating inflow buffer then turns with the buffer about its pivot (Sec. 5.3), after any
 // recycling: positions in the FP32 contract (offset from the pivot, rotated row by row, moved
-// by the difference), velocities rotated row by row.
-template <int D>
+// by the difference), velocities rotated row by row.  ROT: some buffer of the domain rotates
+// (the turn is compiled out otherwise).
+template <int D, bool ROT>
 __device__ __forceinline__ void decide(const DomainDev& d, Staged& sm, int k, unsigned i, const Cand& p, int lin_c,
                                        const int c_c[3], const float cp_c[3]) {
   const BufDev& b = sm.bufs[k];
@@ -140,7 +141,7 @@ __device__ __forceinline__ void decide(const DomainDev& d, Staged& sm, int k, un
       if (b.kind == KIND_BIDIR) del = X[0] < -b.ha;
     }
   }
-  const bool rot = test && b.rotating;
+  const bool rot = ROT && test && b.rotating;
   if (!__any_sync(kFull, inj || del || rot)) return;
   Decision rec;
   rec.k = (unsigned)k;
@@ -168,7 +169,7 @@ __device__ __forceinline__ void decide(const DomainDev& d, Staged& sm, int k, un
 #pragma unroll
     for (int x = 0; x < D; ++x) ok &= move_fold(fw[x], c[x], b.shift[x], g.cs);
   }
-  if (rot) {
+  if (ROT && rot) {
     float Dv[3] = {0.f, 0.f, 0.f}, Dn[3], vn[3];
 #pragma unroll
     for (int x = 0; x < D; ++x)
@@ -210,7 +211,7 @@ __device__ __forceinline__ void decide(const DomainDev& d, Staged& sm, int k, un
 
 // Decisions (restricted to candidate cells, or over all particles), then the block's lists
 // and duplicates.
-template <int D, bool FULL>
+template <int D, bool FULL, bool ROT>
 __device__ __forceinline__ void buffer_body(const DomainDev& d, unsigned bid, unsigned nblk) {
   __shared__ Staged sm;
   const int lane = threadIdx.x & 31;
@@ -247,7 +248,7 @@ __device__ __forceinline__ void buffer_body(const DomainDev& d, unsigned bid, un
       load_cand<D>(d, i, i < n, p);
       const int none[3] = {0, 0, 0};
       const float zero[3] = {0.f, 0.f, 0.f};
-      for (int kk = 0; kk < d.nbuf; ++kk) decide<D>(d, sm, kk, i, p, -1, none, zero);
+      for (int kk = 0; kk < d.nbuf; ++kk) decide<D, ROT>(d, sm, kk, i, p, -1, none, zero);
     }
   } else {
     // four particles per lane are loaded before any is tested (cells of up to 32 particles
@@ -273,7 +274,7 @@ __device__ __forceinline__ void buffer_body(const DomainDev& d, unsigned bid, un
           load_cand<D>(d, i, i < j1, p[q]);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) decide<D>(d, sm, kc, j0 + it * 32 + q * 8 + gl, p[q], lin, cc, cp);
+        for (int q = 0; q < 4; ++q) decide<D, ROT>(d, sm, kc, j0 + it * 32 + q * 8 + gl, p[q], lin, cc, cp);
       }
       s0 = s1;
     }
@@ -290,17 +291,17 @@ __device__ __forceinline__ void buffer_body(const DomainDev& d, unsigned bid, un
   for (unsigned e = threadIdx.x; e < nd; e += blockDim.x) write_deletion(d, sm.del[e], sm.base_del + e);
 }
 
-template <int D, bool FULL>
+template <int D, bool FULL, bool ROT>
 __global__ void __launch_bounds__(kBufThreads) k_buffer(DomainDev d) {
-  buffer_body<D, FULL>(d, blockIdx.x, gridDim.x);
+  buffer_body<D, FULL, ROT>(d, blockIdx.x, gridDim.x);
 }
 
-template <int D, bool FULL>
+template <int D, bool FULL, bool ROT>
 __global__ void __launch_bounds__(kBufThreads) k_buffer_batch(BatchDev b) {
   __shared__ DomainDev sd;
   const int4 m = b.map[blockIdx.x];
   load_domain(sd, b.doms + m.x);
-  buffer_body<D, FULL>(sd, (unsigned)m.y, (unsigned)m.z);
+  buffer_body<D, FULL, ROT>(sd, (unsigned)m.y, (unsigned)m.z);
 }
 
 template <int D>
@@ -342,49 +343,55 @@ int launch_identify(const DomainDev& d, cudaStream_t s) {
   return 1;
 }
 
-int launch_decide(const DomainDev& d, bool full_domain, cudaStream_t s) {
-  int blocks;
-  if (full_domain) {
-    blocks = d.g.dim == 2 ? one_wave(d, k_buffer<2, true>) : one_wave(d, k_buffer<3, true>);
-  } else {
+namespace {
+
+template <int D, bool FULL, bool ROT>
+void launch_decide_t(const DomainDev& d, cudaStream_t s) {
+  const int wave = one_wave(d, k_buffer<D, FULL, ROT>);
+  int blocks = wave;
+  if (!FULL) {
     const int cells_per_block = 4 * (kBufThreads / 32);
-    blocks = (d.nseg + cells_per_block - 1) / cells_per_block;
-    const int wave = d.g.dim == 2 ? one_wave(d, k_buffer<2, false>) : one_wave(d, k_buffer<3, false>);
-    if (blocks > wave) blocks = wave;
-    if (blocks < 1) blocks = 1;
+    blocks = std::max(1, std::min(wave, (d.nseg + cells_per_block - 1) / cells_per_block));
   }
+  k_buffer<D, FULL, ROT><<<blocks, kBufThreads, 0, s>>>(d);
+}
+
+template <int D, bool FULL>
+void launch_batch_t(const BatchDev& b, int nblocks, bool rot, cudaStream_t s) {
+  if (rot)
+    k_buffer_batch<D, FULL, true><<<nblocks, kBufThreads, 0, s>>>(b);
+  else
+    k_buffer_batch<D, FULL, false><<<nblocks, kBufThreads, 0, s>>>(b);
+}
+
+}  // namespace
+
+int launch_decide(const DomainDev& d, bool full_domain, cudaStream_t s) {
+  const bool rot = d.any_rot != 0;
   if (d.g.dim == 2) {
     if (full_domain)
-      k_buffer<2, true><<<blocks, kBufThreads, 0, s>>>(d);
+      rot ? launch_decide_t<2, true, true>(d, s) : launch_decide_t<2, true, false>(d, s);
     else
-      k_buffer<2, false><<<blocks, kBufThreads, 0, s>>>(d);
+      rot ? launch_decide_t<2, false, true>(d, s) : launch_decide_t<2, false, false>(d, s);
   } else {
     if (full_domain)
-      k_buffer<3, true><<<blocks, kBufThreads, 0, s>>>(d);
+      rot ? launch_decide_t<3, true, true>(d, s) : launch_decide_t<3, true, false>(d, s);
     else
-      k_buffer<3, false><<<blocks, kBufThreads, 0, s>>>(d);
+      rot ? launch_decide_t<3, false, true>(d, s) : launch_decide_t<3, false, false>(d, s);
   }
   return 1;
 }
 
 int launch_apply(const DomainDev&, cudaStream_t) { return 0; }  // ids assigned by the rebuild
 
-int launch_batch_buffer(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s) {
-  if (k == K_BUFFER) {
-    if (dim == 2)
-      k_buffer_batch<2, false><<<nblocks, kBufThreads, 0, s>>>(b);
-    else
-      k_buffer_batch<3, false><<<nblocks, kBufThreads, 0, s>>>(b);
-    return 1;
-  }
-  if (k == K_BUFFER_FULL) {
-    if (dim == 2)
-      k_buffer_batch<2, true><<<nblocks, kBufThreads, 0, s>>>(b);
-    else
-      k_buffer_batch<3, true><<<nblocks, kBufThreads, 0, s>>>(b);
-    return 1;
-  }
-  return 0;
+int launch_batch_buffer(Kern k, int dim, const BatchDev& b, int nblocks, bool rot, cudaStream_t s) {
+  if (k != K_BUFFER && k != K_BUFFER_FULL) return 0;
+  const bool full = k == K_BUFFER_FULL;
+  if (dim == 2)
+    full ? launch_batch_t<2, true>(b, nblocks, rot, s) : launch_batch_t<2, false>(b, nblocks, rot, s);
+  else
+    full ? launch_batch_t<3, true>(b, nblocks, rot, s) : launch_batch_t<3, false>(b, nblocks, rot, s);
+  return 1;
 }
 
 }  // namespace sphbuf

@@ -409,6 +409,48 @@ __global__ void __launch_bounds__(256) k_finalize_batch(BatchDev b) {
   finalize_body(b.doms[m.x], 1, (unsigned)m.y, (unsigned)m.z);
 }
 
+__global__ void __launch_bounds__(256) k_ingest(DomainDev d, const float* __restrict__ frac,
+                                                const float* __restrict__ vel, unsigned n, int ids_given,
+                                                int labels_given, int nbuf) {
+  const int D = d.g.dim;
+  unsigned bad = 0, mx = 0;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int c = d.B.cell[i];
+    if (c < 0 || (long long)c >= d.g.ncell) bad |= 1u;
+    for (int x = 0; x < D; ++x) {
+      const float f = frac[(size_t)i * D + x];
+      if (!(f >= 0.f && f < d.g.cs)) bad |= 2u;
+      d.B.f[x][i] = f;
+      d.B.v[x][i] = vel[(size_t)i * D + x];
+    }
+    if (labels_given) {
+      const uint8_t lab = d.B.label[i];
+      if (lab != 0 && (lab == kDead || (int)lab > nbuf)) bad |= 4u;
+    } else {
+      d.B.label[i] = 0;
+    }
+    if (!ids_given) d.B.id[i] = i;
+    mx = max(mx, d.B.id[i]);
+  }
+  bad = __reduce_or_sync(0xFFFFFFFFu, bad);
+  mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+  if ((threadIdx.x & 31) == 0) {
+    if (bad) atomicOr(&d.io[0], bad);
+    atomicMax(&d.io[1], mx);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_egest(DomainDev d, float* __restrict__ frac, float* __restrict__ vel,
+                                               unsigned n) {
+  const int D = d.g.dim;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int x = 0; x < D; ++x) {
+      if (frac) frac[(size_t)i * D + x] = d.A.f[x][i];
+      if (vel) vel[(size_t)i * D + x] = d.A.v[x][i];
+    }
+  }
+}
+
 __global__ void k_decode(DomainDev d, double* out, double lo0, double lo1, double lo2, double cs) {
   const unsigned n = d.st->n;
   const int D = d.g.dim;
@@ -513,6 +555,15 @@ int batch_threads(Kern k) {
     default:
       return 256;
   }
+}
+
+void launch_ingest(const DomainDev& d, const float* frac, const float* vel, unsigned n, int ids_given,
+                   int labels_given, int nbuf, cudaStream_t s) {
+  k_ingest<<<d.sm_count * 4, 256, 0, s>>>(d, frac, vel, n, ids_given, labels_given, nbuf);
+}
+
+void launch_egest(const DomainDev& d, float* frac, float* vel, unsigned n, cudaStream_t s) {
+  k_egest<<<d.sm_count * 4, 256, 0, s>>>(d, frac, vel, n);
 }
 
 void launch_decode_positions(const DomainDev& d, double* pos_out, const double lo[3], double cs,

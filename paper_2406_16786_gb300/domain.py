@@ -258,12 +258,26 @@ class Domain:
         self._check(self.lib.sphbuf_count(self.h, ctypes.byref(n)), "count")
         return n.value
 
-    def read(self):
-        """Sorted particle state as numpy arrays (cell, frac, vel, rho, id, label)."""
+    def read(self, out=None):
+        """Sorted particle state as numpy arrays (cell, frac, vel, rho, id, label).
+
+        ``out`` (optional) holds preallocated arrays of those names, e.g. in pinned host memory,
+        with at least ``count()`` rows; the returned arrays are views of their first rows.
+        """
         n = self.count()
         d = self.dim
-        out = dict(cell=np.zeros(n, np.int32), frac=np.zeros((n, d), np.float32), vel=np.zeros((n, d), np.float32),
-                   rho=np.zeros(n, np.float32), id=np.zeros(n, np.uint32), label=np.zeros(n, np.uint8))
+        if out is None:
+            out = dict(cell=np.zeros(n, np.int32), frac=np.zeros((n, d), np.float32),
+                       vel=np.zeros((n, d), np.float32), rho=np.zeros(n, np.float32), id=np.zeros(n, np.uint32),
+                       label=np.zeros(n, np.uint8))
+        else:
+            want = dict(cell=np.int32, frac=np.float32, vel=np.float32, rho=np.float32, id=np.uint32, label=np.uint8)
+            for key, dt in want.items():
+                a = out[key]
+                if a.dtype != dt or a.shape[0] < n or not a.flags.c_contiguous or (a.ndim == 2 and a.shape[1] != d):
+                    raise ValueError("read(out=...): %s must be a C-contiguous %s array of >= %d rows"
+                                     % (key, np.dtype(dt).name, n))
+            out = {key: out[key][:n] for key in want}
         nn = ctypes.c_uint64()
         self._check(self.lib.sphbuf_read_particles(self.h, _ptr(out["cell"]), _ptr(out["frac"]), _ptr(out["vel"]),
                                                    _ptr(out["rho"]), _ptr(out["id"]), _ptr(out["label"]), n,

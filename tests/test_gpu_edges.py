@@ -30,6 +30,57 @@ def test_empty_domain_steps():
     d.close()
 
 
+@pytest.mark.parametrize("what", ["cell", "frac", "label", "next_id"])
+def test_write_particles_rejects_bad_arrays(what):
+    from paper_2406_16786_gb300.domain import SphbufError
+
+    case = cases.lockstep_cases()[0][1]
+    d = _dom(case)
+    s = d.read()
+    n = s["id"].shape[0]
+    nid = int(s["id"].max()) + 1
+    k = n // 2
+    if what == "cell":
+        s["cell"][k] = d.ncell
+    elif what == "frac":
+        s["frac"][k, 1] = -1e-7
+    elif what == "label":
+        s["label"][k] = len(case.buffers) + 1
+    else:
+        nid = int(s["id"].max())
+    with pytest.raises(SphbufError) as e:
+        d.write_particles(s["cell"], s["frac"], s["vel"], s["rho"], ids=s["id"], labels=s["label"], next_id=nid)
+    assert e.value.status == 1
+    assert d.count() == 0
+    # a correct write afterwards restores the state exactly
+    s2 = _dom(case).read()
+    d.write_particles(s2["cell"], s2["frac"], s2["vel"], s2["rho"], ids=s2["id"], labels=s2["label"],
+                      next_id=int(s2["id"].max()) + 1)
+    back = d.read()
+    for key in s2:
+        assert np.array_equal(back[key], s2[key]), key
+    d.close()
+
+
+def test_read_into_preallocated_arrays():
+    case = cases.lockstep_cases()[0][1]
+    d = _dom(case)
+    d.step(3)
+    ref = d.read()
+    n = ref["id"].shape[0]
+    out = dict(cell=np.full(n + 7, -5, np.int32), frac=np.zeros((n + 7, 2), np.float32),
+               vel=np.zeros((n + 7, 2), np.float32), rho=np.zeros(n + 7, np.float32), id=np.zeros(n + 7, np.uint32),
+               label=np.zeros(n + 7, np.uint8))
+    got = d.read(out=out)
+    for key in ref:
+        assert np.array_equal(got[key], ref[key]), key
+        assert np.shares_memory(got[key], out[key])
+    assert (out["cell"][n:] == -5).all()
+    with pytest.raises(ValueError):
+        d.read(out=dict(out, frac=np.zeros((n, 3), np.float32)))
+    d.close()
+
+
 def test_capacity_overflow_is_latched_not_faulted():
     from paper_2406_16786_gb300.domain import SphbufError
 

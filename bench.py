@@ -278,12 +278,21 @@ def run_gpu(args):
     hbm = peaks.get("hbm_gbs")
     bu_s = per["buffer"] / 1e3
     bu_gbs = bu_bytes / bu_s / 1e9 if bu_s > 0 else None
+    # the floor of a kernel with the buffer kernel's grid (one wave of 4 blocks per SM at most,
+    # 32 candidate cells per block), timed the same way: nothing, one load, two dependent loads
+    from paper_2406_16786_gb300.domain import probe_launch_floor
+
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    bu_blocks = max(1, min((cells + 31) // 32, 4 * sm_count))
+    floor = {"blocks": bu_blocks, "threads": 256}
+    for fl in (False, True):
+        for ld, key in ((0, "empty"), (1, "one_load"), (2, "two_dependent_loads")):
+            floor[key + ("_cold_l2" if fl else "")] = probe_launch_floor(bu_blocks, 256, ld, fl, 50, stream)
 
     # neighbour passes, bound by FP32 arithmetic: algorithmic flops per particle
     pairs = lattice_pairs(dim, case.h_over_dp)          # neighbours within 2h on the lattice
     cands = 27 * (2 * case.h_over_dp) ** dim            # particles in the 27 cells of side 2h
     flops = {"neighbours": cands * 9.0, "density": pairs * 14.0, "force": pairs * 58.0}
-    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     sm_max = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
     alu_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max / 1e12
     kern = {}
@@ -353,7 +362,8 @@ def run_gpu(args):
                                    "unit": "GB/s", "frac": (bu_gbs / hbm) if (bu_gbs and hbm) else None,
                                    "traffic": traffic_of("k_buffer", n_mean), "bytes_per_step": bu_bytes, "candidate_cells": cells,
                                    "candidate_particles": parts, "injected": len(inj), "deleted": len(dels),
-                                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+                                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                                   "launch_floor_us": floor},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io,
                 "steps": e2e_steps},
         "gpu_launches": launches,

@@ -316,6 +316,10 @@ sphbuf_status sphbuf_batch_use_graph(sphbuf_batch_t b, int enable);
  * (cells per warp fixed) are not tuned. */
 sphbuf_status sphbuf_batch_autotune(sphbuf_batch_t b, int trial_steps, unsigned phases, int *best_m,
                                     double ms_per_step[5]);
+/* Sets the grid multiplier m (blocks per SM of the particle kernels, 1..32) without trial
+ * steps, e.g. the autotuner's choice for another batch of the same domains; the domains do
+ * not advance.  SPHBUF_ERR_INVALID_ARG outside 1..32. */
+sphbuf_status sphbuf_batch_set_grid(sphbuf_batch_t b, int m);
 /* Waits for the batch's stream and returns the first latched error of its domains. */
 sphbuf_status sphbuf_batch_sync(sphbuf_batch_t b);
 sphbuf_status sphbuf_batch_destroy(sphbuf_batch_t b);
@@ -340,6 +344,18 @@ sphbuf_status sphbuf_cell_list_build_noalloc(const int32_t *cell, const uint32_t
                                              const uint8_t *label, uint64_t n, uint64_t ncell,
                                              uint32_t *cell_start, uint32_t *order,
                                              void *cuda_stream);
+
+/* Measurement aid (not part of the method): the time of one launch of a probe kernel with the
+ * grid blocks x threads that does nothing (loads = 0), one scattered load per thread
+ * (loads = 1) or two dependent loads per thread (loads = 2), timed with CUDA events around
+ * the launch on cuda_stream (NULL: the default stream) as the domain's phase times are, and
+ * averaged over reps launches after three untimed ones.  flush_l2 != 0 writes 256 MB before
+ * each launch so that the loads miss L2.  It allocates and frees about 128 MB (+ 256 MB with
+ * flush_l2) of device memory per call and synchronises the stream.  The buffer update's time
+ * is read against this floor.  SPHBUF_ERR_INVALID_ARG for blocks < 1, threads outside
+ * 32..1024, loads outside 0..2 or reps < 1. */
+sphbuf_status sphbuf_probe_launch_floor(int blocks, int threads, int loads, int flush_l2, int reps,
+                                        void *cuda_stream, double *us_per_launch);
 
 #ifdef __cplusplus
 }

@@ -61,6 +61,9 @@ SIGNATURES = {
     "sphbuf_batch_step": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_uint]),
     "sphbuf_batch_use_graph": (ctypes.c_int, [vp, ctypes.c_int]),
     "sphbuf_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_uint, P(ctypes.c_int), vp]),
+    "sphbuf_batch_set_grid": (ctypes.c_int, [vp, ctypes.c_int]),
+    "sphbuf_probe_launch_floor": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 vp, P(ctypes.c_double)]),
     "sphbuf_batch_sync": (ctypes.c_int, [vp]),
     "sphbuf_batch_destroy": (ctypes.c_int, [vp]),
     "sphbuf_cell_list_build": (ctypes.c_int, [vp, vp, vp, c_u64, c_u64, vp, vp, vp]),

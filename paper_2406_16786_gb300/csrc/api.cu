@@ -1476,6 +1476,12 @@ sphbuf_status sphbuf_batch_autotune(sphbuf_batch_t b, int trial_steps, unsigned 
   return SPHBUF_OK;
 }
 
+sphbuf_status sphbuf_batch_set_grid(sphbuf_batch_t b, int m) {
+  if (!b || m < 1 || m > 32) return SPHBUF_ERR_INVALID_ARG;
+  BCK(cudaStreamSynchronize(b->stream));
+  return batch_build_maps(b, m);
+}
+
 sphbuf_status sphbuf_batch_sync(sphbuf_batch_t b) {
   if (!b) return SPHBUF_ERR_INVALID_ARG;
   BCK(cudaStreamSynchronize(b->stream));

@@ -1,0 +1,121 @@
+"""Full-size parity on the other workloads, in the launch configuration the bench times.
+
+* 10 x 1 m channel (16 k particles, plug velocity inlet U = 1, pressure outlet): kinematic
+  steps bit-exact against the FP32-mode oracle; one physics step with every particle checked
+  against the FP64 oracle; the whole 200-step run with the count and mass invariants and the
+  inlet schedule (buffer particles move at exactly U, so each of the inlet's lanes injects
+  floor or ceil of U T / dp particles).
+* 15.4 M-particle T-junction: kinematic steps bit-exact (velocity inlet, two pressure outlets
+  at arbitrary orientations); one physics step sampled against the FP64 oracle.
+* 64 star channels stepped as one batch in graph replay with the autotuner's grid: kinematic
+  steps bit-exact for every domain; one physics step of the batch sampled on three domains.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2406_16786_gb300 import workloads as wl
+from tests import sampled
+
+pytestmark = pytest.mark.gpu
+
+
+def test_channel_kinematic_bit_exact():
+    c = wl.config1()
+    # every particle moves: 0.6 dp per step along the channel plus a shear
+    v = wl.shear_velocity(c, u0=8.0, seed=11) + np.array([20.0, 0.0])
+    assert sampled.kinematic_bit_exact(c, v, 6) > 0
+
+
+def test_channel_physics_step_every_particle():
+    c = wl.config1()
+    assert sampled.physics_step_sampled(c, sample_size=c.n) > 0.99 * c.n
+
+
+def test_channel_full_run_invariants_and_inlet_schedule():
+    from paper_2406_16786_gb300.domain import Domain
+
+    c = wl.config1()
+    dom = Domain.from_case(c)
+    dom.use_graph(True)
+    n0 = dom.count()
+    steps = 200
+    dom.step(steps)
+    dom.sync()
+    cin, cout = dom.counters(0), dom.counters(1)
+    g = dom.global_counters()
+    assert g["escaped"] == 0 and g["steps"] == steps
+    n = dom.count()
+    assert n == n0 + cin["injected"] + cout["injected"] - cin["deleted"] - cout["deleted"]
+    mass = c.rho0 * c.dp ** 2
+    net = (cin["mass_in"] + cout["mass_in"]) - (cin["mass_out"] + cout["mass_out"])
+    assert abs(net - (n - n0) * mass) <= 1e-9 * max(1.0, abs(net))
+    # the inlet's lanes: rows of buffer particles across the channel at spacing dp
+    lanes = int(round(c.buffers[0].extent[1] / c.dp))
+    crossings = 1.0 * steps * c.dt / c.dp
+    assert lanes * (math.floor(crossings) - 1) <= cin["injected"] <= lanes * (math.ceil(crossings) + 1)
+    assert cout["deleted"] > 0 or cout["injected"] == 0
+    dom.close()
+
+
+@pytest.fixture(scope="module")
+def tjunction():
+    return wl.config4()
+
+
+def test_tjunction_full_size_kinematic_bit_exact(tjunction):
+    c = tjunction
+    assert c.n > 15_000_000
+    assert sampled.kinematic_bit_exact(c, c.fluid_vel * 20.0, 2) > 0
+
+
+def test_tjunction_full_size_physics_step_sampled(tjunction):
+    assert sampled.physics_step_sampled(tjunction) > 1000
+
+
+@pytest.fixture(scope="module")
+def stars():
+    return wl.config5()
+
+
+@pytest.fixture(scope="module")
+def tuned_grid(stars):
+    from paper_2406_16786_gb300.domain import Batch, Domain
+
+    doms = [Domain.from_case(c) for c in stars]
+    b = Batch(doms)
+    m, _ = b.autotune(trial_steps=2)
+    b.close()
+    for d in doms:
+        d.close()
+    return m
+
+
+def test_batched_stars_kinematic_bit_exact(stars, tuned_grid):
+    vels = [wl.shear_velocity(c, u0=8.0, seed=40 + q) + 10.0 * c.buffers[0].rotation[0, :2]
+            for q, c in enumerate(stars)]
+    assert sampled.batched_kinematic_bit_exact(stars, vels, 2, tuned_grid) > 0
+
+
+def test_batched_stars_physics_step_sampled(stars, tuned_grid):
+    from paper_2406_16786_gb300.domain import Batch
+
+    doms = []
+    for c in stars:
+        cell, frac = wl.encode_positions(c.fluid_pos, c.lo, c.cs, c.grid_dims())
+        doms.append(sampled._domain(c, cell, frac, c.fluid_vel.astype(np.float32), c.fluid_rho.astype(np.float32)))
+    n0 = [d.count() for d in doms]
+    b = Batch(doms)
+    b.set_grid(tuned_grid)
+    b.use_graph(True)
+    b.step(1)
+    b.sync()
+    sizes = [c.n for c in stars]
+    pick = {int(np.argmax(sizes)), int(np.argmin(sizes))}
+    pick.add(next(q for q, c in enumerate(stars) if len(c.buffers) == 1))
+    for q in sorted(pick):
+        assert sampled.check_physics_step(stars[q], doms[q], n0[q], sample_size=800) > 500
+    b.close()
+    for d in doms:
+        d.close()

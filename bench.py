@@ -8,7 +8,10 @@ One step = density, force + BC + drift, buffer decisions + apply (Algorithms 1-3
 rebuild + relabel: the whole hot path.  ``value`` is particle-steps/s with the state resident
 in HBM (graph replays, CUDA events on the domain's stream); the particle state (~300 MB) is
 larger than L2, so no flush is needed between steps.  ``e2e`` runs the same step through the
-C ABI with host arrays (write_particles, step, read_particles) inside the timed region.
+C ABI with pinned host arrays inside the timed region: every step writes its whole input
+state and reads its whole result back, pipelined (write_particles_async, step,
+read_particles_async; the copies overlap the neighbouring steps) and, as ``e2e.synchronous``,
+with the blocking calls.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -64,7 +67,7 @@ def parse():
     ap.add_argument("--no-rotating", action="store_true")
     ap.add_argument("--no-dual", action="store_true")
     ap.add_argument("--no-tjunction", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -302,28 +305,58 @@ def run_gpu(args):
                     "frac": tf / alu_peak}
     dom_ph = max(kern, key=lambda k: kern[k]["ms"])
 
-    # end to end through the C ABI with host arrays
+    # end to end through the C ABI with pinned host arrays: every step writes its whole input
+    # state from the host, steps, and reads the whole result back
     st = dom.read()
     nn = st["id"].shape[0]
-    e2e_steps = args.e2e_steps
+    K_e2e = max(1, args.e2e_steps)
     pin = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in st.items()}
-    # pinned result arrays with room for the particle count to grow over the steps
-    room = nn + nn // 8 + 1024
-    pout = {k: torch.empty(room * v[:1].nbytes, dtype=torch.uint8).pin_memory().numpy().view(v.dtype)
-            .reshape((room,) + v.shape[1:]) for k, v in st.items()}
+    # pinned result arrays with room for the count to grow in a step (a larger count fails)
+    room = nn + 4096
+    pouts = [{k: torch.empty(room * v[:1].nbytes, dtype=torch.uint8).pin_memory().numpy().view(v.dtype)
+              .reshape((room,) + v.shape[1:]) for k, v in st.items()} for _ in range(2)]
     nid = dom.global_counters()["next_id"]
+    # (a) synchronous calls: write, step, read one after the other
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(max(1, e2e_steps)):
+    for _ in range(K_e2e):
         dom.write_particles(pin["cell"], pin["frac"], pin["vel"], pin["rho"], ids=pin["id"], labels=pin["label"],
                             next_id=nid)
         dom.step(1)
-        back = dom.read(out=pout)
+        dom.read(out=pouts[0])
+    torch.cuda.synchronize()
+    te_sync = time.perf_counter() - t0
+    # (b) pipelined calls: the copies of step k+1's input and of step k-1's result run on the
+    # domain's transfer streams while step k computes
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for q in range(K_e2e):
+        dom.write_particles_async(pin["cell"], pin["frac"], pin["vel"], pin["rho"], ids=pin["id"],
+                                  labels=pin["label"], next_id=nid)
+        dom.step(1)
+        dom.read_async(pouts[q % 2])
+    counts = dom.io_wait()
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
-    bytes_io = nn * state_bytes
-    e2e_value = world * nn * max(1, e2e_steps) / te
-    del back
+    assert len(counts) == K_e2e and all(abs(c - nn) < 4096 for c in counts)
+    # the host link itself: one pinned <-> device copy of the same byte count each way
+    hb = torch.empty(nn * state_bytes, dtype=torch.uint8).pin_memory()
+    db = torch.empty(nn * state_bytes, dtype=torch.uint8, device="cuda")
+    link = {}
+    for key, dst, src in (("h2d_gbs", db, hb), ("d2h_gbs", hb, db)):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(5):
+            dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        link[key] = 5 * nn * state_bytes / (time.perf_counter() - t1) / 1e9
+    del hb, db
+    e2e = {"value": world * nn * K_e2e / te, "unit": UNIT, "h2d_bytes_per_step": nn * state_bytes,
+           "d2h_bytes_per_step": room * state_bytes, "steps": K_e2e,
+           "mode": "pipelined: write_particles_async / step / read_particles_async per step, one io_wait",
+           "synchronous": {"value": world * nn * K_e2e / te_sync, "d2h_bytes_per_step": nn * state_bytes},
+           "host_link": link}
 
     dom.close()
     batched = None if args.no_batched else run_batched(args, stream, rank, world)
@@ -364,8 +397,7 @@ def run_gpu(args):
                                    "candidate_particles": parts, "injected": len(inj), "deleted": len(dels),
                                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                                    "launch_floor_us": floor},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io,
-                "steps": e2e_steps},
+        "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,

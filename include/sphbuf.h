@@ -138,6 +138,35 @@ sphbuf_status sphbuf_write_particles(sphbuf_domain_t d, const int32_t *cell, con
                                      const float *vel, const float *rho, const uint32_t *id,
                                      const uint8_t *label, uint64_t n, uint32_t next_id);
 
+/* Pipelined host transfers (overlap the copies of one step with the work of another).
+ * sphbuf_write_particles_async: the arrays of sphbuf_write_particles, copied to a device
+ * staging area on a stream of the domain's own, so that the copies overlap the work already
+ * enqueued on the domain's stream; the next step (or read) waits for them, checks the arrays
+ * on the device and takes them into the state.  A failed check is latched: the next
+ * synchronising call returns SPHBUF_ERR_INVALID_ARG, and the domain is left with no
+ * particles.  Only one asynchronous write may wait for a step: another one before that
+ * returns SPHBUF_ERR_STATE; a synchronous write replaces it.
+ * sphbuf_read_particles_async: after the work enqueued so far, the device gathers the sorted
+ * state (as sphbuf_read_particles) into a second staging area and the first cap rows of each
+ * array (frac, vel: cap x dim) are copied to the host on another stream, overlapping later
+ * steps; rows past the particle count hold unspecified values.  All six arrays are required.
+ * *n_out (may be NULL) receives the particle count when sphbuf_io_wait returns, which
+ * returns SPHBUF_ERR_CAPACITY if the count exceeded cap (only cap rows were copied).
+ * Up to 64 reads may be pending; the 65th waits for the others first.
+ * sphbuf_io_wait: waits for every pending asynchronous copy and for the domain's stream,
+ * fills n_out of the pending reads and returns any latched error.
+ * Host arrays: page-locked (cudaHostAlloc, cudaHostRegister, torch pin_memory) for the copies
+ * to be asynchronous; the caller keeps them valid and unchanged until sphbuf_io_wait returns.
+ * The first asynchronous call allocates two staging areas of (13 + 8 dim) bytes per particle
+ * of capacity, two streams and four events, held until sphbuf_destroy. */
+sphbuf_status sphbuf_write_particles_async(sphbuf_domain_t d, const int32_t *cell, const float *frac,
+                                           const float *vel, const float *rho, const uint32_t *id,
+                                           const uint8_t *label, uint64_t n, uint32_t next_id);
+sphbuf_status sphbuf_read_particles_async(sphbuf_domain_t d, int32_t *cell, float *frac, float *vel,
+                                          float *rho, uint32_t *id, uint8_t *label, uint64_t cap,
+                                          uint64_t *n_out);
+sphbuf_status sphbuf_io_wait(sphbuf_domain_t d);
+
 /* Adds one in-/outlet buffer: box centre O' (origin), frame R (rotation, see Conventions),
  * extent = (a, b, c): width along X', length along Y', height along Z' (c unused in 2-D).
  * R must be orthonormal with det +1 (tolerance 1e-9).  Candidate regions of two buffers

@@ -62,6 +62,9 @@ SIGNATURES = {
     "sphbuf_batch_use_graph": (ctypes.c_int, [vp, ctypes.c_int]),
     "sphbuf_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_uint, P(ctypes.c_int), vp]),
     "sphbuf_batch_set_grid": (ctypes.c_int, [vp, ctypes.c_int]),
+    "sphbuf_write_particles_async": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, ctypes.c_uint64, ctypes.c_uint32]),
+    "sphbuf_read_particles_async": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, ctypes.c_uint64, P(ctypes.c_uint64)]),
+    "sphbuf_io_wait": (ctypes.c_int, [vp]),
     "sphbuf_probe_launch_floor": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  vp, P(ctypes.c_double)]),
     "sphbuf_batch_sync": (ctypes.c_int, [vp]),

@@ -62,6 +62,24 @@ struct sphbuf_domain {
   bool use_graph = false;
   cudaGraphExec_t graph = nullptr;
   unsigned graph_phases = 0;
+  // pipelined host transfers (set up by the first asynchronous call): copies on two streams
+  // of their own, staged in device memory, ordered against the domain's stream by events
+  struct PendingRead {
+    uint64_t* n_out;
+    uint64_t cap;
+    int slot;
+  };
+  cudaStream_t io_h2d = nullptr, io_d2h = nullptr;
+  cudaEvent_t ev_ingest = nullptr, ev_h2d = nullptr, ev_egest = nullptr, ev_d2h = nullptr;
+  unsigned char* in_stage = nullptr;
+  unsigned char* out_stage = nullptr;
+  unsigned* n_pinned = nullptr;  // host ring of the particle counts of pending reads
+  int ring_next = 0;
+  std::vector<PendingRead> reads;
+  bool ingest_pending = false;
+  uint64_t w_n = 0;
+  uint32_t w_next_id = 0;
+  bool w_ids = false, w_labels = false;
   std::string err;
 };
 
@@ -332,11 +350,55 @@ sphbuf_status read_state(sphbuf_domain* d, StepState* out) {
   CK(cudaStreamSynchronize(d->stream));
   CK(cudaMemcpy(out, d->dev.st, sizeof(StepState), cudaMemcpyDeviceToHost));
   if (out->status) {
-    const char* what = out->status == SPHBUF_ERR_CAPACITY ? "particle or decision-list capacity exceeded"
-                       : out->status == SPHBUF_ERR_NAN    ? "non-finite particle position"
-                                                          : "device-side error";
+    const char* what = out->status == SPHBUF_ERR_CAPACITY      ? "particle or decision-list capacity exceeded"
+                       : out->status == SPHBUF_ERR_NAN         ? "non-finite particle position"
+                       : out->status == SPHBUF_ERR_INVALID_ARG ? "asynchronously written arrays failed the checks "
+                                                                 "(cell, offset, label or next_id)"
+                                                               : "device-side error";
     return fail(d, (sphbuf_status)out->status, what);
   }
+  return SPHBUF_OK;
+}
+
+// Device staging of the pipelined transfers: the six particle arrays of up to C particles
+// (cell, frac rows, vel rows, rho, id, label) and a count word.
+struct Stage {
+  int* cell;
+  float* frac;
+  float* vel;
+  float* rho;
+  unsigned* id;
+  uint8_t* label;
+  unsigned* count;
+};
+
+size_t stage_bytes(size_t C, int D) { return ((13 * C + 8 * C * (size_t)D + 15) / 16) * 16 + 16; }
+
+Stage stage_of(unsigned char* base, size_t C, int D) {
+  Stage s;
+  s.cell = reinterpret_cast<int*>(base);
+  s.frac = reinterpret_cast<float*>(base + 4 * C);
+  s.vel = reinterpret_cast<float*>(base + 4 * C + 4 * C * D);
+  s.rho = reinterpret_cast<float*>(base + 4 * C + 8 * C * D);
+  s.id = reinterpret_cast<unsigned*>(base + 8 * C + 8 * C * D);
+  s.label = base + 12 * C + 8 * C * D;
+  s.count = reinterpret_cast<unsigned*>(base + stage_bytes(C, D) - 16);
+  return s;
+}
+
+constexpr int kIoRing = 64;  // pending asynchronous reads at most
+
+sphbuf_status ensure_io(sphbuf_domain* d) {
+  if (d->io_h2d) return SPHBUF_OK;
+  const size_t C = d->desc.capacity;
+  const int D = d->desc.dim;
+  CK(dalloc(d, &d->in_stage, stage_bytes(C, D)));
+  CK(dalloc(d, &d->out_stage, stage_bytes(C, D)));
+  CK(cudaHostAlloc(reinterpret_cast<void**>(&d->n_pinned), kIoRing * sizeof(unsigned), cudaHostAllocDefault));
+  for (cudaEvent_t* e : {&d->ev_ingest, &d->ev_h2d, &d->ev_egest, &d->ev_d2h})
+    CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  CK(cudaStreamCreateWithFlags(&d->io_d2h, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&d->io_h2d, cudaStreamNonBlocking));
   return SPHBUF_OK;
 }
 
@@ -358,6 +420,18 @@ sphbuf_status commit(sphbuf_domain* d) {
     d->committed = true;
   }
   if (d->need_rebuild) {
+    if (d->ingest_pending) {
+      // the staged arrays of an asynchronous write, once their copies have landed
+      CK(cudaStreamWaitEvent(d->stream, d->ev_h2d, 0));
+      const Stage in = stage_of(d->in_stage, d->desc.capacity, d->desc.dim);
+      launch_ingest_staged(d->dev, in.cell, in.frac, in.vel, in.rho, d->w_ids ? in.id : nullptr,
+                           d->w_labels ? in.label : nullptr, (unsigned)d->w_n, d->w_next_id, (int)d->bufs.size(),
+                           d->stream);
+      CK(cudaGetLastError());
+      CK(cudaEventRecord(d->ev_ingest, d->stream));
+      d->launches += d->w_n ? 2 : 1;
+      d->ingest_pending = false;
+    }
     if (!d->labels_given) d->launches += launch_identify(d->dev, d->stream);
     d->launches += launch_rebuild(d->dev, false, d->stream);
     CK(cudaGetLastError());
@@ -551,6 +625,14 @@ sphbuf_status sphbuf_create_domain(const sphbuf_domain_desc* desc, void* cuda_st
 sphbuf_status sphbuf_destroy(sphbuf_domain_t d) {
   if (!d) return SPHBUF_ERR_INVALID_ARG;
   if (d->stream) cudaStreamSynchronize(d->stream);
+  for (cudaStream_t s : {d->io_h2d, d->io_d2h})
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  for (cudaEvent_t e : {d->ev_ingest, d->ev_h2d, d->ev_egest, d->ev_d2h})
+    if (e) cudaEventDestroy(e);
+  if (d->n_pinned) cudaFreeHost(d->n_pinned);
   if (d->graph) cudaGraphExecDestroy(d->graph);
   for (void* p : d->allocs) cudaFree(p);
   if (d->seg_mem) cudaFree(d->seg_mem);
@@ -628,6 +710,7 @@ sphbuf_status sphbuf_write_particles(sphbuf_domain_t d, const int32_t* cell, con
   if (n > d->desc.capacity) return fail(d, SPHBUF_ERR_CAPACITY, "more particles than the domain capacity");
   const int D = d->desc.dim;
   CK(cudaStreamSynchronize(d->stream));
+  d->ingest_pending = false;  // replaces a pending asynchronous write
   Particles& B = d->dev.B;
   cudaStream_t s = d->stream;
   if (n) {
@@ -676,6 +759,92 @@ sphbuf_status sphbuf_write_particles(sphbuf_domain_t d, const int32_t* cell, con
   d->labels_given = label != nullptr;
   d->need_rebuild = true;
   return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_write_particles_async(sphbuf_domain_t d, const int32_t* cell, const float* frac,
+                                           const float* vel, const float* rho, const uint32_t* id,
+                                           const uint8_t* label, uint64_t n, uint32_t next_id) {
+  if (!d || (n && (!cell || !frac || !vel || !rho))) return SPHBUF_ERR_INVALID_ARG;
+  if (n > d->desc.capacity) return fail(d, SPHBUF_ERR_CAPACITY, "more particles than the domain capacity");
+  if (d->ingest_pending)
+    return fail(d, SPHBUF_ERR_STATE, "the previous asynchronous write has not been taken by a step or read yet");
+  sphbuf_status s = ensure_io(d);
+  if (s != SPHBUF_OK) return s;
+  const int D = d->desc.dim;
+  const Stage in = stage_of(d->in_stage, d->desc.capacity, D);
+  cudaStream_t q = d->io_h2d;
+  // the staging is free once the previous ingest has read it
+  CK(cudaStreamWaitEvent(q, d->ev_ingest, 0));
+  if (n) {
+    CK(cudaMemcpyAsync(in.cell, cell, n * sizeof(int32_t), cudaMemcpyHostToDevice, q));
+    CK(cudaMemcpyAsync(in.frac, frac, n * D * sizeof(float), cudaMemcpyHostToDevice, q));
+    CK(cudaMemcpyAsync(in.vel, vel, n * D * sizeof(float), cudaMemcpyHostToDevice, q));
+    CK(cudaMemcpyAsync(in.rho, rho, n * sizeof(float), cudaMemcpyHostToDevice, q));
+    if (id) CK(cudaMemcpyAsync(in.id, id, n * sizeof(uint32_t), cudaMemcpyHostToDevice, q));
+    if (label) CK(cudaMemcpyAsync(in.label, label, n, cudaMemcpyHostToDevice, q));
+  }
+  CK(cudaEventRecord(d->ev_h2d, q));
+  d->ingest_pending = true;
+  d->w_n = n;
+  d->w_next_id = next_id;
+  d->w_ids = id != nullptr;
+  d->w_labels = label != nullptr;
+  d->labels_given = label != nullptr;
+  d->need_rebuild = true;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_read_particles_async(sphbuf_domain_t d, int32_t* cell, float* frac, float* vel, float* rho,
+                                          uint32_t* id, uint8_t* label, uint64_t cap, uint64_t* n_out) {
+  if (!d || !cell || !frac || !vel || !rho || !id || !label) return SPHBUF_ERR_INVALID_ARG;
+  if (!d->committed && !d->need_rebuild) return fail(d, SPHBUF_ERR_STATE, "no particles written");
+  sphbuf_status s = SPHBUF_OK;
+  if (d->need_rebuild && (s = commit(d)) != SPHBUF_OK) return s;
+  if ((s = ensure_io(d)) != SPHBUF_OK) return s;
+  if (d->reads.size() >= (size_t)kIoRing && (s = sphbuf_io_wait(d)) != SPHBUF_OK) return s;
+  const int D = d->desc.dim;
+  const uint64_t rows = std::min<uint64_t>(cap, d->desc.capacity);
+  const Stage out = stage_of(d->out_stage, d->desc.capacity, D);
+  // the staging is free once the previous read's copies have left it
+  CK(cudaStreamWaitEvent(d->stream, d->ev_d2h, 0));
+  launch_egest_staged(d->dev, out.cell, out.frac, out.vel, out.rho, out.id, out.label, out.count, (unsigned)rows,
+                      d->stream);
+  CK(cudaGetLastError());
+  d->launches += 1;
+  CK(cudaEventRecord(d->ev_egest, d->stream));
+  cudaStream_t q = d->io_d2h;
+  CK(cudaStreamWaitEvent(q, d->ev_egest, 0));
+  if (rows) {
+    CK(cudaMemcpyAsync(cell, out.cell, rows * sizeof(int32_t), cudaMemcpyDeviceToHost, q));
+    CK(cudaMemcpyAsync(frac, out.frac, rows * D * sizeof(float), cudaMemcpyDeviceToHost, q));
+    CK(cudaMemcpyAsync(vel, out.vel, rows * D * sizeof(float), cudaMemcpyDeviceToHost, q));
+    CK(cudaMemcpyAsync(rho, out.rho, rows * sizeof(float), cudaMemcpyDeviceToHost, q));
+    CK(cudaMemcpyAsync(id, out.id, rows * sizeof(uint32_t), cudaMemcpyDeviceToHost, q));
+    CK(cudaMemcpyAsync(label, out.label, rows, cudaMemcpyDeviceToHost, q));
+  }
+  const int slot = d->ring_next;
+  d->ring_next = (d->ring_next + 1) % kIoRing;
+  CK(cudaMemcpyAsync(d->n_pinned + slot, out.count, sizeof(unsigned), cudaMemcpyDeviceToHost, q));
+  CK(cudaEventRecord(d->ev_d2h, q));
+  d->reads.push_back({n_out, cap, slot});
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_io_wait(sphbuf_domain_t d) {
+  if (!d) return SPHBUF_ERR_INVALID_ARG;
+  if (d->io_h2d) CK(cudaStreamSynchronize(d->io_h2d));
+  if (d->io_d2h) CK(cudaStreamSynchronize(d->io_d2h));
+  sphbuf_status ret = SPHBUF_OK;
+  for (const sphbuf_domain::PendingRead& r : d->reads) {
+    const uint64_t n = d->n_pinned[r.slot];
+    if (r.n_out) *r.n_out = n;
+    if (n > r.cap && ret == SPHBUF_OK)
+      ret = fail(d, SPHBUF_ERR_CAPACITY, "host arrays of an asynchronous read smaller than the particle count");
+  }
+  d->reads.clear();
+  StepState st;
+  sphbuf_status s = read_state(d, &st);
+  return ret != SPHBUF_OK ? ret : s;
 }
 
 sphbuf_status sphbuf_set_fluid(sphbuf_domain_t d, const double* pos, const float* vel, const float* rho, uint64_t n) {

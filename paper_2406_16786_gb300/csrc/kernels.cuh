@@ -110,6 +110,16 @@ void launch_ingest(const DomainDev& d, const float* frac, const float* vel, unsi
                    int labels_given, int nbuf, cudaStream_t s);
 // egest: staged AoS arrays <- A (the sorted state).
 void launch_egest(const DomainDev& d, float* frac, float* vel, unsigned n, cudaStream_t s);
+// Pipelined host transfers.  ingest_staged: B <- arrays of n particles staged in device memory
+// (id / label NULL: 0..n-1 / 0), with the checks of sphbuf_write_particles; a failed check
+// latches SPHBUF_ERR_INVALID_ARG and leaves the domain with no particles, otherwise n and
+// next_id become the state's.  egest_staged: rows [0, min(n, cap)) of A into staged arrays and
+// n (the particle count, from the device state) into *n_out.
+void launch_ingest_staged(const DomainDev& d, const int* cell, const float* frac, const float* vel, const float* rho,
+                          const unsigned* id, const uint8_t* label, unsigned n, unsigned next_id, int nbuf,
+                          cudaStream_t s);
+void launch_egest_staged(const DomainDev& d, int* cell, float* frac, float* vel, float* rho, unsigned* id,
+                         uint8_t* label, unsigned* n_out, unsigned cap, cudaStream_t s);
 void launch_decode_positions(const DomainDev& d, double* pos_out, const double lo[3], double cs,
                              cudaStream_t s);
 cudaError_t cell_list_build(const int32_t* cell, const uint32_t* id, const uint8_t* label,

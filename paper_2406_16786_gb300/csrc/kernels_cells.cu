@@ -440,6 +440,70 @@ __global__ void __launch_bounds__(256) k_ingest(DomainDev d, const float* __rest
   }
 }
 
+__global__ void __launch_bounds__(256) k_ingest_staged(DomainDev d, const int* __restrict__ cell,
+                                                       const float* __restrict__ frac, const float* __restrict__ vel,
+                                                       const float* __restrict__ rho, const unsigned* __restrict__ id,
+                                                       const uint8_t* __restrict__ label, unsigned n, int nbuf) {
+  const int D = d.g.dim;
+  unsigned bad = 0, mx = 0;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int c = cell[i];
+    if (c < 0 || (long long)c >= d.g.ncell) bad |= 1u;
+    d.B.cell[i] = c;
+    for (int x = 0; x < D; ++x) {
+      const float f = frac[(size_t)i * D + x];
+      if (!(f >= 0.f && f < d.g.cs)) bad |= 2u;
+      d.B.f[x][i] = f;
+      d.B.v[x][i] = vel[(size_t)i * D + x];
+    }
+    d.B.rho[i] = rho[i];
+    const uint8_t lab = label ? label[i] : (uint8_t)0;
+    if (lab != 0 && (lab == kDead || (int)lab > nbuf)) bad |= 4u;
+    d.B.label[i] = lab;
+    const unsigned q = id ? id[i] : i;
+    d.B.id[i] = q;
+    mx = max(mx, q);
+  }
+  bad = __reduce_or_sync(0xFFFFFFFFu, bad);
+  mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+  if ((threadIdx.x & 31) == 0) {
+    if (bad) atomicOr(&d.io[0], bad);
+    atomicMax(&d.io[1], mx);
+  }
+}
+
+// The checks of the staged arrays decided: the state takes (n, next_id), or no particles
+// and SPHBUF_ERR_INVALID_ARG.
+__global__ void k_ingest_finish(DomainDev d, unsigned n, unsigned next_id) {
+  StepState* st = d.st;
+  const bool ok = n == 0 || (d.io[0] == 0 && next_id > d.io[1]);
+  st->n = ok ? n : 0u;
+  st->n_inj = 0;
+  st->n_del = 0;
+  st->next_id = next_id;
+  st->status = ok ? 0 : 1 /* SPHBUF_ERR_INVALID_ARG */;
+}
+
+__global__ void __launch_bounds__(256) k_egest_staged(DomainDev d, int* __restrict__ cell, float* __restrict__ frac,
+                                                      float* __restrict__ vel, float* __restrict__ rho,
+                                                      unsigned* __restrict__ id, uint8_t* __restrict__ label,
+                                                      unsigned* n_out, unsigned cap) {
+  const int D = d.g.dim;
+  const unsigned n = d.st->n;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *n_out = n;
+  const unsigned m = min(n, cap);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    cell[i] = d.A.cell[i];
+    for (int x = 0; x < D; ++x) {
+      frac[(size_t)i * D + x] = d.A.f[x][i];
+      vel[(size_t)i * D + x] = d.A.v[x][i];
+    }
+    rho[i] = d.A.rho[i];
+    id[i] = d.A.id[i];
+    label[i] = d.A.label[i];
+  }
+}
+
 __global__ void __launch_bounds__(256) k_egest(DomainDev d, float* __restrict__ frac, float* __restrict__ vel,
                                                unsigned n) {
   const int D = d.g.dim;
@@ -560,6 +624,19 @@ int batch_threads(Kern k) {
 void launch_ingest(const DomainDev& d, const float* frac, const float* vel, unsigned n, int ids_given,
                    int labels_given, int nbuf, cudaStream_t s) {
   k_ingest<<<d.sm_count * 4, 256, 0, s>>>(d, frac, vel, n, ids_given, labels_given, nbuf);
+}
+
+void launch_ingest_staged(const DomainDev& d, const int* cell, const float* frac, const float* vel, const float* rho,
+                          const unsigned* id, const uint8_t* label, unsigned n, unsigned next_id, int nbuf,
+                          cudaStream_t s) {
+  cudaMemsetAsync(d.io, 0, 4 * sizeof(unsigned), s);
+  if (n) k_ingest_staged<<<d.sm_count * 4, 256, 0, s>>>(d, cell, frac, vel, rho, id, label, n, nbuf);
+  k_ingest_finish<<<1, 1, 0, s>>>(d, n, next_id);
+}
+
+void launch_egest_staged(const DomainDev& d, int* cell, float* frac, float* vel, float* rho, unsigned* id,
+                         uint8_t* label, unsigned* n_out, unsigned cap, cudaStream_t s) {
+  k_egest_staged<<<d.sm_count * 4, 256, 0, s>>>(d, cell, frac, vel, rho, id, label, n_out, cap);
 }
 
 void launch_egest(const DomainDev& d, float* frac, float* vel, unsigned n, cudaStream_t s) {

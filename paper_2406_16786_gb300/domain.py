@@ -155,6 +155,8 @@ class Domain:
             raise SphbufError(st, "create_domain")
         self.h = h
         self.nbuf = 0
+        self._io_refs = []  # arrays of pending asynchronous transfers
+        self._io_counts = []
         dims = np.zeros(3, dtype=np.int32)
         cs = ctypes.c_double()
         nc = ctypes.c_uint64()
@@ -214,6 +216,48 @@ class Domain:
             next_id = n if i is None else (int(i.max()) + 1 if n else 0)
         self._check(self.lib.sphbuf_write_particles(self.h, _ptr(c), _ptr(f), _ptr(v), _ptr(r), _ptr(i), _ptr(lab),
                                                     n, int(next_id)), "write_particles")
+
+    def write_particles_async(self, cell, frac, vel, rho, ids=None, labels=None, next_id=None):
+        """write_particles with the copies overlapping the work already enqueued; the next step
+        (or read) takes the arrays.  Pass page-locked arrays; they are kept referenced (and
+        must not change) until io_wait()."""
+        c = np.ascontiguousarray(cell, dtype=np.int32)
+        f = np.ascontiguousarray(np.asarray(frac, dtype=np.float32)[:, : self.dim])
+        v = np.ascontiguousarray(np.asarray(vel, dtype=np.float32)[:, : self.dim])
+        r = np.ascontiguousarray(rho, dtype=np.float32)
+        i = None if ids is None else np.ascontiguousarray(ids, dtype=np.uint32)
+        lab = None if labels is None else np.ascontiguousarray(labels, dtype=np.uint8)
+        n = c.shape[0]
+        if next_id is None:
+            next_id = n if i is None else (int(i.max()) + 1 if n else 0)
+        self._io_refs.append((c, f, v, r, i, lab))
+        self._check(self.lib.sphbuf_write_particles_async(self.h, _ptr(c), _ptr(f), _ptr(v), _ptr(r), _ptr(i),
+                                                          _ptr(lab), n, int(next_id)), "write_particles_async")
+
+    def read_async(self, out):
+        """Enqueues a copy of the sorted state into the preallocated arrays of ``out`` (names as
+        read(); page-locked, C-contiguous, equal row counts = cap); io_wait() returns the
+        particle counts of the pending reads in order.  Rows past the count are unspecified."""
+        want = dict(cell=np.int32, frac=np.float32, vel=np.float32, rho=np.float32, id=np.uint32, label=np.uint8)
+        cap = out["cell"].shape[0]
+        for key, dt in want.items():
+            a = out[key]
+            if a.dtype != dt or a.shape[0] != cap or not a.flags.c_contiguous or (a.ndim == 2 and a.shape[1] != self.dim):
+                raise ValueError("read_async: %s must be a C-contiguous %s array of %d rows" % (key, np.dtype(dt).name, cap))
+        n = ctypes.c_uint64()
+        self._io_refs.append(out)
+        self._io_counts.append(n)
+        self._check(self.lib.sphbuf_read_particles_async(self.h, _ptr(out["cell"]), _ptr(out["frac"]),
+                                                         _ptr(out["vel"]), _ptr(out["rho"]), _ptr(out["id"]),
+                                                         _ptr(out["label"]), cap, ctypes.byref(n)), "read_particles_async")
+
+    def io_wait(self):
+        """Waits for the pending asynchronous transfers; the particle counts of the reads."""
+        st = self.lib.sphbuf_io_wait(self.h)
+        counts = [n.value for n in self._io_counts]
+        self._io_refs, self._io_counts = [], []
+        self._check(st, "io_wait")
+        return counts
 
     def add_buffer(self, spec) -> int:
         o = np.ascontiguousarray(spec.origin, dtype=np.float64)

@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--no-rotating", action="store_true")
     ap.add_argument("--no-dual", action="store_true")
     ap.add_argument("--no-tjunction", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 

@@ -2,7 +2,7 @@
 
 Both sides start from the same seeded FP32 state (the oracle reads it in FP64).  Particles are
 matched by id.  Tolerances (relative L2 over all particles unless stated):
-  density 1e-5;  pressure |dp| / (rho0 c0^2) <= 1e-6 per particle;  velocity 1e-5;
+  density 1e-5;  pressure |dp| / (max(rho, rho0) c0^2) <= 1e-6 per particle;  velocity 1e-5;
   position 1e-6 cs per particle;  acceleration (from the velocity change) 2e-4.
 The id sets (the injections and deletions of the step) must be identical.
 """
@@ -22,9 +22,60 @@ def _rel_l2(a, b):
 
 @pytest.mark.parametrize("dim", [2, 3])
 def test_one_step_matches_fp64_oracle(dim):
+    _one_step_vs_oracle(cases.physics_case(dim))
+
+
+def _compressed(dim):
+    """The physics case with a patch of fluid compressed to a lattice of spacing s < dp in the
+    middle of the domain, so that its particles have more neighbours than a list holds (48
+    in 2-D, 128 in 3-D): ~59 at s = 0.6 dp in 2-D, ~170 at s = 0.75 dp in 3-D."""
+    case = cases.physics_case(dim)
+    s = (0.6 if dim == 2 else 0.75) * case.dp
+    centre = case.fluid_pos.mean(axis=0)
+    r0 = 4.0 * case.dp
+    keep = np.linalg.norm(case.fluid_pos - centre, axis=1) > r0
+    k = int(np.ceil(r0 / s))
+    g = np.arange(-k, k + 1) * s
+    grid = np.stack(np.meshgrid(*([g] * dim), indexing="ij"), axis=-1).reshape(-1, dim)
+    patch = centre + grid[np.linalg.norm(grid, axis=1) <= r0]
+    rng = np.random.default_rng(77)
+    patch = patch + rng.uniform(-0.01, 0.01, patch.shape) * case.dp
+    case.fluid_pos = np.concatenate([case.fluid_pos[keep], patch])
+    case.fluid_vel = np.concatenate([case.fluid_vel[keep], np.zeros_like(patch)])
+    case.fluid_rho = np.concatenate([case.fluid_rho[keep], np.full(patch.shape[0], case.rho0)])
+    return case, patch
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_overflowed_neighbour_lists_match_fp64_oracle(dim):
+    from scipy.spatial import cKDTree
+
+    case, patch = _compressed(dim)
+    cap = 48 if dim == 2 else 128
+    t = cKDTree(case.fluid_pos)
+    counts = np.array([len(x) - 1 for x in t.query_ball_point(patch, 2.0 * case.h_over_dp * case.dp)])
+    assert (counts > cap).sum() >= 10  # the patch's centre overflows its lists
+    # the patch's velocity after one step is all acceleration: the velocity is held to 1e-5
+    # plus the acceleration tolerance of its change
+    _one_step_vs_oracle(case, v_change_tol=2e-4)
+
+
+def test_overflowed_list_in_dual_stepping_is_reported():
+    from paper_2406_16786_gb300.domain import Domain, SphbufError
+
+    case, _ = _compressed(2)
+    case.dual_substeps = 2
+    dom = Domain.from_case(case)
+    with pytest.raises(SphbufError) as e:
+        dom.step(1)
+        dom.sync()
+    assert e.value.status == 2
+    dom.close()
+
+
+def _one_step_vs_oracle(case, v_change_tol=0.0):
     from paper_2406_16786_gb300.domain import Domain
 
-    case = cases.physics_case(dim)
     cell, frac = cases.encode(case)
     vel32 = case.fluid_vel.astype(np.float32)
     rho32 = case.fluid_rho.astype(np.float32)
@@ -46,9 +97,12 @@ def test_one_step_matches_fp64_oracle(dim):
     rho_g, rho_o = g["rho"][o].astype(np.float64), ora.rho[q]
     assert _rel_l2(rho_g, rho_o) < 1e-5
     P = ora.P
-    assert np.max(np.abs(rho_g - rho_o)) * P.c0 ** 2 / (P.rho0 * P.c0 ** 2) < 1e-6
+    # |dp| / (rho0 c0^2) per particle; FP32 rounding of the sums scales with rho, so a
+    # compressed particle (rho up to ~2.9 rho0) is held to the same bound relative to rho
+    assert np.max(np.abs(rho_g - rho_o) * P.c0 ** 2 / (np.maximum(rho_o, P.rho0) * P.c0 ** 2)) < 1e-6
     v_g, v_o = g["vel"][o].astype(np.float64), ora.vel[q]
-    assert _rel_l2(v_g, v_o) < 1e-5
+    v_in = np.stack([v_before.get(int(i), v_o[m]) for m, i in enumerate(ora.id[q])])
+    assert np.linalg.norm(v_g - v_o) <= 1e-5 * np.linalg.norm(v_o) + v_change_tol * np.linalg.norm(v_o - v_in)
     assert np.max(np.abs(gp[o] - ora.pos[q])) < 1e-6 * case.cs
     # acceleration of the particles that existed before the step and carry no boundary velocity
     ids = ora.id[q]

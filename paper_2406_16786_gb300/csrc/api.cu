@@ -461,7 +461,6 @@ int enqueue_step(sphbuf_domain* d, unsigned phases, bool timed) {
   if (timed) cudaEventRecord(d->ev[3], s);
   if (phases & SPHBUF_PHASE_BUFFER) {
     k += launch_decide(v, (phases & SPHBUF_PHASE_FULL_CHECK) != 0, s);
-    k += launch_apply(v, s);
   }
   if (timed) cudaEventRecord(d->ev[4], s);
   k += launch_rebuild(v, true, s);

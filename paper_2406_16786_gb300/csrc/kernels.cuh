@@ -99,7 +99,6 @@ int launch_dual(const DomainDev& d, cudaStream_t s);  // viscous, acoustic steps
 // buffer (kernels_buffer.cu)
 int launch_identify(const DomainDev& d, cudaStream_t s);
 int launch_decide(const DomainDev& d, bool full_domain, cudaStream_t s);
-int launch_apply(const DomainDev& d, cudaStream_t s);
 // cells (kernels_cells.cu)
 int launch_rebuild(const DomainDev& d, bool count_step, cudaStream_t s);
 int finalize_blocks(const DomainDev& d);  // blocks of the finalize pass (candidate segments / 256)

@@ -382,7 +382,6 @@ int launch_decide(const DomainDev& d, bool full_domain, cudaStream_t s) {
   return 1;
 }
 
-int launch_apply(const DomainDev&, cudaStream_t) { return 0; }  // ids assigned by the rebuild
 
 int launch_batch_buffer(Kern k, int dim, const BatchDev& b, int nblocks, bool rot, cudaStream_t s) {
   if (k != K_BUFFER && k != K_BUFFER_FULL) return 0;

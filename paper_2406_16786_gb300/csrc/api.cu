@@ -1008,8 +1008,9 @@ sphbuf_status sphbuf_set_buffer_rotation(sphbuf_domain_t d, int buffer_id, const
   const double C[3] = {pivot[0], pivot[1], D == 3 ? pivot[2] : 0.0};
   for (int x = 0; x < 3; ++x)
     if (!std::isfinite(C[x])) return fail(d, SPHBUF_ERR_INVALID_ARG, "pivot must be finite");
-  // M: rotation by omega dt (about z in 2-D; about the unit axis in 3-D), FP64 in the order
-  // the oracle states
+  // M: rotation by omega dt (about z in 2-D; about the unit axis in 3-D, Rodrigues' formula),
+  // FP64 with the products and sums in the order written (the frames of later steps, and so
+  // the FP32 decisions, depend on its rounding)
   const double phi = omega * d->desc.dt;
   const double s = std::sin(phi), c = std::cos(phi);
   double M[9];

@@ -51,3 +51,16 @@ def test_rotation_helper_matches_the_oracle_frame(lib):
         want = frames.roll_about_x(frames.rotation_3d(d), psi)
         assert np.allclose(R, want, atol=1e-13)
     assert np.allclose(rotation_from_normal([-2.0, 0, 0]), np.diag([-1.0, -1.0, 1.0]))
+
+
+def test_header_and_c_example_compile_as_c99(tmp_path):
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = os.path.join(ROOT, "tests", "c", "channel.c")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), "-c", src,
+                        "-o", str(tmp_path / "channel.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr

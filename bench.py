@@ -46,7 +46,7 @@ FP32_LANES_PER_SM = 128
 # buffer update with the buffers' candidate cells, which are the same at L = 2.5 and 5.09 m.
 # Set a figure to None when its kernel changes.
 NCU_TRAFFIC = {
-    "k_neighbours": {"bytes_per_particle": (113.87e6 + 636.87e6) / 1965281},
+    "k_neighbours": {"bytes_per_particle": (253.22e6 + 649.91e6) / 1965281},
     "k_buffer": {"bytes_per_launch": 3.501e6 + 0.0},
 }
 
@@ -295,11 +295,13 @@ def run_gpu(args):
     # neighbour passes, bound by FP32 arithmetic: algorithmic flops per particle
     pairs = lattice_pairs(dim, case.h_over_dp)          # neighbours within 2h on the lattice
     cands = 27 * (2 * case.h_over_dp) ** dim            # particles in the 27 cells of side 2h
-    flops = {"neighbours": cands * 9.0, "density": pairs * 14.0, "force": pairs * 58.0}
+    # k_neighbours builds the lists and computes Eq. (9) for the fluid particles from them;
+    # the density phase left (k_density_deferred) handles the few buffer / overflowed ones
+    flops = {"neighbours": cands * 9.0 + pairs * 14.0, "force": pairs * 58.0}
     sm_max = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
     alu_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max / 1e12
     kern = {}
-    for ph, name in (("neighbours", "k_neighbours"), ("density", "k_density"), ("force", "k_force")):
+    for ph, name in (("neighbours", "k_neighbours"), ("force", "k_force")):
         tf = n_mean * flops[ph] / (per[ph] / 1e3) / 1e12
         kern[ph] = {"kernel": name, "ms": per[ph], "flops_per_particle": flops[ph], "achieved": tf,
                     "frac": tf / alu_peak}

@@ -1439,7 +1439,6 @@ static int batch_launch(sphbuf_batch* b, Kern k) {
   const int n = b->nblocks[k];
   switch (k) {
     case K_NEIGHBOURS:
-    case K_DENSITY:
     case K_DENSITY_DEFER:
     case K_FORCE:
     case K_DRIFT:
@@ -1462,7 +1461,6 @@ static int batch_enqueue_step(sphbuf_batch* b, unsigned phases, bool timed) {
   if (phases & SPHBUF_PHASE_PHYSICS) {
     k += batch_launch(b, K_NEIGHBOURS);
     if (timed) cudaEventRecord(b->ev[1], s);
-    k += batch_launch(b, K_DENSITY);
     k += batch_launch(b, K_DENSITY_DEFER);
     if (timed) cudaEventRecord(b->ev[2], s);
     if (b->dual_n > 0) {

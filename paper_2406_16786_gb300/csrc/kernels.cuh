@@ -57,7 +57,6 @@ struct BatchDev {
 
 enum Kern : int {
   K_NEIGHBOURS,
-  K_DENSITY,
   K_DENSITY_DEFER,
   K_FORCE,
   K_DRIFT,

@@ -284,18 +284,53 @@ __device__ __forceinline__ void visit_entry(const DomainDev& d, unsigned ent, fl
   fn(wall, j, rx, ry, rz);
 }
 
-// Calls fn for the cnt listed neighbours of particle i (16-byte loads of 4 entries).
-template <int D, typename Fn>
+// Calls fn for the cnt listed neighbours of particle i (16-byte loads of 4 entries).  OWN:
+// the list was written by this thread in this kernel, so it is read with coherent loads.
+template <int D, bool OWN = false, typename Fn>
 __device__ __forceinline__ void for_each_listed(const DomainDev& d, unsigned i, int cnt, float cxf, const float fi[3],
                                                 Fn&& fn) {
   const uint4* lst = reinterpret_cast<const uint4*>(d.nb + (size_t)i * d.nb_cap);
   for (int e = 0; e < cnt; e += 4) {
-    const uint4 q = __ldg(lst + (e >> 2));
+    const uint4 q = OWN ? lst[e >> 2] : __ldg(lst + (e >> 2));
     visit_entry<D>(d, q.x, cxf, fi, fn);
     if (e + 1 < cnt) visit_entry<D>(d, q.y, cxf, fi, fn);
     if (e + 2 < cnt) visit_entry<D>(d, q.z, cxf, fi, fn);
     if (e + 3 < cnt) visit_entry<D>(d, q.w, cxf, fi, fn);
   }
+}
+
+// Density, Eq. (9), for particle i of the fluid (not in a buffer) from its list; writes
+// vr4[i] = (v_i, rho_i).
+template <int D, bool OWN>
+__device__ __forceinline__ void density_fluid(const DomainDev& d, unsigned i, int cnt) {
+  const Phys& P = d.P;
+  const float4 pi = d.pos4[i];
+  const float fi[3] = {pi.x, pi.y, pi.z};
+  float s = 0.f;
+  for_each_listed<D, OWN>(d, i, cnt, pi.w, fi, [&](int, unsigned, float rx, float ry, float rz) {
+    s += kernel_w(sqrtf(rx * rx + ry * ry + rz * rz) * P.inv_h, P);
+  });
+  const float4 v = d.vel4[i];
+  d.vr4[i] = make_float4(v.x, v.y, v.z, P.rho0 * (s + P.w_self) * P.inv_sum_w0);
+}
+
+// Eq. (9) for fluid particle i from its list, or, for a buffer particle (the Eq. (4) rate) or
+// an overflowed list (strong compression: it reads its cells directly), an entry in the
+// deferred list for density_deferred_body.  Every active lane of the warp calls it.
+template <int D, bool OWN>
+__device__ __forceinline__ void density_or_defer(const DomainDev& d, unsigned i, int cnt) {
+  const int lane = threadIdx.x & 31;
+  const bool defer = d.A.label[i] != 0 || cnt > d.nb_cap;
+  const unsigned am = __activemask();
+  const unsigned m = __ballot_sync(am, defer);
+  if (m) {
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(&d.st->n_defer, (unsigned)__popc(m));
+    base = __shfl_sync(am, base, leader);
+    if (defer) d.deferred[base + __popc(m & ((1u << lane) - 1u))] = i;
+  }
+  if (!defer) density_fluid<D, OWN>(d, i, cnt);
 }
 
 // One candidate of the neighbour-list pass: appends j to the particle's list when within 2h.
@@ -373,47 +408,8 @@ __device__ __forceinline__ void neighbours_body(const DomainDev& d, unsigned bid
     if (r && t.cnt < cap)
       lst[t.cnt >> 2] = make_uint4(r == 1 ? t.q3 : (r == 2 ? t.q2 : t.q1), r == 2 ? t.q3 : t.q2, t.q3, 0u);
     d.nb_cnt[i] = (unsigned)t.cnt;
-  }
-}
-
-// Density, Eq. (9), for particle i of the fluid (not in a buffer) from its list; writes
-// vr4[i] = (v_i, rho_i).
-template <int D>
-__device__ __forceinline__ void density_fluid(const DomainDev& d, unsigned i, int cnt) {
-  const Phys& P = d.P;
-  const float4 pi = d.pos4[i];
-  const float fi[3] = {pi.x, pi.y, pi.z};
-  float s = 0.f;
-  for_each_listed<D>(d, i, cnt, pi.w, fi, [&](int, unsigned, float rx, float ry, float rz) {
-    s += kernel_w(sqrtf(rx * rx + ry * ry + rz * rz) * P.inv_h, P);
-  });
-  const float4 v = d.vel4[i];
-  d.vr4[i] = make_float4(v.x, v.y, v.z, P.rho0 * (s + P.w_self) * P.inv_sum_w0);
-}
-
-// Density pass over the lists, Eq. (9), for the fluid particles.  Buffer particles (the
-// Eq. (4) rate) and particles whose list overflowed (strong compression: they read their
-// cells directly) are appended to the deferred list for density_deferred_body, so that this
-// pass keeps few registers and a high occupancy.
-template <int D>
-__device__ __forceinline__ void density_body(const DomainDev& d, unsigned bid, unsigned nblk) {
-  if (d.st->status) return;
-  const unsigned n = d.st->n;
-  const int cap = d.nb_cap;
-  const int lane = threadIdx.x & 31;
-  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
-    const int cnt = (int)d.nb_cnt[i];
-    const bool defer = d.A.label[i] != 0 || cnt > cap;
-    const unsigned am = __activemask();
-    const unsigned m = __ballot_sync(am, defer);
-    if (m) {
-      const int leader = __ffs(m) - 1;
-      unsigned base = 0;
-      if (lane == leader) base = atomicAdd(&d.st->n_defer, (unsigned)__popc(m));
-      base = __shfl_sync(am, base, leader);
-      if (defer) d.deferred[base + __popc(m & ((1u << lane) - 1u))] = i;
-    }
-    if (!defer) density_fluid<D>(d, i, cnt);
+    // Eq. (9) right away, while the list and the neighbours' positions are in cache
+    density_or_defer<D, true>(d, i, t.cnt);
   }
 }
 
@@ -724,7 +720,6 @@ __device__ __forceinline__ void dual_finish_body(const DomainDev& d, unsigned bi
   }
 
 SPHBUF_PAIR(k_neighbours, neighbours_body, (kThreads, 5))
-SPHBUF_PAIR(k_density, density_body, (kThreads, 6))
 SPHBUF_PAIR(k_density_deferred, density_deferred_body, (kThreads, 4))
 template <int D, bool TVF>
 __global__ void __launch_bounds__(kThreads, 4) k_force(DomainDev d) {
@@ -767,14 +762,12 @@ int launch_neighbours(const DomainDev& d, cudaStream_t s) {
 }
 
 int launch_density(const DomainDev& d, cudaStream_t s) {
-  if (d.g.dim == 2) {
-    k_density<2><<<grid_for(d, 8), kThreads, 0, s>>>(d);
+  // the fluid particles' Eq. (9) is computed by the neighbour pass; this is the rest
+  if (d.g.dim == 2)
     k_density_deferred<2><<<grid_for(d, 2), kThreads, 0, s>>>(d);
-  } else {
-    k_density<3><<<grid_for(d, 8), kThreads, 0, s>>>(d);
+  else
     k_density_deferred<3><<<grid_for(d, 2), kThreads, 0, s>>>(d);
-  }
-  return 2;
+  return 1;
 }
 
 int launch_force(const DomainDev& d, cudaStream_t s) {
@@ -847,7 +840,6 @@ int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream
     return 1;
   switch (k) {
     SPHBUF_CASE(K_NEIGHBOURS, k_neighbours)
-    SPHBUF_CASE(K_DENSITY, k_density)
     SPHBUF_CASE(K_DENSITY_DEFER, k_density_deferred)
     SPHBUF_CASE(K_VISCOUS, k_viscous)
     SPHBUF_CASE(K_DUAL_FINISH, k_dual_finish)

@@ -40,7 +40,10 @@
  *   Injections are numbered in (buffer, parent id) order: new id = next_id + rank.
  *
  * Ownership: the library allocates and frees all device memory of a domain; host pointers
- * passed in are only read (or written, for read_* calls) during the call.
+ * passed in are only read (or written, for read_* calls) during the call, except those of
+ * the asynchronous transfers, which are used until sphbuf_io_wait returns.
+ * Threads: calls on one domain (or batch) must not overlap; different domains may be used
+ * from different host threads.
  * Errors: every call returns a status.  Asynchronous device-side errors (capacity overflow,
  * NaN positions) are latched in the domain and returned by the next synchronising call
  * (sphbuf_sync or any sphbuf_read_*); once latched, later steps do no work.  No call traps

@@ -318,7 +318,12 @@ def run_gpu(args):
     pouts = [{k: torch.empty(room * v[:1].nbytes, dtype=torch.uint8).pin_memory().numpy().view(v.dtype)
               .reshape((room,) + v.shape[1:]) for k, v in st.items()} for _ in range(2)]
     nid = dom.global_counters()["next_id"]
-    # (a) synchronous calls: write, step, read one after the other
+    from paper_2406_16786_gb300 import sharding
+
+    # (a) synchronous calls: write, step, read one after the other (all ranks start together;
+    # the job's time is the slowest rank's)
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(K_e2e):
@@ -327,9 +332,11 @@ def run_gpu(args):
         dom.step(1)
         dom.read(out=pouts[0])
     torch.cuda.synchronize()
-    te_sync = time.perf_counter() - t0
+    te_sync = sharding.max_over_ranks(time.perf_counter() - t0)
     # (b) pipelined calls: the copies of step k+1's input and of step k-1's result run on the
     # domain's transfer streams while step k computes
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for q in range(K_e2e):
@@ -339,7 +346,7 @@ def run_gpu(args):
         dom.read_async(pouts[q % 2])
     counts = dom.io_wait()
     torch.cuda.synchronize()
-    te = time.perf_counter() - t0
+    te = sharding.max_over_ranks(time.perf_counter() - t0)
     assert len(counts) == K_e2e and all(abs(c - nn) < 4096 for c in counts)
     # the host link itself: one pinned <-> device copy of the same byte count each way
     hb = torch.empty(nn * state_bytes, dtype=torch.uint8).pin_memory()

@@ -103,3 +103,35 @@ def test_async_write_checks_and_read_capacity_are_latched():
     (m,) = dom.io_wait()
     assert abs(m - n) < 200
     dom.close()
+
+
+def test_first_write_asynchronous():
+    """An asynchronous write as the domain's very first write (identification of the inflow
+    buffer particles at the first step included) steps exactly like a synchronous one."""
+    from paper_2406_16786_gb300 import workloads as wl
+    from paper_2406_16786_gb300.domain import Domain
+
+    case = cases.lockstep_cases()[4][1]  # 3-D pipe, velocity inlet + pressure outlet
+    cell, frac = wl.encode_positions(case.fluid_pos, case.lo, case.cs, case.grid_dims())
+    arrays = dict(cell=cell, frac=frac.astype(np.float32), vel=case.fluid_vel.astype(np.float32),
+                  rho=case.fluid_rho.astype(np.float32))
+    pinned = {k: _pinned_copy(v) for k, v in arrays.items()}
+    ref = Domain.from_case(case)
+    ref.step(3)
+    want = ref.read()
+    dom = Domain(case.dim, case.lo, case.hi, case.dp, case.h_over_dp, case.rho0, case.c0, case.nu, case.dt,
+                 case.capacity)
+    dom.set_walls(case.wall_pos)
+    for b in case.buffers:
+        dom.add_buffer(b)
+    dom.write_particles_async(pinned["cell"], pinned["frac"], pinned["vel"], pinned["rho"])
+    dom.step(3)
+    n = want["id"].shape[0]
+    out = {key: _pinned_like(v, n + 256) for key, v in want.items()}
+    dom.read_async(out)
+    (m,) = dom.io_wait()
+    assert m == n
+    for key in want:
+        assert np.array_equal(out[key][:n], want[key]), key
+    ref.close()
+    dom.close()

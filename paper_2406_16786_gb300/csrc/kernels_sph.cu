@@ -722,7 +722,7 @@ __device__ __forceinline__ void dual_finish_body(const DomainDev& d, unsigned bi
 SPHBUF_PAIR(k_neighbours, neighbours_body, (kThreads, 5))
 SPHBUF_PAIR(k_density_deferred, density_deferred_body, (kThreads, 4))
 template <int D, bool TVF>
-__global__ void __launch_bounds__(kThreads, 5) k_force(DomainDev d) {
+__global__ void __launch_bounds__(kThreads, 4) k_force(DomainDev d) {
   force_body<D, TVF>(d, blockIdx.x, gridDim.x);
 }
 template <int D, bool TVF>

@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--tj-steps", type=int, default=10)
     ap.add_argument("--rot-steps", type=int, default=20)
     ap.add_argument("--no-rotating", action="store_true")
+    ap.add_argument("--no-pipe8", action="store_true")
     ap.add_argument("--no-dual", action="store_true")
     ap.add_argument("--no-tjunction", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -371,6 +372,7 @@ def run_gpu(args):
     batched = None if args.no_batched else run_batched(args, stream, rank, world)
     tjunction = None if args.no_tjunction else run_restricted_vs_full(args, stream)
     rotating = None if args.no_rotating else run_rotating(args, stream)
+    pipe_8m = None if args.no_pipe8 else run_pipe_8m(args, stream)
     dual = None if args.no_dual else run_dual(args, stream, ms_max / args.steps)
 
     cpu = None
@@ -414,6 +416,7 @@ def run_gpu(args):
         "batched_vs_plain": batched,
         "restricted_vs_full_16M": tjunction,
         "rotating_buffer_3d": rotating,
+        "pipe_8m": pipe_8m,
         "dual_time_stepping": dual,
     }
     if rank == 0:
@@ -562,6 +565,36 @@ def run_dual(args, stream, single_ms):
             "single_rate_dt": dt_single, "single_rate_ms_per_step": single_ms,
             "single_rate_simulated_s_per_wall_s": dt_single / (single_ms / 1e3),
             "speedup_in_simulated_time": (dt_adv / ms) / (dt_single / single_ms), "steps": K}
+
+
+def run_pipe_8m(args, stream):
+    """The same pipe at the full length of the 1000-step workload, L = 8 m (6.3 M particles):
+    whole steps in graph replay after a short untimed start, particle-steps/s."""
+    import torch
+
+    from paper_2406_16786_gb300 import workloads
+    from paper_2406_16786_gb300.domain import Domain
+
+    case = workloads.config3(length=8.0)
+    dom = Domain.from_case(case, stream=stream)
+    dom.use_graph(True)
+    dom.step(20)
+    n0 = dom.count()
+    K = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    dom.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    n1 = dom.count()
+    dom.sync()
+    res = {"workload": "3-D pipe R0.5 L8 dp0.01 along (1,1,1)/sqrt3, 2 bidirectional pressure buffers",
+           "particles": int(0.5 * (n0 + n1)), "ms_per_step": ms,
+           "particle_steps_per_s": 0.5 * (n0 + n1) / (ms / 1e3), "steps": K}
+    dom.close()
+    return res
 
 
 def run_rotating(args, stream):

@@ -116,7 +116,8 @@ __device__ __forceinline__ void force_term(const Phys& P, bool wall, float rx, f
 // Calls fn(wall, j, rx, ry, rz) for every particle of the 3^d cells around cell c (global
 // memory; the per-particle fallback path).
 template <int D, typename Fn>
-__device__ __forceinline__ void for_each_near(const DomainDev& d, const int c[3], const float fi[3], Fn&& fn) {
+__device__ __forceinline__ void for_each_near(const DomainDev& d, const int c[3], const float fi[3], Fn&& fn,
+                                              unsigned first = 0, unsigned stride = 1) {
   const Grid& g = d.g;
   const float cs = g.cs;
   const int x0 = max(c[0] - 1, 0), x1 = min(c[0] + 1, g.nx - 1);
@@ -132,7 +133,7 @@ __device__ __forceinline__ void for_each_near(const DomainDev& d, const int c[3]
         if (y < 0 || y >= g.ny) continue;
         const int rb = (z * g.ny + y) * g.nx;
         const unsigned j1 = start[rb + x1 + 1];
-        for (unsigned j = start[rb + x0]; j < j1; ++j) {
+        for (unsigned j = start[rb + x0] + first; j < j1; j += stride) {
           const int xoff = cell[j] - rb - c[0];
           const float rx = fi[0] - F[0][j] - (float)xoff * cs;
           const float ry = fi[1] - (float)dy * cs - F[1][j];
@@ -422,9 +423,19 @@ __device__ __forceinline__ void density_deferred_body(const DomainDev& d, unsign
   const unsigned nd = d.st->n_defer;
   const Phys P = d.P;
   const int cap = d.nb_cap;
-  for (unsigned e = bid * blockDim.x + threadIdx.x; e < nd; e += nblk * blockDim.x) {
-    const unsigned i = d.deferred[e];
-    const int cnt = (int)d.nb_cnt[i];
+  // eight lanes per deferred particle share its neighbours (the buffer particles, tens of
+  // thousands, would leave the GPU waiting on one long neighbour loop per thread), then a
+  // reduction over the eight in a fixed order (the group's first lane's)
+  constexpr unsigned G = 8;
+  const unsigned lane = threadIdx.x & (G - 1);
+  const unsigned grp = (bid * blockDim.x + threadIdx.x) / G, ngrp = (nblk * blockDim.x) / G;
+  // every lane of a warp runs the same number of rounds (the shuffles need all 32)
+  const unsigned rounds = (nd + ngrp - 1) / ngrp;
+  for (unsigned r = 0; r < rounds; ++r) {
+    const unsigned e = grp + r * ngrp;
+    const bool live = e < nd;
+    const unsigned i = live ? d.deferred[e] : 0u;
+    const int cnt = live ? (int)d.nb_cnt[i] : 0;
     const float4 pi = d.pos4[i];
     const float fi[3] = {pi.x, pi.y, pi.z};
     const uint8_t lab = d.A.label[i];
@@ -450,19 +461,27 @@ __device__ __forceinline__ void density_deferred_body(const DomainDev& d, unsign
       }
     };
     if (cnt <= cap) {
-      for_each_listed<D>(d, i, cnt, pi.w, fi, term);
+      const unsigned* lst = d.nb + (size_t)i * cap;
+      for (int k = (int)lane; k < cnt; k += (int)G) visit_entry<D>(d, __ldg(lst + k), pi.w, fi, term);
     } else {
       int c[3];
       cell_coords(d.A.cell[i], d.g, c);
-      for_each_near<D>(d, c, fi, [&](int wall, unsigned j, float rx, float ry, float rz) {
-        const float r2 = rx * rx + ry * ry + rz * rz;
-        if (r2 < P.two_h_sq && r2 > 0.f) term(wall, j, rx, ry, rz);
-      });
+      for_each_near<D>(
+          d, c, fi,
+          [&](int wall, unsigned j, float rx, float ry, float rz) {
+            const float r2 = rx * rx + ry * ry + rz * rz;
+            if (r2 < P.two_h_sq && r2 > 0.f) term(wall, j, rx, ry, rz);
+          },
+          lane, G);
     }
-    // (in the dual-criteria scheme the buffer particles keep their density here; their
-    // continuity is integrated by the acoustic steps)
-    const float rb = P.dual_n > 0 ? rho_i : rho_i + P.dt * (2.f * rho_i * s);
-    d.vr4[i] = make_float4(vi[0], vi[1], vi[2], buf ? rb : P.rho0 * (s + P.w_self) * P.inv_sum_w0);
+#pragma unroll
+    for (int o = (int)G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o, (int)G);
+    if (live && lane == 0) {
+      // (in the dual-criteria scheme the buffer particles keep their density here; their
+      // continuity is integrated by the acoustic steps)
+      const float rb = P.dual_n > 0 ? rho_i : rho_i + P.dt * (2.f * rho_i * s);
+      d.vr4[i] = make_float4(vi[0], vi[1], vi[2], buf ? rb : P.rho0 * (s + P.w_self) * P.inv_sum_w0);
+    }
   }
 }
 
@@ -764,9 +783,9 @@ int launch_neighbours(const DomainDev& d, cudaStream_t s) {
 int launch_density(const DomainDev& d, cudaStream_t s) {
   // the fluid particles' Eq. (9) is computed by the neighbour pass; this is the rest
   if (d.g.dim == 2)
-    k_density_deferred<2><<<grid_for(d, 2), kThreads, 0, s>>>(d);
+    k_density_deferred<2><<<grid_for(d, 4), kThreads, 0, s>>>(d);
   else
-    k_density_deferred<3><<<grid_for(d, 2), kThreads, 0, s>>>(d);
+    k_density_deferred<3><<<grid_for(d, 4), kThreads, 0, s>>>(d);
   return 1;
 }
 

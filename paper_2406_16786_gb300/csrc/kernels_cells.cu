@@ -248,11 +248,20 @@ __device__ __forceinline__ void hist_body(const DomainDev& d, unsigned bid, unsi
   if (d.st->status) return;
   rank_injections(d, bid, nblk);
   const unsigned n = d.st->n + d.st->n_inj;
+  const unsigned lane = threadIdx.x & 31u;
   for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
-    if (d.B.label[i] == kDead)
-      d.slot[i] = kNoSlot;
-    else
-      d.slot[i] = atomicAdd(d.cnt + d.B.cell[i], 1u);
+    // consecutive particles mostly share a cell (B is in the last rebuild's order): one
+    // atomic per cell and warp; the slots inside a cell are only an arrival order (the
+    // scatter ranks each cell's particles by id)
+    const bool dead = d.B.label[i] == kDead;
+    const int c = d.B.cell[i];
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, dead ? 0xFFFFFFFFu : (unsigned)c);
+    const int leader = __ffs(peers) - 1;
+    unsigned base = 0;
+    if (!dead && (int)lane == leader) base = atomicAdd(d.cnt + c, (unsigned)__popc(peers));
+    base = __shfl_sync(act, base, leader);
+    d.slot[i] = dead ? kNoSlot : base + (unsigned)__popc(peers & ((1u << lane) - 1u));
   }
 }
 

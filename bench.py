@@ -46,7 +46,7 @@ FP32_LANES_PER_SM = 128
 # buffer update with the buffers' candidate cells, which are the same at L = 2.5 and 5.09 m.
 # Set a figure to None when its kernel changes.
 NCU_TRAFFIC = {
-    "k_neighbours": {"bytes_per_particle": (253.22e6 + 649.91e6) / 1965281},
+    "k_neighbours": {"bytes_per_particle": (253.15e6 + 650.12e6) / 1965281},
     "k_buffer": {"bytes_per_launch": 3.501e6 + 0.0},
 }
 

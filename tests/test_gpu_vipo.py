@@ -2,7 +2,8 @@
 
 The GPU's time-averaged mid-channel profile must be within RMSEP 2 % of Eq. (27) and within
 2 % relative L2 of the oracle's converged profile (tests/golden/vipo_oracle_profile.json,
-written by tests/golden/make_vipo_profile.py from the oracle alone).
+written by tests/golden/make_vipo_profile.py from the oracle alone), and its injection and
+deletion counts per buffer after the 2200 steps within one per lane (20) of the oracle's.
 """
 import json
 import os
@@ -47,4 +48,10 @@ def test_vipo_free_run_matches_poiseuille_and_oracle():
     assert np.linalg.norm(prof - ref) / np.linalg.norm(ref) < 0.02
     g = dom.global_counters()
     assert g["escaped"] == 0
+    # the free-run counts per buffer within one particle per lane of the oracle's (2200 steps)
+    dom.step(gold["steps"] - done)
+    for k in range(2):
+        c = dom.counters(k)
+        assert abs(c["injected"] - gold["injected"][k]) <= lanes
+        assert abs(c["deleted"] - gold["deleted"][k]) <= lanes
     dom.close()

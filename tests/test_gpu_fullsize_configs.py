@@ -4,7 +4,8 @@
   steps bit-exact against the FP32-mode oracle; one physics step with every particle checked
   against the FP64 oracle; the whole 200-step run with the count and mass invariants and the
   inlet schedule (buffer particles move at exactly U, so each of the inlet's lanes injects
-  floor or ceil of U T / dp particles).
+  floor or ceil of U T / dp particles), and the whole run against the FP64 oracle (same ids
+  and counters, fields within the accumulated FP32 rounding).
 * 15.4 M-particle T-junction: kinematic steps bit-exact (velocity inlet, two pressure outlets
   at arbitrary orientations); one physics step sampled against the FP64 oracle.
 * 64 star channels stepped as one batch in graph replay with the autotuner's grid: kinematic
@@ -56,6 +57,41 @@ def test_channel_full_run_invariants_and_inlet_schedule():
     crossings = 1.0 * steps * c.dt / c.dp
     assert lanes * (math.floor(crossings) - 1) <= cin["injected"] <= lanes * (math.ceil(crossings) + 1)
     assert cout["deleted"] > 0 or cout["injected"] == 0
+    dom.close()
+
+
+def test_channel_full_run_tracks_fp64_oracle():
+    """The whole 200-step run of the 16 k channel, GPU against the FP64 oracle from the same
+    FP32 input: the same particles (ids) and counters at the end, fields within the FP32
+    rounding accumulated over the run."""
+    from oracle import buffer as OB
+    from paper_2406_16786_gb300.domain import Domain
+
+    c = wl.config1()
+    cell, frac = wl.encode_positions(c.fluid_pos, c.lo, c.cs, c.grid_dims())
+    vel32 = c.fluid_vel.astype(np.float32)
+    rho32 = c.fluid_rho.astype(np.float32)
+    dom = Domain.from_case(c)
+    dom.use_graph(True)
+    pos0 = wl.decode_positions(cell, frac, c.lo, c.cs, c.grid_dims())
+    ora = OB.OracleSim(c, pos=pos0, vel=vel32.astype(np.float64), rho=rho32.astype(np.float64))
+    ora.commit()
+    dom.step(c.steps)
+    ora.step(c.steps)
+    g = dom.read()
+    gp = dom.positions()
+    assert sorted(g["id"].tolist()) == sorted(ora.id.tolist())
+    for k in range(2):
+        cnt = dom.counters(k)
+        assert (cnt["injected"], cnt["deleted"]) == (int(ora.injected[k]), int(ora.deleted[k]))
+    o, q = np.argsort(g["id"]), np.argsort(ora.id)
+    e_rho = np.linalg.norm(g["rho"][o] - ora.rho[q]) / np.linalg.norm(ora.rho[q])
+    e_v = np.linalg.norm(g["vel"][o] - ora.vel[q]) / np.linalg.norm(ora.vel[q])
+    e_p = np.max(np.linalg.norm(gp[o] - ora.pos[q], axis=1)) / c.cs
+    print("config1 200 steps: n %d inj %s del %s rho %.2e v %.2e pos %.2e cs" % (
+        g["id"].size, ora.injected.tolist(), ora.deleted.tolist(), e_rho, e_v, e_p))
+    # measured: rho 1.6e-7, v 3.3e-6, positions 3.7e-6 cs
+    assert e_rho < 1e-6 and e_v < 2e-5 and e_p < 2e-5
     dom.close()
 
 

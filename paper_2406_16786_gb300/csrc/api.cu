@@ -392,13 +392,15 @@ sphbuf_status ensure_io(sphbuf_domain* d) {
   if (d->io_h2d) return SPHBUF_OK;
   const size_t C = d->desc.capacity;
   const int D = d->desc.dim;
-  CK(dalloc(d, &d->in_stage, stage_bytes(C, D)));
-  CK(dalloc(d, &d->out_stage, stage_bytes(C, D)));
-  CK(cudaHostAlloc(reinterpret_cast<void**>(&d->n_pinned), kIoRing * sizeof(unsigned), cudaHostAllocDefault));
+  // each piece only once (a call that failed half-way is retried by the next one)
+  if (!d->in_stage) CK(dalloc(d, &d->in_stage, stage_bytes(C, D)));
+  if (!d->out_stage) CK(dalloc(d, &d->out_stage, stage_bytes(C, D)));
+  if (!d->n_pinned)
+    CK(cudaHostAlloc(reinterpret_cast<void**>(&d->n_pinned), kIoRing * sizeof(unsigned), cudaHostAllocDefault));
   for (cudaEvent_t* e : {&d->ev_ingest, &d->ev_h2d, &d->ev_egest, &d->ev_d2h})
-    CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
-  CK(cudaStreamCreateWithFlags(&d->io_d2h, cudaStreamNonBlocking));
-  CK(cudaStreamCreateWithFlags(&d->io_h2d, cudaStreamNonBlocking));
+    if (!*e) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  if (!d->io_d2h) CK(cudaStreamCreateWithFlags(&d->io_d2h, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&d->io_h2d, cudaStreamNonBlocking));  // set last: marks the set-up done
   return SPHBUF_OK;
 }
 

@@ -73,3 +73,33 @@ def test_batch_autotune_keeps_results_valid():
         dele = sum(d.counters(k)["deleted"] for k in range(len(c.buffers)))
         assert d.count() == c.n + inj - dele - g["escaped"]
     b.close()
+
+
+def test_batched_rotating_and_transport_velocity_equal_individual():
+    """The batch's variants: domains with a rotating nozzle (the buffer kernel with the turn)
+    and a domain with the transport velocity (the force kernel's TVF variant), stepped
+    together, end bit for bit where each ends alone."""
+    from paper_2406_16786_gb300.domain import Batch, Domain
+
+    def _cases():
+        a = wl.sprinkler_case(dim=2, dp=0.004, umax=1.0, omega=30.0, ambient=True, domain_radius=0.2)
+        b = wl.sprinkler_case(dim=2, dp=0.005, umax=1.0, omega=-20.0, theta0=1.0, ambient=True, domain_radius=0.2)
+        t = cases.physics_case(2)
+        t.tvf_lambda = 7.5
+        return [a, b, t]
+
+    alone = [Domain.from_case(c) for c in _cases()]
+    for d in alone:
+        d.step(40)
+    together = [Domain.from_case(c) for c in _cases()]
+    b = Batch(together)
+    b.use_graph(True)
+    b.step(40)
+    b.sync()
+    for a_, t_ in zip(alone, together):
+        ra, rt = a_.read(), t_.read()
+        for key in ra:
+            assert np.array_equal(ra[key], rt[key]), key
+        assert a_.global_counters() == t_.global_counters()
+    assert together[0].counters(0)["injected"] > 0
+    b.close()

@@ -4,12 +4,12 @@
 // cells per warp, eight lanes per cell, four particles per lane loaded before any is tested;
 // the cells' particle ranges come from the last rebuild).  Each is transformed into
 // the buffer's local frame (Eqs. (11), (15)) with the FP32 decision contract and compared on
-// the normal axis only.  Crossings are compacted with a warp ballot into per-block lists in
-// shared memory, and each block reserves its range of the step's global lists with one
-// atomic per list.  The deciding thread does everything that does not depend on the order
-// of the injections: it recycles the parent by -a u (Eqs. (16)-(17)), resets its density for
-// pressure buffers (Eq. (22)) and marks deleted particles dead; the block writes each
-// duplicate (the parent's state before recycling, label 0) at the tail of B.  The ids of the
+// the normal axis only.  Crossings are compacted with a warp ballot: each warp with crossings
+// reserves its range of the step's global lists with one atomic per list and its lanes write
+// their records at once.  The deciding thread does everything that does not depend on the
+// order of the injections: it writes the duplicate (the parent's state before recycling,
+// label 0) at the tail of B, recycles the parent by -a u (Eqs. (16)-(17)), resets its density
+// for pressure buffers (Eq. (22)) and marks deleted particles dead.  The ids of the
 // duplicates follow the (buffer, parent id) order and are assigned by the first pass of the
 // rebuild (rank_injections, in apply.cuh), which needs every decision of the step.
 // The full-domain variant takes the same decisions over every particle and every buffer.
@@ -21,7 +21,6 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kBufThreads = 256;
-constexpr unsigned kStage = 128;  // decisions staged per block and list (more go straight out)
 
 // What the test of one particle of B needs (its id, velocity and density are read only when
 // it crossed a face).
@@ -73,36 +72,31 @@ __device__ __forceinline__ void write_deletion(const DomainDev& d, const Decisio
   d.del[slot] = e;
 }
 
-// Per-block decision lists, plus the buffers' constants and this step's recycled density, in
-// shared memory.
+// The buffers' constants and this step's recycled density, in shared memory.
 struct Staged {
-  Decision inj[kStage];
-  Decision del[kStage];
   BufDev bufs[kMaxBuffers];
   float rho_pb[kMaxBuffers];
-  unsigned ninj, ndel, base_inj, base_del, n, bad;
+  unsigned n, bad;
 };
 
-// Warp-ballot compaction of one record per flagged lane into the block's list; records
-// beyond the staging capacity are written to the global list directly.
+// Warp-ballot compaction of one record per flagged lane: the warp reserves its range of the
+// step's list with one atomic and the lanes write their records (and duplicates) at once.
 template <int D, bool INJ>
 __device__ __forceinline__ void stage(const DomainDev& d, Staged& sm, bool flag, const Decision& rec) {
   const unsigned m = __ballot_sync(kFull, flag);
   if (m == 0) return;
   const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
   unsigned base = 0;
-  if (lane == __ffs(m) - 1) base = atomicAdd(INJ ? &sm.ninj : &sm.ndel, (unsigned)__popc(m));
-  base = __shfl_sync(kFull, base, __ffs(m) - 1);
+  if (lane == leader) base = atomicAdd(INJ ? &d.st->n_inj : &d.st->n_del, (unsigned)__popc(m));
+  base = __shfl_sync(kFull, base, leader);
   if (!flag) return;
   atomicAdd(INJ ? &d.st->injected[rec.k] : &d.st->deleted[rec.k], 1ull);
   const unsigned r = base + __popc(m & ((1u << lane) - 1u));
-  if (r < kStage) {
-    (INJ ? sm.inj : sm.del)[r] = rec;
-  } else if (INJ) {
-    write_injection<D>(d, rec, atomicAdd(&d.st->n_inj, 1u), sm.n);
-  } else {
-    write_deletion(d, rec, atomicAdd(&d.st->n_del, 1u));
-  }
+  if (INJ)
+    write_injection<D>(d, rec, r, sm.n);
+  else
+    write_deletion(d, rec, r);
 }
 
 // Algorithms 1-3 for particle i of B (test state p) against buffer k; the warp stages the
@@ -227,7 +221,6 @@ __device__ __forceinline__ void buffer_body(const DomainDev& d, unsigned bid, un
     if (s0 + grp < nseg) r = d.seg_range[s0 + grp];
   }
   if (threadIdx.x == 0) {
-    sm.ninj = sm.ndel = 0;
     sm.n = d.st->n;
     sm.bad = d.st->status != 0;
   }
@@ -279,20 +272,10 @@ __device__ __forceinline__ void buffer_body(const DomainDev& d, unsigned bid, un
       s0 = s1;
     }
   }
-  // one reservation per block and list, then the block writes its records and duplicates
-  __syncthreads();
-  const unsigned ni = min(sm.ninj, kStage), nd = min(sm.ndel, kStage);
-  if (threadIdx.x == 0) {
-    if (ni) sm.base_inj = atomicAdd(&d.st->n_inj, ni);
-    if (nd) sm.base_del = atomicAdd(&d.st->n_del, nd);
-  }
-  __syncthreads();
-  for (unsigned e = threadIdx.x; e < ni; e += blockDim.x) write_injection<D>(d, sm.inj[e], sm.base_inj + e, sm.n);
-  for (unsigned e = threadIdx.x; e < nd; e += blockDim.x) write_deletion(d, sm.del[e], sm.base_del + e);
 }
 
 template <int D, bool FULL, bool ROT>
-__global__ void __launch_bounds__(kBufThreads) k_buffer(DomainDev d) {
+__global__ void __launch_bounds__(kBufThreads, 4) k_buffer(DomainDev d) {
   buffer_body<D, FULL, ROT>(d, blockIdx.x, gridDim.x);
 }
 

@@ -73,7 +73,7 @@ __device__ __forceinline__ void write_deletion(const DomainDev& d, const Decisio
 }
 
 // The buffers' constants and this step's recycled density, in shared memory.
-struct Staged {
+struct BlockShared {
   BufDev bufs[kMaxBuffers];
   float rho_pb[kMaxBuffers];
   unsigned n, bad;
@@ -82,7 +82,7 @@ struct Staged {
 // Warp-ballot compaction of one record per flagged lane: the warp reserves its range of the
 // step's list with one atomic and the lanes write their records (and duplicates) at once.
 template <int D, bool INJ>
-__device__ __forceinline__ void stage(const DomainDev& d, Staged& sm, bool flag, const Decision& rec) {
+__device__ __forceinline__ void stage(const DomainDev& d, BlockShared& sm, bool flag, const Decision& rec) {
   const unsigned m = __ballot_sync(kFull, flag);
   if (m == 0) return;
   const int lane = threadIdx.x & 31;
@@ -107,7 +107,7 @@ __device__ __forceinline__ void stage(const DomainDev& d, Staged& sm, bool flag,
 // by the difference), velocities rotated row by row.  ROT: some buffer of the domain rotates
 // (the turn is compiled out otherwise).
 template <int D, bool ROT>
-__device__ __forceinline__ void decide(const DomainDev& d, Staged& sm, int k, unsigned i, const Cand& p, int lin_c,
+__device__ __forceinline__ void decide(const DomainDev& d, BlockShared& sm, int k, unsigned i, const Cand& p, int lin_c,
                                        const int c_c[3], const float cp_c[3]) {
   const BufDev& b = sm.bufs[k];
   const Grid& g = d.g;
@@ -207,7 +207,7 @@ __device__ __forceinline__ void decide(const DomainDev& d, Staged& sm, int k, un
 // and duplicates.
 template <int D, bool FULL, bool ROT>
 __device__ __forceinline__ void buffer_body(const DomainDev& d, unsigned bid, unsigned nblk) {
-  __shared__ Staged sm;
+  __shared__ BlockShared sm;
   const int lane = threadIdx.x & 31;
   const unsigned warp = (bid * blockDim.x + threadIdx.x) >> 5;
   const unsigned nwarps = (nblk * blockDim.x) >> 5;

@@ -64,3 +64,10 @@ def test_header_and_c_example_compile_as_c99(tmp_path):
     r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), "-c", src,
                         "-o", str(tmp_path / "channel.o")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No fallback: without the built library the binding raises instead of computing."""
+    monkeypatch.setattr(_ffi, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        _ffi.load(str(tmp_path / "libsphbuf.so"))

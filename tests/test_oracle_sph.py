@@ -136,6 +136,38 @@ def test_continuity_pressure_term_diffuses():
     assert np.all(drho[inner & (np.abs(x) < 0.6 * P.dp)] > 0)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_continuity_pressure_term_magnitude(dim):
+    # Eq. (4) at rest with the Riemann state of Eqs. (6)-(7): U_L = U_R = 0, so
+    # (v_i - v*_ij) . e_ij = (p_i - p_j) / (2 rho-bar c0) and
+    # drho_i/dt = (rho_i / rho-bar) / c0 sum_j V_j (p_i - p_j) dW/dr.
+    # For p = k x^2 the odd part of p_i - p_j cancels inside a full neighbourhood, leaving
+    # k sum_j V_j x_ji^2 |dW/dr|.  Its continuum limit is (d + 1) / d E_W[r] (integrate
+    # x^2 |W'| by parts over the support), and for the Wendland C2 kernel E_W[r] is a pair of
+    # Beta integrals: 2h/3 in 2-D, 5h/6 in 3-D, so the moment is h and 10h/9.  A lost factor
+    # 2 or c0, or the opposite sign of the pressure jump, fails the first check below
+    # (whether rho_i or rho-bar divides is second order here: |drho| / rho0 < 1e-6).
+    P = _params(dim)
+    n = 18 if dim == 2 else 10
+    pos = _lattice(dim, n, P.dp)
+    x = pos[:, 0] - 0.5 * n * P.dp
+    k = 2.0
+    rho = P.rho0 + k * x ** 2 / P.c0 ** 2  # p = k x^2 by Eq. (3); |drho| / rho0 < 1e-6
+    ff, fw = sph.neighbor_pairs(pos, np.zeros((0, dim)), P.h)
+    drho = sph.continuity_rate(P, np.zeros_like(pos), rho, ff, fw)
+    inner = _interior(pos, 0, n * P.dp, 2 * P.h)
+    # the same moment summed over an unbounded lattice
+    ax = np.arange(-4, 5) * P.dp
+    g = np.meshgrid(*([ax] * dim), indexing="ij")
+    X = np.stack([c.ravel() for c in g], axis=1)
+    r = np.linalg.norm(X, axis=1)
+    s = (r > 0) & (r < 2 * P.h)
+    m2_lattice = float(np.sum(P.dp ** dim * X[s, 0] ** 2 * -kernel.dW(r[s], P.h, dim)))
+    m2_continuum = P.h if dim == 2 else 10.0 * P.h / 9.0
+    assert np.allclose(drho[inner] / (k * m2_lattice / P.c0), 1.0, atol=2e-6)
+    assert abs(m2_lattice / m2_continuum - 1.0) < 0.025
+
+
 def test_boundary_pressure_term_cancels_truncation():
     # a lattice block at uniform pressure p_b: with Eq. (18) the edge particles feel no force
     dim = 2

@@ -93,18 +93,20 @@ def test_linear_pressure_field_gives_minus_grad_p_over_rho(dim):
     assert np.allclose(acc[inner, 1:], 0.0, atol=0.02 * G / P.rho0)
 
 
-def test_viscous_term_is_nu_laplacian():
-    dim = 2
+@pytest.mark.parametrize("dim", [2, 3])
+def test_viscous_term_is_nu_laplacian(dim):
     P = _params(dim, nu=2e-3)
-    pos = _lattice(dim, 20, P.dp)
-    A = 0.5  # v_x = A y^2  =>  nu lap v_x = 2 A nu
+    n = 20 if dim == 2 else 10
+    pos = _lattice(dim, n, P.dp)
+    A = 0.5  # v_x = A (y^2 [+ z^2])  =>  nu lap v_x = 2 (d - 1) A nu
     vel = np.zeros_like(pos)
-    vel[:, 0] = A * pos[:, 1] ** 2
+    vel[:, 0] = A * np.sum(pos[:, 1:] ** 2, axis=1)
     rho = np.full(pos.shape[0], P.rho0)
     ff, fw = sph.neighbor_pairs(pos, np.zeros((0, dim)), P.h)
     acc = sph.acceleration(P, vel, rho, np.full(pos.shape[0], np.nan), ff, fw)
-    inner = _interior(pos, 0, 20 * P.dp, 2 * P.h)
-    assert np.allclose(acc[inner, 0] / (2 * A * P.nu), 1.0, atol=0.04)
+    inner = _interior(pos, 0, n * P.dp, 2 * P.h)
+    want = 2 * (dim - 1) * A * P.nu
+    assert np.allclose(acc[inner, 0] / want, 1.0, atol=0.04)
 
 
 @pytest.mark.parametrize("dim", [2, 3])
@@ -182,6 +184,62 @@ def test_boundary_pressure_term_cancels_truncation():
     assert np.abs(with_bc).max() < 1e-12 * np.abs(without).max()
     edge = ~_interior(pos, 0, 12 * P.dp, 2 * P.h)
     assert np.abs(without[edge]).max() > 0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_uniform_pressure_is_in_equilibrium_inside_walls(dim):
+    # A fluid block at rest at uniform density, wrapped in a wall layer 2h thick that
+    # continues the fluid lattice.  The wall neighbours take p_j = p_i, rho_j = rho_i
+    # (reading A11), so every pair of Eq. (5) carries the same coefficient and the sum of
+    # grad W over a full lattice neighbourhood is zero by symmetry: no particle moves and
+    # Eq. (4) gives no density change.  Without the walls the edge particles are pushed
+    # out, so a wall term with the wrong sign, factor or state fails here.
+    P = _params(dim)
+    n = 10 if dim == 2 else 6
+    t = int(np.ceil(2 * P.h / P.dp))
+    grid = _lattice(dim, n + 2 * t, P.dp) - t * P.dp
+    inside = np.all((grid > 0) & (grid < n * P.dp), axis=1)
+    pos, wall = grid[inside], grid[~inside]
+    rho = np.full(pos.shape[0], P.rho0 + 50.0 / P.c0 ** 2)  # p = 50 Pa
+    vel = np.zeros_like(pos)
+    nan = np.full(pos.shape[0], np.nan)
+    ff, fw = sph.neighbor_pairs(pos, wall, P.h)
+    acc = sph.acceleration(P, vel, rho, nan, ff, fw)
+    scale = 50.0 / P.rho0 / P.dp
+    assert np.abs(acc).max() < 1e-10 * scale
+    assert np.abs(sph.continuity_rate(P, vel, rho, ff, fw)).max() < 1e-12 * P.rho0
+    ff0, fw0 = sph.neighbor_pairs(pos, np.zeros((0, dim)), P.h)
+    assert np.abs(sph.acceleration(P, vel, rho, nan, ff0, fw0)).max() > 0.1 * scale
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_wall_continuity_accumulates_the_stopped_mass_flux(dim):
+    # A fluid block at uniform density moving at -u e_x onto a flat wall slab (2h thick,
+    # 2h wider than the block on every side).  Between fluid particles v_i = v_j and
+    # p_i = p_j, so v* = v and Eq. (4) has no fluid term; the mirrored wall state of reading
+    # A11 gives v* = 0, so each wall pair adds 2 rho V (v_i . e_ij) dW/dr.  Summed over the
+    # block, the pairs straddling the wall plane give sum_i V drho_i/dt = rho0 u A times the
+    # lattice moment (1 in the continuum): the density rises at the rate of the mass flux
+    # the wall stops.  A wall at rest (v_j = 0) would give half of it; dropping the wall
+    # term, none.
+    P = _params(dim)
+    n = 8 if dim == 2 else 6
+    t = int(np.ceil(2 * P.h / P.dp))
+    pos = _lattice(dim, n, P.dp)
+    slab = _lattice(dim, n + 2 * t, P.dp) - t * P.dp
+    slab = slab[(slab[:, 0] < 0) & np.all(slab[:, 1:] > -t * P.dp, axis=1)]
+    u = 0.2
+    vel = np.zeros_like(pos)
+    vel[:, 0] = -u
+    rho = np.full(pos.shape[0], P.rho0)
+    ff, fw = sph.neighbor_pairs(pos, slab, P.h)
+    drho = sph.continuity_rate(P, vel, rho, ff, fw)
+    area = (n * P.dp) ** (dim - 1)
+    got = float(np.sum(P.dp ** dim * drho))
+    assert np.isclose(got, P.rho0 * u * area * _lattice_moment(dim, P.dp, P.h), rtol=1e-10)
+    reach = pos[:, 0] + 0.5 * P.dp < 2 * P.h  # the nearest wall layer sits at -dp/2
+    assert np.all(drho[reach] > 0.0)
+    assert np.all(drho[~reach] == 0.0)
 
 
 def test_wall_neighbours_stop_an_approaching_particle():

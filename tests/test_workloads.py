@@ -82,3 +82,29 @@ def test_config5_batched_star_channels():
             assert all(b.bc == wl.PRESSURE_OUTLET for b in c.buffers[1:])
         for b in c.buffers:
             assert math.isclose(b.extent[0], 4 * c.dp)
+
+
+def test_config4_tjunction_recipe_at_a_coarser_spacing():
+    # the same geometry at dp = 0.02 (0.4 M particles) scales to the 15.4 M of dp = 0.006
+    c = wl.tjunction_case(dp=0.02)
+    n = c.fluid_pos.shape[0]
+    assert abs(n * (0.02 / 0.006) ** 3 / 15.4e6 - 1) < 0.015
+    assert [b.bc for b in c.buffers] == [wl.VELOCITY_INLET, wl.PRESSURE_OUTLET, wl.PRESSURE_OUTLET]
+    normals = [b.rotation[0] for b in c.buffers]
+    angles = [math.degrees(math.acos(np.clip(normals[0] @ u, -1.0, 1.0))) for u in normals]
+    assert np.allclose(angles, [0.0, 0.0, 60.0], atol=1e-9)  # main outlet along the pipe, branch at 60 deg
+    assert np.allclose([b.extent[1] for b in c.buffers], [1.0, 1.0, 0.6])  # main R 0.5, branch R 0.3
+    for b in c.buffers:
+        assert math.isclose(b.extent[0], 4 * c.dp)
+
+
+def test_config2_bent_channel_recipe():
+    c = wl.config2()
+    assert c.dim == 2 and c.dp == 0.005
+    assert abs(c.fluid_pos.shape[0] / 0.38e6 - 1) < 0.01
+    inlet, outlet = c.buffers
+    assert (inlet.bc, outlet.bc) == (wl.VELOCITY_INLET, wl.PRESSURE_OUTLET)
+    deg = [math.degrees(math.atan2(b.rotation[0][1], b.rotation[0][0])) for b in c.buffers]
+    assert np.allclose(deg, [30.0, -15.0], atol=1e-9)
+    assert (inlet.umax, inlet.half_width) == (1.5, 0.5)  # parabolic profile over the 1 m width
+    assert math.isclose(inlet.extent[0], 4 * c.dp) and math.isclose(outlet.extent[0], 4 * c.dp)

@@ -647,7 +647,8 @@ def run_reference(args):
     budget = 120.0
     target = int(max(3000, min(200000, rate * budget / max(1, args.steps + args.warmup))))
     r, per_step, sample, npart = time_oracle(args.steps, args.warmup, target)
-    out = {"impl": "reference", "metric": METRIC, "value": r, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+    # n_gpus is the launch's N; the oracle itself runs on one host core of rank 0 (cpu_baseline)
+    out = {"impl": "reference", "metric": METRIC, "value": r, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD % args.length + " (bounded oracle sample)", "particles": npart},

@@ -22,7 +22,7 @@ def test_reference_arm_prints_one_contract_line():
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in rec, key
     assert rec["impl"] == "reference"
-    assert rec["steps"] == 1 and rec["warmup"] == 1
+    assert rec["steps"] == 1 and rec["warmup"] == 1 and rec["n_gpus"] == 1
     assert rec["value"] > 0 and rec["ms_per_step"] > 0
     assert rec["higher_is_better"] is True
     assert rec["unit"] == rec["cpu_baseline"]["unit"] == rec["e2e"]["unit"]

@@ -170,6 +170,56 @@ def test_continuity_pressure_term_magnitude(dim):
     assert abs(m2_lattice / m2_continuum - 1.0) < 0.025
 
 
+def _pair(P, r, vi, vj):
+    pos = np.array([[0.0, 0.0], [r, 0.0]])
+    vel = np.array([[vi, 0.0], [vj, 0.0]])
+    ff, fw = sph.neighbor_pairs(pos, np.zeros((0, 2)), P.h)
+    return pos, vel, ff, fw
+
+
+def test_riemann_velocity_at_rest_is_the_linear_acoustic_solution():
+    # Eq. (6) at rest: U* = (P_L - P_R) / (2 rho-bar c0) = (P_L - P_R) / (Z_L + Z_R) with the
+    # acoustic impedances Z = rho c0, the linear acoustic Riemann solution, at any density
+    # contrast.  Two particles at rest with a 20 % density jump; Eq. (4) carries U* as
+    # (v_i - v*_ij) . e_ij.  (Half the jump over rho_i alone would be off by 10 % here.)
+    P = _params(2, c0=10.0)
+    r = 1.1 * P.dp
+    _, vel, ff, fw = _pair(P, r, 0.0, 0.0)
+    rho = np.array([1000.0, 1200.0])
+    p = P.c0 ** 2 * (rho - P.rho0)
+    drho = sph.continuity_rate(P, vel, rho, ff, fw)
+    dw = float(kernel.dW(r, P.h, 2))
+    for i, j in ((0, 1), (1, 0)):
+        u_star = (p[i] - p[j]) / (rho[i] * P.c0 + rho[j] * P.c0)
+        assert np.isclose(drho[i], 2 * rho[i] * P.mass / rho[j] * u_star * dw, rtol=1e-12)
+
+
+@pytest.mark.parametrize("w", [0.05, 0.2, 1.0, 3.0, -0.5])
+def test_riemann_pressure_limiter(w):
+    # Two equal particles closing at 2w (w < 0: separating), U_L - U_R = 2w.  Eqs. (7)-(8):
+    # in expansion P* = P-bar (no dissipation); in weak compression the low-dissipation value
+    # P-bar + 3/2 rho (U_L - U_R)^2; once 3 (U_L - U_R) >= c0 the limiter gives the linear
+    # acoustic Riemann pressure P-bar + rho c0 (U_L - U_R) / 2.  Eq. (5) turns P* into
+    # a_i = -2 m P* / rho^2 grad W_ij (no viscosity here).
+    P = sph.make_params(2, 0.01, 1.3, 1000.0, 10.0, 0.0, 1e-4)
+    r = 1.1 * P.dp
+    _, vel, ff, fw = _pair(P, r, w, -w)
+    rho = np.full(2, 1001.0)
+    pbar = P.c0 ** 2 * 1.0
+    du = 2 * w
+    if du <= 0:
+        pstar = pbar
+    elif 3 * du < P.c0:
+        pstar = pbar + 1.5 * rho[0] * du ** 2
+    else:
+        pstar = pbar + 0.5 * rho[0] * P.c0 * du
+    acc = sph.acceleration(P, vel, rho, np.full(2, np.nan), ff, fw)
+    dw = float(kernel.dW(r, P.h, 2))
+    # e_01 = (r_0 - r_1) / r = -e_x, so a_0 = +2 m P* dW/dr / rho^2 e_x (dW/dr < 0: pushed back)
+    assert np.isclose(acc[0, 0], 2 * P.mass * pstar * dw / rho[0] ** 2, rtol=1e-12)
+    assert np.isclose(acc[1, 0], -acc[0, 0], rtol=1e-12) and acc[0, 1] == 0.0
+
+
 def test_boundary_pressure_term_cancels_truncation():
     # a lattice block at uniform pressure p_b: with Eq. (18) the edge particles feel no force
     dim = 2

@@ -216,3 +216,35 @@ def test_fp32_threshold_tie_is_not_a_crossing():
             crossed = True
             break
     assert crossed
+
+
+def test_boundary_velocity_states_after_a_step():
+    # After a full FP64 step of a small 3-D pipe along an oblique axis d:
+    #  - velocity-inlet particles carry the pipe profile of Eqs. (23)-(26) with reading A15,
+    #    v = U (1 - rho^2 / R^2) d, rho their distance from the pipe's axis (a closed form from
+    #    the geometry; the drift and the recycling move them along d, which keeps rho);
+    #  - pressure-outlet particles carry the projection of Eq. (19), v parallel to u = d.
+    axis = np.array([1.0, -2.0, 0.5])
+    d = axis / np.linalg.norm(axis)
+    U, R = 0.5, 0.08
+    case = wl.pipe_case(length=0.3, radius=R, dp=0.02, axis=tuple(axis), inlet_bc=wl.VELOCITY_INLET,
+                        outlet_bc=wl.PRESSURE_OUTLET, umax=U, init_velocity="profile", c0=5.0, nu=1e-3,
+                        umax_est=U, seed=9)
+    sim = OB.OracleSim(case)
+    sim.commit()
+    b_in, b_out = sim.buffers
+    was_in = set(sim.id[sim.label == b_in.label].tolist())
+    was_out = set(sim.id[sim.label == b_out.label].tolist())
+    assert was_in and was_out
+    sim.step(1)
+    ids = sim.id.tolist()
+    rows_in = [ids.index(i) for i in was_in]
+    x = sim.pos[rows_in]
+    rho2 = np.sum(x * x, axis=1) - (x @ d) ** 2  # the pipe's axis passes through the origin
+    want = U * np.clip(1.0 - rho2 / R ** 2, 0.0, None)[:, None] * d[None, :]
+    assert np.allclose(sim.vel[rows_in], want, atol=1e-12)
+    assert np.allclose(b_in.u, d) and np.allclose(b_out.u, d)
+    rows_out = [ids.index(i) for i in was_out if i in set(ids)]
+    v = sim.vel[rows_out]
+    assert np.abs(np.cross(v, d)).max() < 1e-12 * max(1.0, np.abs(v).max())
+    assert np.abs(v @ d).max() > 0  # the outlet particles do move

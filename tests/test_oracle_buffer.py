@@ -248,3 +248,14 @@ def test_boundary_velocity_states_after_a_step():
     v = sim.vel[rows_out]
     assert np.abs(np.cross(v, d)).max() < 1e-12 * max(1.0, np.abs(v).max())
     assert np.abs(v @ d).max() > 0  # the outlet particles do move
+
+
+def test_plug_inlet_flux_is_u_times_width():
+    # The volume flux through a buffer (the Q that drives the Windkessel outlet of Eq. (31)) is
+    # sum over its particles of (v . u) dp^d / a.  A plug velocity inlet holds one particle per
+    # layer per lane and imposes v = U u, so Q = U x (lanes dp) = U x width exactly.
+    case = _channel(angle=21.0)
+    sim = OB.OracleSim(case)
+    sim.commit()
+    sim.step(1)
+    assert sim.flux[0] == pytest.approx(1.0 * 0.2, rel=1e-12)

@@ -71,3 +71,78 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(_ffi, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         _ffi.load(str(tmp_path / "libsphbuf.so"))
+
+
+# ------------------------------------------------------------------ host-side error behaviour
+_HOST_ONLY = {"sphbuf_status_string", "sphbuf_error_message", "sphbuf_create_domain", "sphbuf_rotation_from_normal",
+              "sphbuf_probe_launch_floor", "sphbuf_cell_list_build", "sphbuf_cell_list_build_noalloc"}
+
+
+def _zero_args(argtypes):
+    import ctypes
+
+    ints = (ctypes.c_int, ctypes.c_uint, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32)
+    return [0 if a in ints else 0.0 if a is ctypes.c_double else None for a in argtypes]
+
+
+def test_every_handle_call_rejects_a_null_handle(lib):
+    # every entry point that takes a domain or batch handle returns SPHBUF_ERR_INVALID_ARG
+    # for a NULL handle (and NULL / zero for the rest), before any CUDA call: no crash, no trap
+    names = sorted(set(_ffi.SIGNATURES) - _HOST_ONLY)
+    assert len(names) >= 35
+    for name in names:
+        _, argtypes = _ffi.SIGNATURES[name]
+        assert getattr(lib, name)(*_zero_args(argtypes)) == 1, name
+
+
+def _desc(**kw):
+    d = _ffi.DomainDesc(dim=3, dp=0.01, h_over_dp=1.3, rho0=1000.0, c0=10.0, nu=1e-3, dt=1e-4, capacity=1000)
+    for x in range(3):
+        d.lo[x], d.hi[x] = 0.0, 1.0
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+@pytest.mark.parametrize("bad", [dict(dim=1), dict(dim=4), dict(dp=0.0), dict(dp=float("nan")),
+                                 dict(h_over_dp=-1.0), dict(rho0=0.0), dict(c0=0.0), dict(dt=0.0),
+                                 dict(nu=-1.0), dict(capacity=0), dict(capacity=1 << 25), "empty_box"])
+def test_create_domain_validates_its_descriptor(lib, bad):
+    import ctypes
+
+    d = _desc() if bad == "empty_box" else _desc(**bad)
+    if bad == "empty_box":
+        d.hi[1] = d.lo[1]
+    h = ctypes.c_void_p(1)
+    assert lib.sphbuf_create_domain(ctypes.byref(d), None, ctypes.byref(h)) == 1
+    assert h.value is None  # *out is cleared
+    assert lib.sphbuf_create_domain(None, None, ctypes.byref(h)) == 1
+
+
+def test_create_domain_without_a_gpu_reports_a_cuda_error(lib):
+    import ctypes
+
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    d = _desc()
+    h = ctypes.c_void_p(1)
+    assert lib.sphbuf_create_domain(ctypes.byref(d), None, ctypes.byref(h)) == 4  # SPHBUF_ERR_CUDA
+    assert h.value is None
+
+
+def test_host_helpers_reject_bad_input(lib):
+    import ctypes
+
+    R = (ctypes.c_double * 9)()
+    for n in ((0.0, 0.0, 0.0), (float("nan"), 0.0, 0.0), (float("inf"), 1.0, 0.0)):
+        assert lib.sphbuf_rotation_from_normal((ctypes.c_double * 3)(*n), 0.0, R) == 1, n
+    assert lib.sphbuf_rotation_from_normal((ctypes.c_double * 3)(1.0, 0.0, 0.0), 0.0, None) == 1
+    us = ctypes.c_double()
+    assert lib.sphbuf_probe_launch_floor(0, 0, 0, 0, 0, None, ctypes.byref(us)) == 1
+    assert lib.sphbuf_cell_list_build(None, None, None, 0, 0, None, None, None) == 1
+    assert lib.sphbuf_cell_list_build_noalloc(None, None, None, 0, 0, None, None, None) == 1
+    names = [lib.sphbuf_status_string(s) for s in range(8)]
+    assert len(set(names)) == 8 and all(names)
+    assert lib.sphbuf_status_string(8) == lib.sphbuf_status_string(-1) == b"unknown status"

@@ -146,3 +146,20 @@ def test_host_helpers_reject_bad_input(lib):
     names = [lib.sphbuf_status_string(s) for s in range(8)]
     assert len(set(names)) == 8 and all(names)
     assert lib.sphbuf_status_string(8) == lib.sphbuf_status_string(-1) == b"unknown status"
+
+
+def test_binding_raises_instead_of_falling_back(lib):
+    # without a GPU the Python binding raises the library's status; nothing runs on the CPU
+    import torch
+
+    from paper_2406_16786_gb300 import workloads as wl
+    from paper_2406_16786_gb300.domain import Domain, SphbufError, rotation_from_normal
+
+    with pytest.raises(SphbufError) as e:
+        rotation_from_normal([0.0, 0.0, 0.0])
+    assert e.value.status == 1
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(SphbufError) as e:
+        Domain.from_case(wl.config1())
+    assert e.value.status == 4 and "CUDA error" in str(e.value)

@@ -282,17 +282,7 @@ def run_gpu(args):
     hbm = peaks.get("hbm_gbs")
     bu_s = per["buffer"] / 1e3
     bu_gbs = bu_bytes / bu_s / 1e9 if bu_s > 0 else None
-    # the floor of a kernel with the buffer kernel's grid (one wave of 4 blocks per SM at most,
-    # 32 candidate cells per block), timed the same way: nothing, one load, two dependent loads
-    from paper_2406_16786_gb300.domain import probe_launch_floor
-
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
-    bu_blocks = max(1, min((cells + 31) // 32, 4 * sm_count))
-    floor = {"blocks": bu_blocks, "threads": 256}
-    for fl in (False, True):
-        for ld, key in ((0, "empty"), (1, "one_load"), (2, "two_dependent_loads")):
-            floor[key + ("_cold_l2" if fl else "")] = probe_launch_floor(bu_blocks, 256, ld, fl, 50, stream)
-
     # neighbour passes, bound by FP32 arithmetic: algorithmic flops per particle
     pairs = lattice_pairs(dim, case.h_over_dp)          # neighbours within 2h on the lattice
     cands = 27 * (2 * case.h_over_dp) ** dim            # particles in the 27 cells of side 2h
@@ -406,8 +396,7 @@ def run_gpu(args):
                                    "unit": "GB/s", "frac": (bu_gbs / hbm) if (bu_gbs and hbm) else None,
                                    "traffic": traffic_of("k_buffer", n_mean), "bytes_per_step": bu_bytes, "candidate_cells": cells,
                                    "candidate_particles": parts, "injected": len(inj), "deleted": len(dels),
-                                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                                   "launch_floor_us": floor},
+                                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,

@@ -316,10 +316,12 @@ sphbuf_status sphbuf_read_launch_count(sphbuf_domain_t d, uint64_t *launches);
  * cell[n] (linear cell index in [0, ncell)), id[n], optional label[n] (entries equal to 255
  * are skipped; NULL = none skipped).  Writes cell_start[ncell + 1] (exclusive prefix sum of
  * the per-cell counts) and order[n_kept]: order[p] = input index of the particle in sorted
- * slot p, sorted by (cell, id).  Ids within one cell must be distinct.  Scratch memory is
- * allocated and freed on the stream (cudaMallocAsync).  Returns INVALID_ARG for a cell index
- * outside [0, ncell) (checked on the device, reported at the end of the call, which
- * synchronises the stream). */
+ * slot p, sorted by (cell, id).  Ids within one cell must be distinct; at most 1024 particles
+ * may share one cell (a particle is ranked inside its cell by comparing it with every other
+ * particle of the cell).  Scratch memory is allocated and freed on the stream
+ * (cudaMallocAsync).  Returns INVALID_ARG for a cell index outside [0, ncell) or a cell with
+ * more than 1024 particles (checked on the device, reported at the end of the call, which
+ * synchronises the stream; order[] is then incomplete). */
 sphbuf_status sphbuf_cell_list_build(const int32_t *cell, const uint32_t *id, const uint8_t *label,
                                      uint64_t n, uint64_t ncell, uint32_t *cell_start,
                                      uint32_t *order, void *cuda_stream);
@@ -360,15 +362,18 @@ sphbuf_status sphbuf_batch_destroy(sphbuf_batch_t b);
  * device memory: for example a host program whose GPU memory is already fully reserved by
  * another allocator, or a latency-bound loop in which cudaMalloc / cudaFree (which can
  * synchronise the device) are not acceptable.  This call performs no cudaMalloc, cudaFree or
- * other allocating call; its scratch lives in a fixed array inside the library (about 16 MiB,
- * held by every GPU that loads the library until the process exits).  The paper has no
- * counterpart of this entry point.
+ * other allocating call; its scratch lives in a fixed array inside the library (about 16 MiB).
+ * A GPU holds that array from the library's first use on it (when the library's device code
+ * is loaded there, which may be lazy) until the process exits: a caller that hands all the
+ * remaining device memory to another allocator should make one call (or any other library
+ * call that launches work) on that device first.  The paper has no counterpart of this entry
+ * point.
  *   Limits: n <= 1048576 particles and ncell <= 1048575 cells; larger sizes return
  *   SPHBUF_ERR_CAPACITY without doing any work.
  *   Inputs, outputs and errors as for sphbuf_cell_list_build (the call synchronises the stream).
- *   The first call on each device looks up the array's device address with that device
- *   current (the device current at the call); make that first call before any stream
- *   capture.
+ *   Every call looks up the array's address on the device current at the call (no
+ *   allocation); the first call on a device may load the library's device code there, so
+ *   make that first call before any stream capture.
  *   All calls share the one array and it keeps the last call's contents (each call clears the
  *   parts that must start at zero): calls whose work overlaps on the GPU, from several streams
  *   or threads, race and give wrong results; serialise them. */
@@ -376,18 +381,6 @@ sphbuf_status sphbuf_cell_list_build_noalloc(const int32_t *cell, const uint32_t
                                              const uint8_t *label, uint64_t n, uint64_t ncell,
                                              uint32_t *cell_start, uint32_t *order,
                                              void *cuda_stream);
-
-/* Measurement aid (not part of the method): the time of one launch of a probe kernel with the
- * grid blocks x threads that does nothing (loads = 0), one scattered load per thread
- * (loads = 1) or two dependent loads per thread (loads = 2), timed with CUDA events around
- * the launch on cuda_stream (NULL: the default stream) as the domain's phase times are, and
- * averaged over reps launches after three untimed ones.  flush_l2 != 0 writes 256 MB before
- * each launch so that the loads miss L2.  It allocates and frees about 128 MB (+ 256 MB with
- * flush_l2) of device memory per call and synchronises the stream.  The buffer update's time
- * is read against this floor.  SPHBUF_ERR_INVALID_ARG for blocks < 1, threads outside
- * 32..1024, loads outside 0..2 or reps < 1. */
-sphbuf_status sphbuf_probe_launch_floor(int blocks, int threads, int loads, int flush_l2, int reps,
-                                        void *cuda_stream, double *us_per_launch);
 
 #ifdef __cplusplus
 }

@@ -65,8 +65,6 @@ SIGNATURES = {
     "sphbuf_write_particles_async": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, ctypes.c_uint64, ctypes.c_uint32]),
     "sphbuf_read_particles_async": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, ctypes.c_uint64, P(ctypes.c_uint64)]),
     "sphbuf_io_wait": (ctypes.c_int, [vp]),
-    "sphbuf_probe_launch_floor": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                                 vp, P(ctypes.c_double)]),
     "sphbuf_batch_sync": (ctypes.c_int, [vp]),
     "sphbuf_batch_destroy": (ctypes.c_int, [vp]),
     "sphbuf_cell_list_build": (ctypes.c_int, [vp, vp, vp, c_u64, c_u64, vp, vp, vp]),

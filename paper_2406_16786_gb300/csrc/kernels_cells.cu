@@ -11,8 +11,6 @@
 //   finalize particle count, next id, and the particle ranges of the buffers' candidate cells
 // The result is sorted by (cell, id) whatever order the atomics took, so it is
 // deterministic and identical to a plain sort.
-#include <mutex>
-
 #include "apply.cuh"
 #include "kernels.cuh"
 
@@ -329,6 +327,9 @@ __device__ __forceinline__ void finalize_body(const DomainDev& d, int count_step
   if (bid == 0 && threadIdx.x == 0) {
     st->n = d.cell_start[d.g.ncell];
     st->next_id += min(st->n_inj, d.P.list_cap);
+    // the next step's neighbour pass counts its deferred particles from zero (reset here, in
+    // a launch of its own, not by that pass's first block while the others add to it)
+    st->n_defer = 0;
     if (count_step) {
       st->step += 1;
       // Sec. 5.3: re-establish the frames of rotating buffers for the next step (their
@@ -559,12 +560,21 @@ __global__ void k_keys_raw(const int32_t* cell, const uint32_t* id, unsigned n, 
   }
 }
 
+// Rank of each particle among its cell's ids: O(m) loads per particle of a cell of m, so the
+// stand-alone entry points accept at most kMaxPerCellRaw particles in one cell (a larger cell
+// sets the input flag and is left unsorted instead of running for minutes).
+constexpr unsigned kMaxPerCellRaw = 1024;
+
 __global__ void k_order_raw(const int32_t* cell, const uint32_t* id, unsigned n, const unsigned* slot,
-                            const unsigned* start, const unsigned* tmp, uint32_t* order) {
+                            const unsigned* start, const unsigned* tmp, uint32_t* order, int* bad) {
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (slot[i] == kNoSlot) continue;
     const int c = cell[i];
     const unsigned s0 = start[c], s1 = start[c + 1], my = id[i];
+    if (s1 - s0 > kMaxPerCellRaw) {
+      atomicExch(bad, 1);
+      continue;
+    }
     unsigned rank = 0;
     for (unsigned p = s0; p < s1; ++p) rank += tmp[p] < my;
     order[s0 + rank] = i;
@@ -686,7 +696,7 @@ cudaError_t cell_list_build(const int32_t* cell, const uint32_t* id, const uint8
     k_hist_raw<<<blocks, 256, 0, s>>>(cell, label, nn, (long long)ncell, cnt, slot, bad);
     scan_cells(cnt, part, start, tiles, nullptr, s);
     k_keys_raw<<<blocks, 256, 0, s>>>(cell, id, nn, slot, start, tmp);
-    k_order_raw<<<blocks, 256, 0, s>>>(cell, id, nn, slot, start, tmp, order);
+    k_order_raw<<<blocks, 256, 0, s>>>(cell, id, nn, slot, start, tmp, order, bad);
     chk(cudaGetLastError());
     chk(cudaMemcpyAsync(cell_start, start, (size_t)(ncell + 1) * sizeof(unsigned), cudaMemcpyDeviceToDevice, s));
     int hbad = 0;
@@ -707,7 +717,8 @@ cudaError_t cell_list_build(const int32_t* cell, const uint32_t* id, const uint8
 //
 // For callers that cannot allocate device memory.  Layout of the array (32-bit words):
 //   count[kNaPad] | start[kNaPad + 1] | part[kNaTiles] | slot[kNaMaxN] | tmp[kNaMaxN] | flag[1]
-// Every GPU that loads the library holds this array (about 16 MiB) until the process exits.
+// A GPU holds this array (about 16 MiB) from the library's first use on it (when its device
+// code is loaded there) until the process exits.
 namespace {
 
 constexpr unsigned long long kNaMaxN = 1ull << 20;          // particles per call
@@ -724,24 +735,15 @@ constexpr size_t kNaWords = kNaFlag + 4;
 
 static __device__ __align__(256) unsigned g_noalloc_scratch[kNaWords];
 
-constexpr int kNaMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-unsigned* g_noalloc_ptr[kNaMaxDevices] = {};
-
-// Device address of the scratch array for the current device, looked up once per device.
+// Device address of the scratch array on the current device, looked up on every call
+// (cudaGetSymbolAddress allocates nothing; a cached address would go stale after a
+// cudaDeviceReset reloads the module).  The first lookup on a device loads the library's
+// device code there if it was not loaded yet, which is when the array is reserved.
 cudaError_t noalloc_scratch(unsigned** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_noalloc_ptr[dev] = static_cast<unsigned*>(p);
-  }
-  *out = g_noalloc_ptr[dev];
+  *out = static_cast<unsigned*>(p);
   return cudaSuccess;
 }
 
@@ -777,7 +779,7 @@ cudaError_t cell_list_build_noalloc(const int32_t* cell, const uint32_t* id, con
   k_hist_raw<<<blocks, 256, 0, s>>>(cell, label, nn, (long long)ncell, cnt, slot, bad);
   scan_cells(cnt, part, start, tiles, nullptr, s);
   k_keys_raw<<<blocks, 256, 0, s>>>(cell, id, nn, slot, start, tmp);
-  k_order_raw<<<blocks, 256, 0, s>>>(cell, id, nn, slot, start, tmp, order);
+  k_order_raw<<<blocks, 256, 0, s>>>(cell, id, nn, slot, start, tmp, order, bad);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(cell_start, start, (size_t)(ncell + 1) * sizeof(unsigned), cudaMemcpyDeviceToDevice, s);

@@ -23,12 +23,13 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Step prologue, run by one thread of the step's first kernel: per-step constants.
+// Step prologue, run by one thread of the step's first kernel: per-step constants.  (The
+// deferred-particle count is not reset here: the other blocks of the neighbour pass add to it
+// while this runs; the rebuild's last pass zeroes it at the end of every step.)
 __device__ __forceinline__ void begin_step(const DomainDev& d) {
   StepState* st = d.st;
   st->n_inj = 0;
   st->n_del = 0;
-  st->n_defer = 0;
   // Eq. (10): p_max = lambda rho0 v_max^2 with v_max of the last force pass (0 at the start)
   const double vmax = (double)__uint_as_float(st->vmax_bits);
   st->p_max = (float)((double)d.P.tvf_lambda * d.P.rho0_d * vmax * vmax);
@@ -414,9 +415,9 @@ __device__ __forceinline__ void neighbours_body(const DomainDev& d, unsigned bid
   }
 }
 
-// The deferred particles of the density pass: Eq. (4) rate for buffer particles (plain v_j
-// of the neighbours, their start-of-step density), Eq. (9) from the cells for fluid
-// particles with an overflowed list.
+// The deferred particles of the density pass: Eq. (4) rate for buffer particles (the Riemann
+// intermediate velocity of reading A9 against the neighbours' start-of-step velocity and
+// density, density_term), Eq. (9) from the cells for fluid particles with an overflowed list.
 template <int D>
 __device__ __forceinline__ void density_deferred_body(const DomainDev& d, unsigned bid, unsigned nblk) {
   if (d.st->status) return;

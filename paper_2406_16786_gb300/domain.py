@@ -63,20 +63,6 @@ def cell_list_build(cell_dev: int, id_dev: int, label_dev: Optional[int], n: int
         raise SphbufError(st, "cell_list_build")
 
 
-def probe_launch_floor(blocks: int, threads: int, loads: int, flush_l2: bool = False, reps: int = 50,
-                       stream=None) -> float:
-    """Microseconds of one event-timed launch of a probe kernel (blocks x threads) doing
-    nothing (loads 0), one scattered load (1) or two dependent loads (2) per thread."""
-    lib = _ffi.load()
-    us = ctypes.c_double()
-    handle = _stream_handle(stream)
-    st = lib.sphbuf_probe_launch_floor(int(blocks), int(threads), int(loads), 1 if flush_l2 else 0, int(reps),
-                                       None if handle is None else ctypes.c_void_p(handle), ctypes.byref(us))
-    if st:
-        raise SphbufError(st, "probe_launch_floor")
-    return us.value
-
-
 class Batch:
     """Independent domains stepped together by multi-domain kernel launches."""
 

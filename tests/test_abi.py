@@ -75,7 +75,7 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
 
 # ------------------------------------------------------------------ host-side error behaviour
 _HOST_ONLY = {"sphbuf_status_string", "sphbuf_error_message", "sphbuf_create_domain", "sphbuf_rotation_from_normal",
-              "sphbuf_probe_launch_floor", "sphbuf_cell_list_build", "sphbuf_cell_list_build_noalloc"}
+              "sphbuf_cell_list_build", "sphbuf_cell_list_build_noalloc"}
 
 
 def _zero_args(argtypes):
@@ -139,8 +139,6 @@ def test_host_helpers_reject_bad_input(lib):
     for n in ((0.0, 0.0, 0.0), (float("nan"), 0.0, 0.0), (float("inf"), 1.0, 0.0)):
         assert lib.sphbuf_rotation_from_normal((ctypes.c_double * 3)(*n), 0.0, R) == 1, n
     assert lib.sphbuf_rotation_from_normal((ctypes.c_double * 3)(1.0, 0.0, 0.0), 0.0, None) == 1
-    us = ctypes.c_double()
-    assert lib.sphbuf_probe_launch_floor(0, 0, 0, 0, 0, None, ctypes.byref(us)) == 1
     assert lib.sphbuf_cell_list_build(None, None, None, 0, 0, None, None, None) == 1
     assert lib.sphbuf_cell_list_build_noalloc(None, None, None, 0, 0, None, None, None) == 1
     names = [lib.sphbuf_status_string(s) for s in range(8)]

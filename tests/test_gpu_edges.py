@@ -145,3 +145,29 @@ def test_physics_steps_are_deterministic():
         assert a.counters(k) == b.counters(k)
     a.close()
     b.close()
+
+
+def test_nan_velocity_written_by_the_host_latches_the_nan_status():
+    """A NaN velocity written through sphbuf_write_particles (the transfer checks cells,
+    offsets, labels and ids, not velocities) makes the step's drift non-finite: the step
+    stops with SPHBUF_ERR_NAN at the next synchronising call, without a device fault, and a
+    clean write afterwards steps normally."""
+    from paper_2406_16786_gb300.domain import SphbufError
+
+    case = cases.physics_case(2)
+    d = _dom(case)
+    clean = d.read()
+    s = {k: v.copy() for k, v in clean.items()}
+    s["vel"][s["id"].shape[0] // 3, 0] = np.nan
+    nid = int(s["id"].max()) + 1
+    d.write_particles(s["cell"], s["frac"], s["vel"], s["rho"], ids=s["id"], labels=s["label"], next_id=nid)
+    d.step(1)
+    with pytest.raises(SphbufError) as e:
+        d.sync()
+    assert e.value.status == 6
+    d.write_particles(clean["cell"], clean["frac"], clean["vel"], clean["rho"], ids=clean["id"],
+                      labels=clean["label"], next_id=nid)
+    d.step(2)
+    d.sync()
+    assert d.global_counters()["escaped"] >= 0 and d.count() > 0
+    d.close()

@@ -1,0 +1,146 @@
+"""The full-size synthetic workloads run to their stated lengths on the GPU.
+
+* 2-D bent channel (inlet leg at +30 deg, bend, outlet leg at -15 deg; parabolic velocity inlet
+  Umax 1.5, pressure outlet), dp 0.005, 0.38 M particles: 2000 steps.
+* 3-D pipe R 0.5 along (1,1,1)/sqrt3 with two bidirectional pressure buffers (inlet
+  50 sin(pi t) Pa, outlet 0), dp 0.01: L = 8 m (6.3 M particles) and the 4.0 M bench length
+  (L = 5.09 m), 1000 steps each (1.07 s of simulated time).
+* 3-D T-junction (velocity inlet, two pressure outlets at arbitrary orientations), dp 0.006,
+  15.4 M particles: 500 steps.
+* 64 star channels (1-6 arms, mixed buffer types) stepped as one batch in graph replay with
+  the autotuner's grid: 500 steps, and every domain bit-for-bit equal to its own plain run
+  of 500 steps.
+
+Every run must end with status OK and:
+  * the count invariant N = N0 + injected - deleted exactly, with no escaped particle;
+  * the FP64 mass balance: mass in - mass out = (N - N0) m;
+  * max |rho - rho0| / rho0 below the workload's bound (stated per run: a few times the
+    Mach-number estimate U^2 / c0^2 or p / (rho0 c0^2) of the flow);
+  * at buffers whose flow enters the domain (velocity inlets, and the bidirectional inlet of
+    the pipe, whose driving pressure keeps the flow forward for the whole 1.07 s), deletions
+    at the outer face within a budget: none at a velocity inlet (Algorithm 1 deletes
+    nothing), at most 2 % of its injections at the pipe's bidirectional inlet.
+The wall time of each run is printed.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2406_16786_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+INFLOW_KINDS = (wl.VELOCITY_INLET, wl.PRESSURE_INLET)
+
+
+def _check_run(dom, case, n0, steps, rho_bound, inflow_side, outer_budget):
+    """Invariants at the end of a run; returns a dict of the figures (also printed)."""
+    g = dom.global_counters()
+    n = dom.count()
+    cnt = [dom.counters(k) for k in range(len(case.buffers))]
+    inj = sum(c["injected"] for c in cnt)
+    dels = sum(c["deleted"] for c in cnt)
+    mass = case.rho0 * case.dp ** case.dim
+    net = sum(c["mass_in"] for c in cnt) - sum(c["mass_out"] for c in cnt)
+    st = dom.read()
+    drho = float(np.max(np.abs(st["rho"].astype(np.float64) - case.rho0)) / case.rho0) if n else 0.0
+    fig = {"particles": n, "n0": n0, "steps": g["steps"], "injected": [c["injected"] for c in cnt],
+           "deleted": [c["deleted"] for c in cnt], "max_drho": drho, "escaped": g["escaped"]}
+    print(case.name, fig)
+    assert g["steps"] == steps and g["escaped"] == 0
+    assert n == n0 + inj - dels
+    assert abs(net - (n - n0) * mass) <= 1e-9 * max(1.0, abs(net))
+    assert drho < rho_bound, drho
+    for k in inflow_side:
+        b = case.buffers[k]
+        if b.bc in INFLOW_KINDS:
+            assert cnt[k]["deleted"] == 0
+        else:
+            assert cnt[k]["deleted"] <= outer_budget * max(cnt[k]["injected"], 1), (k, cnt[k])
+    return fig
+
+
+def _run(case, steps, rho_bound, inflow_side=(), outer_budget=0.0):
+    from paper_2406_16786_gb300.domain import Domain
+
+    dom = Domain.from_case(case)
+    dom.use_graph(True)
+    n0 = dom.count()
+    t0 = time.perf_counter()
+    dom.step(steps)
+    dom.sync()
+    wall = time.perf_counter() - t0
+    fig = _check_run(dom, case, n0, steps, rho_bound, inflow_side, outer_budget)
+    print("%s: %d steps in %.2f s of wall time (%.3f ms/step)" % (case.name, steps, wall, 1e3 * wall / steps))
+    dom.close()
+    return fig
+
+
+def test_bent_channel_2000_steps():
+    c = wl.config2()
+    # U = 1.5, c0 = 15: U^2 / c0^2 = 1 %
+    _run(c, 2000, rho_bound=0.05, inflow_side=[0])
+
+
+@pytest.mark.parametrize("length", [8.0, 5.09])
+def test_pipe_1000_steps(length):
+    c = wl.config3(length=length)
+    # 50 Pa / (rho0 c0^2) = 0.56 %
+    _run(c, 1000, rho_bound=0.03, inflow_side=[0], outer_budget=0.02)
+
+
+def test_tjunction_500_steps():
+    c = wl.config4()
+    # U = 1, c0 = 10: 1 %
+    _run(c, 500, rho_bound=0.05, inflow_side=[0])
+
+
+def test_batched_stars_500_steps_equal_plain_runs():
+    from paper_2406_16786_gb300.domain import Batch, Domain
+
+    stars = wl.config5()
+    steps = 500
+    # every domain alone (graph replays), its final state kept on the host
+    alone = []
+    t0 = time.perf_counter()
+    for c in stars:
+        d = Domain.from_case(c)
+        d.use_graph(True)
+        d.step(steps)
+        d.sync()
+        alone.append((d.read(), d.global_counters(), [d.counters(k) for k in range(len(c.buffers))]))
+        d.close()
+    t_plain = time.perf_counter() - t0
+    # the autotuner's grid, chosen on a separate copy of the domains (its trial steps advance
+    # the domains it times)
+    trial = [Domain.from_case(c) for c in stars]
+    tb = Batch(trial)
+    m, _ = tb.autotune(trial_steps=2)
+    tb.close()
+    for d in trial:
+        d.close()
+    doms = [Domain.from_case(c) for c in stars]
+    n0 = [d.count() for d in doms]
+    b = Batch(doms)
+    b.set_grid(m)
+    b.use_graph(True)
+    t0 = time.perf_counter()
+    b.step(steps)
+    b.sync()
+    t_batch = time.perf_counter() - t0
+    print("64 star channels, %d steps: plain runs %.2f s, batch %.2f s (grid multiplier %d)"
+          % (steps, t_plain, t_batch, m))
+    for q, (c, d) in enumerate(zip(stars, doms)):
+        ra, ga, ca = alone[q]
+        rt = d.read()
+        for key in ra:
+            assert np.array_equal(ra[key], rt[key]), (q, key)
+        assert d.global_counters() == ga
+        assert [d.counters(k) for k in range(len(c.buffers))] == ca
+        # stars: U = 1, c0 = 10
+        inflow = [k for k, bs in enumerate(c.buffers) if bs.bc in INFLOW_KINDS]
+        _check_run(d, c, n0[q], steps, 0.05, inflow, 0.0)
+    b.close()
+    for d in doms:
+        d.close()

@@ -3,7 +3,11 @@
 Both sides start from the same seeded FP32 state (the oracle reads it in FP64).  Particles are
 matched by id.  Tolerances (relative L2 over all particles unless stated):
   density 1e-5;  pressure |dp| / (max(rho, rho0) c0^2) <= 1e-6 per particle;  velocity 1e-5;
-  position 1e-6 cs per particle;  acceleration (from the velocity change) 2e-4.
+  position 1e-6 cs per particle;  acceleration (from the velocity change) 2e-4, over the fluid
+  particles and, on their own, over the buffer particles (whose change carries the boundary
+  pressure term of Eq. (18) and the projection of Eq. (19), or the profile of Eqs. (23)-(26)),
+  where each particle's change is also held to 2e-3 of the larger of its own and the buffer's
+  RMS change.
 The id sets (the injections and deletions of the step) must be identical.
 """
 import numpy as np
@@ -87,6 +91,7 @@ def _one_step_vs_oracle(case, v_change_tol=0.0):
     assert np.array_equal(g0["id"].astype(np.int64), ora.id)
     assert np.array_equal(g0["label"].astype(np.int64), ora.label)
     v_before = {int(i): v for i, v in zip(ora.id, ora.vel)}
+    lab_before = {int(i): int(lb) for i, lb in zip(ora.id, ora.label)}
     dom.step(1)
     ora.step(1)
     g = dom.read()
@@ -110,6 +115,18 @@ def _one_step_vs_oracle(case, v_change_tol=0.0):
     dv_o = np.stack([v_o[m] - v_before[int(i)] for m, i in enumerate(ids) if keep[m]])
     dv_g = np.stack([v_g[m] - v_before[int(i)] for m, i in enumerate(ids) if keep[m]])
     assert _rel_l2(dv_g, dv_o) < 2e-4
+    # the buffer particles of the step's start, on their own
+    bkeep = np.array([lab_before.get(int(i), 0) != 0 for i in ids])
+    if bkeep.any():
+        bdv_o = np.stack([v_o[m] - v_before[int(i)] for m, i in enumerate(ids) if bkeep[m]])
+        bdv_g = np.stack([v_g[m] - v_before[int(i)] for m, i in enumerate(ids) if bkeep[m]])
+        err = np.linalg.norm(bdv_g - bdv_o, axis=1)
+        mag = np.linalg.norm(bdv_o, axis=1)
+        rms = float(np.sqrt(np.mean(mag ** 2)))
+        print("buffer particles %d: dv rel L2 %.2e, worst per-particle %.2e of max(|dv|, rms)" % (
+            bdv_o.shape[0], _rel_l2(bdv_g, bdv_o), float(np.max(err / np.maximum(mag, rms)))))
+        assert _rel_l2(bdv_g, bdv_o) < 2e-4
+        assert np.all(err <= 2e-3 * np.maximum(mag, rms))
     inj, dels = dom.last_decisions()
     assert [(k, p) for k, p, _ in inj] == [(k, p) for k, p, _ in ora.last_inj]
     assert sorted(dels) == sorted(ora.last_del)

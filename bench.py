@@ -40,14 +40,14 @@ METRIC = "particle-steps/s at 4M (3-D pipe, 2 bidirectional pressure buffers); b
 UNIT = "particle-steps/s"
 FP32_LANES_PER_SM = 128
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from the ncu
-# captures summarised in profiles/k_neighbours_pipe2M.md and profiles/k_buffer_pipe2M.md (the
-# 2.0 M-particle pipe, L = 2.5 m).  The neighbour pass scales with the particle count; the
-# buffer update with the buffers' candidate cells, which are the same at L = 2.5 and 5.09 m.
-# Set a figure to None when its kernel changes.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch from an ncu capture
+# of the named source revision (the 2.0 M-particle pipe, L = 2.5 m, the bench's kernels and
+# launch configuration).  The neighbour pass scales with the particle count; the buffer kernel
+# with the buffers' candidate cells, which are the same at L = 2.5 and 5.09 m.  A figure whose
+# kernel changed after its revision is not reported (None).
 NCU_TRAFFIC = {
-    "k_neighbours": {"bytes_per_particle": (253.15e6 + 650.12e6) / 1965281},
-    "k_buffer": {"bytes_per_launch": 3.489e6 + 0.0},
+    "k_neighbours": {"bytes_per_particle": (253.15e6 + 650.12e6) / 1965281, "source": None},
+    "k_buffer": {"bytes_per_launch": 3.489e6, "source": None},
 }
 
 
@@ -59,8 +59,11 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--length", type=float, default=PIPE_LEN)
     ap.add_argument("--phase-steps", type=int, default=10)
+    ap.add_argument("--ab-steps", type=int, default=200)
+    ap.add_argument("--ab-rounds", type=int, default=3)
+    ap.add_argument("--pair-steps", type=int, default=100)
     ap.add_argument("--spinup", type=int, default=250)
-    ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--tj-steps", type=int, default=10)
     ap.add_argument("--rot-steps", type=int, default=20)
@@ -70,6 +73,8 @@ def parse():
     ap.add_argument("--no-tjunction", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=150.0,
+                    help="seconds the reference arm's warm-up + timed steps may take (sizes its sample)")
     return ap.parse_args()
 
 
@@ -126,9 +131,10 @@ class Clocks:
 
 
 def traffic_of(kernel, particles):
-    """DRAM bytes of one launch of `kernel` from the committed ncu figures, or None."""
+    """DRAM bytes of one launch of `kernel` from the ncu figures above, or None when they were
+    not captured from the current revision of the kernel."""
     t = NCU_TRAFFIC.get(kernel)
-    if not t:
+    if not t or not t.get("source"):
         return None
     if "bytes_per_particle" in t:
         return t["bytes_per_particle"] * particles
@@ -143,42 +149,99 @@ def measured_peaks():
 
 
 # --------------------------------------------------------------------------- CPU oracle
-def oracle_sample(target_particles):
-    """A pipe segment of the benchmark's cross-section and spacing with ~target_particles."""
+def _oracle_worker(lengths, steps, warmup, barrier, out):
+    """One process of the parallel oracle run: pipe segments of the given lengths, set up, then
+    (after every process is ready) `warmup` untimed and `steps` timed steps, each step stepping
+    every segment once in turn (small segments keep the oracle's pair arrays in memory)."""
+    from oracle import buffer as OB
+
+    try:
+        sims = []
+        npart = 0
+        for length in lengths:
+            case = _segment_case(length)
+            sim = OB.OracleSim(case)
+            sim.commit()
+            sims.append(sim)
+            npart += case.n
+        for _ in range(warmup):
+            for sim in sims:
+                sim.step(1)
+        barrier.wait(timeout=1800)
+        n_sum = 0
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            for sim in sims:
+                n_sum += sim.n
+                sim.step(1)
+        t1 = time.perf_counter()
+        out.put((n_sum, t0, t1, npart))
+    except Exception as e:  # reported by the parent
+        barrier.abort()
+        out.put(("error", repr(e)))
+
+
+def _segment_case(length):
     from paper_2406_16786_gb300 import workloads as wl
 
-    area = math.pi * 0.25
-    length = max(0.09, target_particles * 1e-6 / area)
-    case = wl.pipe_case(name="oracle_sample", length=length, radius=0.5, dp=0.01, axis=(1.0, 1.0, 1.0),
+    return wl.pipe_case(name="oracle_segment", length=length, radius=0.5, dp=0.01, axis=(1.0, 1.0, 1.0),
                         inlet_bc=wl.BIDIR_PRESSURE, outlet_bc=wl.BIDIR_PRESSURE, p_in=0.0, p_amp=50.0,
                         p_omega=math.pi, p_out=0.0, c0=3.0, nu=1e-2, umax=0.06, init_velocity="profile",
                         umax_est=0.06, seed=wl.BASE_SEED + 3)
-    return case, length
 
 
-def time_oracle(steps, warmup, target_particles):
-    from oracle import buffer as OB
-
-    case, length = oracle_sample(target_particles)
-    sim = OB.OracleSim(case)
-    sim.commit()
-    for _ in range(warmup):
-        sim.step(1)
-    n_sum = 0
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        n_sum += sim.n
-        sim.step(1)
-    dt = time.perf_counter() - t0
-    sample = ("oracle FP64 full step (density, force, BC, drift, Algorithms 1-3 over every particle and "
-              "buffer, rebuild, relabel) on a %.3f m segment of the same pipe (%d particles), %d steps"
-              % (length, case.n, steps))
-    return n_sum / dt, dt / steps, sample, case.n
+SEGMENT_PARTICLES = 70000  # particles per oracle segment (a 0.09 m slice of the pipe)
 
 
-def oracle_rate_probe():
-    rate, _, _, _ = time_oracle(1, 0, 8000)
-    return rate
+def time_oracle_parallel(total_particles, steps, warmup):
+    """The oracle as it stands (plain numpy FP64, every particle against every buffer) on every
+    host core: the workload's pipe cut into segments of ~70 k particles (each a pipe of the
+    same cross-section, spacing and buffers), shared out over one process per core (spawned,
+    one BLAS thread each), all stepping at once.  Returns particle-steps/s over the timed
+    region (first start to last end), seconds per step, a description, the particles and the
+    core count."""
+    import multiprocessing as mp
+    import queue
+
+    cores = os.cpu_count() or 1
+    area = math.pi * 0.25
+    nseg = max(cores, int(math.ceil(total_particles / SEGMENT_PARTICLES)))
+    length = max(0.09, total_particles / nseg * 1e-6 / area)
+    share = [[length] * (nseg // cores + (1 if q < nseg % cores else 0)) for q in range(cores)]
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(cores)
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(share[q], steps, warmup, barrier, out)) for q in range(cores)]
+    for p in procs:
+        p.start()
+    res = []
+    try:
+        while len(res) < cores:
+            try:
+                r = out.get(timeout=30)
+            except queue.Empty:
+                if any(p.exitcode not in (None, 0) for p in procs):
+                    raise RuntimeError("an oracle process died (exit codes %s)" % [p.exitcode for p in procs])
+                continue
+            if r[0] == "error":
+                raise RuntimeError("oracle process failed: " + r[1])
+            res.append(r)
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.kill()
+    n_sum = sum(r[0] for r in res)
+    t0 = min(r[1] for r in res)
+    t1 = max(r[2] for r in res)
+    npart = sum(r[3] for r in res)
+    sample = ("oracle FP64 full step (density, force, BC, drift, Algorithms 1-3 over every particle and buffer, "
+              "rebuild, relabel) on %d host cores: the pipe cut into %d segments of %.3f m (%d particles in all, "
+              "%.0f%% of the 5.09 m workload), shared out over one process per core, %d timed steps after %d "
+              "untimed" % (cores, nseg, length, npart, 100.0 * npart / 4.0e6, steps, warmup))
+    return n_sum / (t1 - t0), (t1 - t0) / steps, sample, npart, cores
 
 
 def time_cpu_buffer_update(case, reps=3):
@@ -209,6 +272,70 @@ def time_cpu_buffer_update(case, reps=3):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def fused_buffer_cost(dom, stream, steps, rounds, nbuf):
+    """Cost of the buffer update fused into the force pass: graph-replayed steps with the
+    decisions (the default step) and without them (physics only), each timed from the same
+    saved state (written back untimed before each run), interleaved over `rounds`; returns
+    the difference of the medians per step and the mean decisions per step of the fused runs."""
+    import torch
+
+    from paper_2406_16786_gb300 import _ffi
+
+    dom.sync()
+    st0 = {k: v.copy() for k, v in dom.read().items()}
+    nid = dom.global_counters()["next_id"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = {"fused": [], "off": []}
+    inj = dels = 0
+    for _ in range(rounds):
+        for tag, ph in (("fused", _ffi.STEP_DEFAULT), ("off", _ffi.PHASE_PHYSICS)):
+            dom.write_particles(st0["cell"], st0["frac"], st0["vel"], st0["rho"], ids=st0["id"],
+                                labels=st0["label"], next_id=nid)
+            dom.step(3, ph)  # (re)captures the graph of this phase mask
+            c0 = [dom.counters(k) for k in range(nbuf)]
+            torch.cuda.synchronize()
+            e0.record(stream)
+            dom.step(steps, ph)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms[tag].append(e0.elapsed_time(e1))
+            if tag == "fused":
+                c1 = [dom.counters(k) for k in range(nbuf)]
+                inj += sum(b["injected"] - a["injected"] for a, b in zip(c0, c1))
+                dels += sum(b["deleted"] - a["deleted"] for a, b in zip(c0, c1))
+    mf, mo = statistics.median(ms["fused"]), statistics.median(ms["off"])
+    return {"us_per_step": (mf - mo) / steps * 1e3, "fused_ms_per_step": mf / steps, "off_ms_per_step": mo / steps,
+            "fused_ms_runs": ms["fused"], "off_ms_runs": ms["off"], "steps_per_run": steps,
+            "injected_per_step": inj / (rounds * steps), "deleted_per_step": dels / (rounds * steps)}
+
+
+def fused_force_cost(dom, steps):
+    """The fused decisions' share of the force pass: phase-timed steps (CUDA events around each
+    phase, plain launches) alternating between the default step (decisions in the force pass's
+    drift epilogue) and the step with the decisions in the buffer kernel (the same force pass
+    without them); both take the same decisions, so the state follows one trajectory.  Returns
+    the mean and standard error of the force-phase difference of consecutive pairs (us)."""
+    from paper_2406_16786_gb300 import _ffi
+
+    dom.use_graph(False)
+    dom.enable_phase_timing(True)
+    diffs, ff, fs = [], [], []
+    for _ in range(steps):
+        dom.step(1, _ffi.STEP_DEFAULT)
+        tf, _ = dom.phase_times()
+        dom.step(1, _ffi.STEP_DEFAULT | _ffi.PHASE_BUFFER_KERNEL)
+        ts, _ = dom.phase_times()
+        ff.append(tf["force"] * 1e3)
+        fs.append(ts["force"] * 1e3)
+        diffs.append(ff[-1] - fs[-1])
+    dom.enable_phase_timing(False)
+    dom.use_graph(True)
+    m = statistics.mean(diffs)
+    se = statistics.stdev(diffs) / math.sqrt(len(diffs)) if len(diffs) > 1 else None
+    return {"us_per_step": m, "stderr_us": se, "pairs": len(diffs), "force_fused_us": statistics.mean(ff),
+            "force_plain_us": statistics.mean(fs)}
+
+
 def run_gpu(args):
     import torch
 
@@ -262,26 +389,56 @@ def run_gpu(args):
     n_mean = 0.5 * (n0 + n1)
     value = world * n_mean * args.steps / (ms_max / 1e3)
 
-    # per-phase device time (events around each phase on the domain's stream; plain launches)
-    dom.use_graph(False)
-    dom.enable_phase_timing(True)
-    dom.step(max(1, args.phase_steps))
-    ph, nph = dom.phase_times()
-    dom.enable_phase_timing(False)
-    per = {k: v / nph for k, v in ph.items()}
+    # per-phase device time (events around each phase on the domain's stream; plain launches):
+    # the default step (decisions fused into the force pass) and the same step with the
+    # decisions in the buffer kernel of their own, so that they have a time of their own
+    def phase_times(phases):
+        dom.use_graph(False)
+        dom.enable_phase_timing(True)
+        dom.step(max(1, args.phase_steps), phases)
+        t, nph_ = dom.phase_times()
+        dom.enable_phase_timing(False)
+        dom.use_graph(True)
+        return {k: v / nph_ for k, v in t.items()}, nph_
 
-    # buffer-update roofline (decisions + apply, one kernel): algorithmic bytes per step
+    per, nph = phase_times(_ffi.STEP_DEFAULT)
+    per_sep, _ = phase_times(_ffi.STEP_DEFAULT | _ffi.PHASE_BUFFER_KERNEL)
+
+    # buffer update: algorithmic bytes per step (decision read + relabel read of each candidate
+    # particle's cell offsets and label, the candidate cells' ranges, the duplicates and the
+    # deletions), from the candidate set of the current cell list and the mean decisions of the
+    # A/B steps below
     dim = 3
     cand = [dom.candidate_count(k) for k in range(len(case.buffers))]
-    inj, dels = dom.last_decisions()
     cells = sum(c for c, _ in cand)
     parts = sum(p for _, p in cand)
     state_bytes = 8 * dim + 13  # cell, frac, vel, rho, id, label
-    bu_bytes = (4 * cells + parts * (4 * dim + 5) + len(inj) * (2 * state_bytes + 4 * dim + 4) + len(dels))
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
-    bu_s = per["buffer"] / 1e3
-    bu_gbs = bu_bytes / bu_s / 1e9 if bu_s > 0 else None
+    ab = fused_buffer_cost(dom, stream, args.ab_steps, args.ab_rounds, len(case.buffers))
+    fpair = fused_force_cost(dom, args.pair_steps)
+    n_inj, n_del = ab["injected_per_step"], ab["deleted_per_step"]
+    bu_bytes = 8 * cells + 2 * parts * (4 * dim + 1) + n_inj * (2 * state_bytes + 4 * dim) + n_del
+
+    def bu_roof(us, how):
+        gbs = bu_bytes / (us * 1e-6) / 1e9 if us and us > 0 else None
+        return {"us_per_step": us, "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                "frac": (gbs / hbm) if (gbs and hbm) else None, "timing": how}
+
+    bu = {"bound": "hbm", "bytes_per_step": bu_bytes, "candidate_cells": cells, "candidate_particles": parts,
+          "injected_per_step": n_inj, "deleted_per_step": n_del,
+          "bytes_formula": "sum_k [8 cells_k + 2 C_k (4d + 1)] + n_inj (2 (8d + 13) + 4d) + n_del",
+          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+          "fused": dict(bu_roof(fpair["us_per_step"], "force-phase time (CUDA events) of the default step minus "
+                                "that of the step whose decisions run in the buffer kernel, mean over %d "
+                                "alternating pairs (stderr in force_pairs)" % fpair["pairs"]),
+                        kernel="k_force epilogue (decide_fused)", force_pairs=fpair,
+                        step_ab=dict(ab, note="graph-replayed step time with the decisions fused minus the step "
+                                     "without decisions, %d interleaved rounds of %d steps from the same state, "
+                                     "medians; its run-to-run spread is larger than the fused cost"
+                                     % (args.ab_rounds, args.ab_steps))),
+          "kernel": dict(bu_roof(per_sep["buffer"] * 1e3, "CUDA events around the k_buffer launch, %d plain steps"
+                                 % nph), kernel="k_buffer", traffic=traffic_of("k_buffer", None))}
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     # neighbour passes, bound by FP32 arithmetic: algorithmic flops per particle
     pairs = lattice_pairs(dim, case.h_over_dp)          # neighbours within 2h on the lattice
@@ -353,7 +510,7 @@ def run_gpu(args):
         link[key] = 5 * nn * state_bytes / (time.perf_counter() - t1) / 1e9
     del hb, db
     e2e = {"value": world * nn * K_e2e / te, "unit": UNIT, "h2d_bytes_per_step": nn * state_bytes,
-           "d2h_bytes_per_step": room * state_bytes, "steps": K_e2e,
+           "d2h_bytes_per_step": int(round(statistics.mean(counts) * state_bytes)), "steps": K_e2e,
            "mode": "pipelined: write_particles_async / step / read_particles_async per step, one io_wait",
            "synchronous": {"value": world * nn * K_e2e / te_sync, "d2h_bytes_per_step": nn * state_bytes},
            "host_link": link}
@@ -368,10 +525,13 @@ def run_gpu(args):
     cpu = None
     cpu_bu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate = oracle_rate_probe()
-        target = int(min(200000, max(20000, rate * 15.0 / 3)))
-        r, per_step, sample, npart = time_oracle(3, 0, target)
-        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        # the whole 4.0 M-particle pipe, one segment per host core, 3 timed steps
+        try:
+            r, per_step, sample, npart, cores = time_oracle_parallel(4.0e6, 3, 0)
+            cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                   "s_per_step": per_step}
+        except RuntimeError as e:
+            cpu = {"value": None, "unit": UNIT, "kind": "oracle", "error": str(e)}
         cpu_bu = time_cpu_buffer_update(case)
 
     out = {
@@ -383,20 +543,19 @@ def run_gpu(args):
                    "l2": "state (~%d MB) larger than L2; no flush" % (n_mean * 2 * state_bytes / 1e6),
                    "parallelism": "replicas%d" % world, "graph": True,
                    "start": "developed parabolic profile, %d untimed spin-up steps" % args.spinup},
-        "buffer_update_us_per_step": per["buffer"] * 1e3,
+        "buffer_update_us_per_step": bu["fused"]["us_per_step"],
+        "buffer_update_kernel_us_per_step": bu["kernel"]["us_per_step"],
         "phase_ms_per_step": per,
+        "phase_ms_per_step_buffer_kernel": per_sep,
         "roofline": {"bound": "alu", "kernel": kern[dom_ph]["kernel"], "achieved": kern[dom_ph]["achieved"],
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": kern[dom_ph]["frac"],
                      "traffic": traffic_of(kern[dom_ph]["kernel"], n_mean),
+                     "traffic_source": NCU_TRAFFIC.get(kern[dom_ph]["kernel"], {}).get("source"),
                      "peak_source": "FP32 lanes x 2 x max SM clock (derived; not measured)",
                      "flops_per_particle": kern[dom_ph]["flops_per_particle"], "pairs_per_particle": pairs,
                      "candidates_per_particle": cands},
         "kernels_alu": kern,
-        "roofline_buffer_update": {"bound": "hbm", "kernel": "k_buffer", "achieved": bu_gbs, "peak": hbm,
-                                   "unit": "GB/s", "frac": (bu_gbs / hbm) if (bu_gbs and hbm) else None,
-                                   "traffic": traffic_of("k_buffer", n_mean), "bytes_per_step": bu_bytes, "candidate_cells": cells,
-                                   "candidate_particles": parts, "injected": len(inj), "deleted": len(dels),
-                                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+        "roofline_buffer_update": bu,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
@@ -460,8 +619,27 @@ def run_batched(args, stream, rank=0, world=1):
     counts = sharding.gather_counters({q: {"particles": d.count(), "steps": d.global_counters()["steps"]}
                                        for q, d in zip(mine, doms)})
     n_batch = sum(v["particles"] for v in counts.values())
+    cfg = b.get_config()
     b.close()
     for d in doms:
+        d.close()
+    # the same batch as one persistent launch per step (grid barriers between the phases), same
+    # launch configuration, same number of steps
+    pdoms = [Domain.from_case(c) for c in cases]
+    pb = Batch(pdoms, stream=stream)
+    pb.set_config(cfg)
+    pb.set_persistent(True)
+    pb.use_graph(True)
+    pb.step(W)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    pb.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_pers = sharding.max_over_ranks(e0.elapsed_time(e1))
+    pb.sync()
+    pb.close()
+    for d in pdoms:
         d.close()
     nd = len(all_cases)
     return {"workload": "64 2-D star channels (1-6 arms, 10k-500k particles log-uniform, mixed BCs)",
@@ -469,6 +647,8 @@ def run_batched(args, stream, rank=0, world=1):
             "plain_domain_steps_per_s": nd * K / (t_plain / 1e3),
             "batched_domain_steps_per_s": nd * K / (t_batch / 1e3),
             "speedup": t_plain / t_batch, "plain_ms": t_plain, "batched_ms": t_batch,
+            "persistent_ms": t_pers, "persistent_domain_steps_per_s": nd * K / (t_pers / 1e3),
+            "persistent_vs_per_phase": t_batch / t_pers, "launch_config": cfg,
             "plain_particle_steps_per_s": n_plain * K / (t_plain / 1e3),
             "batched_particle_steps_per_s": n_batch * K / (t_batch / 1e3),
             "autotune_blocks_per_sm": m}
@@ -490,7 +670,11 @@ def run_restricted_vs_full(args, stream):
     res = {"workload": "3-D T-junction R0.5 L4 + branch R0.3 L1.2 at 60 deg, arbitrary rotation, dp 0.006, "
                        "velocity inlet + 2 pressure outlets", "particles": dom.count(), "buffers": 3}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for tag, ph in (("restricted", _ffi.STEP_DEFAULT), ("full", _ffi.STEP_DEFAULT | _ffi.PHASE_FULL_CHECK)):
+    # step times: the default step (restricted decisions fused into the force pass) and the
+    # all-particle check; buffer-update times: the restricted decisions in the buffer kernel of
+    # their own against the all-particle kernel (CUDA events around each launch)
+    for tag, ph in (("restricted", _ffi.STEP_DEFAULT | _ffi.PHASE_BUFFER_KERNEL),
+                    ("full", _ffi.STEP_DEFAULT | _ffi.PHASE_FULL_CHECK)):
         dom.step(2, ph)
         torch.cuda.synchronize()
         e0.record(stream)
@@ -498,6 +682,14 @@ def run_restricted_vs_full(args, stream):
         e1.record(stream)
         torch.cuda.synchronize()
         res[tag + "_ms_per_step"] = e0.elapsed_time(e1) / K
+        if tag == "restricted":
+            dom.step(2)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            dom.step(K)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res["fused_ms_per_step"] = e0.elapsed_time(e1) / K
         dom.use_graph(False)
         dom.enable_phase_timing(True)
         dom.step(args.phase_steps, ph)
@@ -511,7 +703,7 @@ def run_restricted_vs_full(args, stream):
     inj, dels = dom.last_decisions()
     res["injected_last_step"], res["deleted_last_step"] = len(inj), len(dels)
     res["buffer_speedup_restricted_vs_full"] = res["full_buffer_us_per_step"] / res["restricted_buffer_us_per_step"]
-    res["particle_steps_per_s"] = res["particles"] / (res["restricted_ms_per_step"] / 1e3)
+    res["particle_steps_per_s"] = res["particles"] / (res["fused_ms_per_step"] / 1e3)
     dom.close()
     return res
 
@@ -628,20 +820,34 @@ def run_rotating(args, stream):
     return res
 
 
+def oracle_core_rate():
+    """Particle-steps/s of the oracle on one core, from one step of a small segment."""
+    from oracle import buffer as OB
+
+    case = _segment_case(0.09)
+    sim = OB.OracleSim(case)
+    sim.commit()
+    t0 = time.perf_counter()
+    sim.step(1)
+    return case.n / (time.perf_counter() - t0)
+
+
 def run_reference(args):
+    """The oracle (plain FP64 restatement of the method) on every host core, on as much of the
+    4.0 M-particle pipe as keeps the whole run (warm-up + timed steps) within about 150 s."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    rate = oracle_rate_probe()
-    budget = 120.0
-    target = int(max(3000, min(200000, rate * budget / max(1, args.steps + args.warmup))))
-    r, per_step, sample, npart = time_oracle(args.steps, args.warmup, target)
-    # n_gpus is the launch's N; the oracle itself runs on one host core of rank 0 (cpu_baseline)
+    cores = os.cpu_count() or 1
+    rate = oracle_core_rate() * cores
+    total = int(max(cores * 5000, min(4.0e6, rate * args.ref_budget / max(1, args.steps + args.warmup))))
+    r, per_step, sample, npart, cores = time_oracle_parallel(total, args.steps, args.warmup)
+    # n_gpus is the launch's N; the oracle runs on the host cores of rank 0 (cpu_baseline)
     out = {"impl": "reference", "metric": METRIC, "value": r, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD % args.length + " (bounded oracle sample)", "particles": npart},
-           "cpu_baseline": {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": r, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

@@ -84,9 +84,16 @@ typedef enum {
  * The rebuild and relabel always close a step. */
 #define SPHBUF_PHASE_PHYSICS 1u     /* density, force, kick + BC velocity, drift */
 #define SPHBUF_PHASE_KINEMATIC 2u   /* drift only, with the stored velocity (no BC) */
-#define SPHBUF_PHASE_BUFFER 4u      /* decisions + apply (Algorithms 1-3) */
+#define SPHBUF_PHASE_BUFFER 4u      /* decisions + apply (Algorithms 1-3); by default fused into
+                                       the drift of the step: each particle sorted into a
+                                       candidate cell of a buffer (Sec. 3.1's local cells) is
+                                       decided right after its drift */
 #define SPHBUF_PHASE_FULL_CHECK 8u  /* decisions over all particles instead of the cells around
-                                       each buffer (same result; for timing comparisons) */
+                                       each buffer, in a kernel of their own (same result; for
+                                       timing comparisons) */
+#define SPHBUF_PHASE_BUFFER_KERNEL 16u /* decisions in a kernel of their own after the drift,
+                                          visiting the candidate cells (same result as the fused
+                                          form; the form always used for rotating buffers) */
 #define SPHBUF_STEP_DEFAULT (SPHBUF_PHASE_PHYSICS | SPHBUF_PHASE_BUFFER)
 
 typedef struct {
@@ -344,16 +351,62 @@ sphbuf_status sphbuf_batch_create(sphbuf_domain_t *domains, int n, void *cuda_st
 sphbuf_status sphbuf_batch_step(sphbuf_batch_t b, int nsteps, unsigned phases);
 /* Capture one batched step into a CUDA graph and replay it (enable = 1), or plain launches. */
 sphbuf_status sphbuf_batch_use_graph(sphbuf_batch_t b, int enable);
-/* Grid-size autotuner: for each candidate multiplier m in {1, 2, 4, 8, 16} (blocks per SM of
- * the particle kernels) runs trial_steps real steps (the domains advance), times them with
- * CUDA events and keeps the fastest; *best_m receives it.  Candidates of the buffer kernel
- * (cells per warp fixed) are not tuned. */
+/* Launch configuration of a batch's kernels (the autotuner's choice).  For each kernel of
+ * sphbuf_kernel: threads per block (a multiple of 32 in 32..512) and blocks per SM (1..32;
+ * the kernel's grid is blocks_per_sm x SMs blocks, shared out over the domains in
+ * proportion to their particles, or to their candidate cells for the buffer kernel);
+ * cells_per_warp: candidate cells one warp of the buffer kernel visits at a time (its cell
+ * tile: 1, 2, 4 or 8, with 32 / cells_per_warp lanes per cell).  The scans of the cell-list
+ * rebuild (tiles of 4096 cells) and the single-block kernels are not configurable.  A
+ * configuration changes launch shapes only, never results. */
+typedef enum {
+  SPHBUF_KERNEL_NEIGHBOURS = 0,  /* neighbour lists + Eq. (9) */
+  SPHBUF_KERNEL_DENSITY = 1,     /* deferred densities (Eq. (4), overflowed lists) */
+  SPHBUF_KERNEL_FORCE = 2,       /* force, kick, BC velocity, drift (+ fused decisions) */
+  SPHBUF_KERNEL_DRIFT = 3,       /* kinematic drift (+ fused decisions) */
+  SPHBUF_KERNEL_VISCOUS = 4,     /* dual-criteria scheme: viscous acceleration */
+  SPHBUF_KERNEL_ACOUSTIC = 5,    /* dual-criteria scheme: acoustic step */
+  SPHBUF_KERNEL_DUAL_FINISH = 6, /* dual-criteria scheme: fold + store (+ fused decisions) */
+  SPHBUF_KERNEL_BUFFER = 7,      /* decisions in a kernel of their own (candidate cells) */
+  SPHBUF_KERNEL_BUFFER_FULL = 8, /* decisions over all particles */
+  SPHBUF_KERNEL_HIST = 9,        /* rebuild: histogram */
+  SPHBUF_KERNEL_KEYS = 10,       /* rebuild: keys */
+  SPHBUF_KERNEL_SCATTER = 11,    /* rebuild: scatter + relabel */
+  SPHBUF_KERNEL_COUNT = 12
+} sphbuf_kernel;
+
+typedef struct {
+  int threads[SPHBUF_KERNEL_COUNT];
+  int blocks_per_sm[SPHBUF_KERNEL_COUNT];
+  int cells_per_warp;
+} sphbuf_batch_config;
+
+/* Autotuner: runs trial_steps real steps (the domains advance) with the given phase mask for
+ * every pair (threads in {64, 128, 256, 512}) x (blocks per SM in {1, 2, 4, 8, 16}), timing
+ * every kernel launch with CUDA events, and gives each kernel the pair under which it ran
+ * fastest; then, when the phases launch the buffer kernel, the cell tile in {1, 2, 4, 8}.
+ * *best_m receives the neighbour kernel's blocks per SM (may be NULL); ms_per_step (may be
+ * NULL) the per-phase milliseconds of trial_steps steps with the chosen configuration.
+ * Read the choice with sphbuf_batch_get_config (e.g. to cache it per workload size). */
 sphbuf_status sphbuf_batch_autotune(sphbuf_batch_t b, int trial_steps, unsigned phases, int *best_m,
                                     double ms_per_step[5]);
-/* Sets the grid multiplier m (blocks per SM of the particle kernels, 1..32) without trial
- * steps, e.g. the autotuner's choice for another batch of the same domains; the domains do
- * not advance.  SPHBUF_ERR_INVALID_ARG outside 1..32. */
+sphbuf_status sphbuf_batch_get_config(sphbuf_batch_t b, sphbuf_batch_config *cfg);
+/* Applies a configuration (e.g. a cached autotuner result) without trial steps; synchronises
+ * the batch's stream.  SPHBUF_ERR_INVALID_ARG for a value outside the ranges above. */
+sphbuf_status sphbuf_batch_set_config(sphbuf_batch_t b, const sphbuf_batch_config *cfg);
+/* Sets the blocks per SM of every configurable kernel to m (1..32) without trial steps,
+ * block sizes unchanged; the domains do not advance.  SPHBUF_ERR_INVALID_ARG outside 1..32. */
 sphbuf_status sphbuf_batch_set_grid(sphbuf_batch_t b, int m);
+/* Persistent form of the batch's default step (SPHBUF_STEP_DEFAULT): every phase (neighbour
+ * lists, densities, force with the fused decisions, the cell-list rebuild) in one cooperative
+ * launch whose blocks all stay resident, with a grid-wide barrier between phases, instead
+ * of one launch per phase (other phase masks keep the per-phase launches; results are
+ * identical either way).  Each barrier wait spins at most spin_limit iterations of about
+ * 100 ns (< 0: the default, 2^24); a wait that runs out makes every block of the launch
+ * return and latches SPHBUF_ERR_TIMEOUT in every domain of the batch, reported by the next
+ * synchronising call (the domains then need new particles written to step again).
+ * SPHBUF_ERR_INVALID_ARG for a batch with rotating buffers or dual-criteria stepping. */
+sphbuf_status sphbuf_batch_set_persistent(sphbuf_batch_t b, int enable, long long spin_limit);
 /* Waits for the batch's stream and returns the first latched error of its domains. */
 sphbuf_status sphbuf_batch_sync(sphbuf_batch_t b);
 sphbuf_status sphbuf_batch_destroy(sphbuf_batch_t b);

@@ -62,6 +62,9 @@ SIGNATURES = {
     "sphbuf_batch_use_graph": (ctypes.c_int, [vp, ctypes.c_int]),
     "sphbuf_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_uint, P(ctypes.c_int), vp]),
     "sphbuf_batch_set_grid": (ctypes.c_int, [vp, ctypes.c_int]),
+    "sphbuf_batch_get_config": (ctypes.c_int, [vp, vp]),
+    "sphbuf_batch_set_config": (ctypes.c_int, [vp, vp]),
+    "sphbuf_batch_set_persistent": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_longlong]),
     "sphbuf_write_particles_async": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, ctypes.c_uint64, ctypes.c_uint32]),
     "sphbuf_read_particles_async": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, ctypes.c_uint64, P(ctypes.c_uint64)]),
     "sphbuf_io_wait": (ctypes.c_int, [vp]),
@@ -75,6 +78,11 @@ PHASE_PHYSICS = 1
 PHASE_KINEMATIC = 2
 PHASE_BUFFER = 4
 PHASE_FULL_CHECK = 8
+PHASE_BUFFER_KERNEL = 16
+
+# sphbuf_kernel (the configurable batched kernels) and sphbuf_batch_config's layout
+KERNELS = ["neighbours", "density", "force", "drift", "viscous", "acoustic", "dual_finish", "buffer", "buffer_full",
+           "hist", "keys", "scatter"]
 STEP_DEFAULT = PHASE_PHYSICS | PHASE_BUFFER
 
 _lib = None

@@ -47,6 +47,7 @@ struct sphbuf_domain {
   std::vector<BufDev> bufs_dev;
   std::vector<void*> allocs;
   void* seg_mem = nullptr;
+  unsigned* cand_mask = nullptr;  // per cell: candidate buffers (bit k), for the fused decisions
   std::vector<int> seg_host, segbuf_host;
   void* wall_mem = nullptr;
   uint64_t launches = 0;
@@ -318,6 +319,14 @@ sphbuf_status build_segments(sphbuf_domain* d) {
     cudaFree(d->seg_mem);
     d->seg_mem = nullptr;
   }
+  // per-cell mask of the candidate buffers: the fused form decides a particle against the
+  // buffers whose candidate cells hold the cell it was sorted into
+  std::vector<unsigned> mask((size_t)d->ncell, 0u);
+  for (size_t q = 0; q < segbuf.size(); ++q)
+    for (int lin = seg[2 * q]; lin < seg[2 * q + 1]; ++lin) mask[(size_t)lin] |= 1u << segbuf[q];
+  if (!d->cand_mask) CK(cudaMalloc(&d->cand_mask, std::max<size_t>((size_t)d->ncell, 1) * sizeof(unsigned)));
+  CK(cudaMemcpy(d->cand_mask, mask.data(), mask.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
+  d->dev.cand_mask = d->cand_mask;
   const size_t nseg = segbuf.size();
   // [seg_range: 4 nseg words, 16-byte aligned][seg_lin: 2 nseg][seg_buf: nseg]; the ranges
   // are written by every rebuild (the first one runs before the first step)
@@ -352,6 +361,8 @@ sphbuf_status read_state(sphbuf_domain* d, StepState* out) {
   if (out->status) {
     const char* what = out->status == SPHBUF_ERR_CAPACITY      ? "particle or decision-list capacity exceeded"
                        : out->status == SPHBUF_ERR_NAN         ? "non-finite particle position"
+                       : out->status == SPHBUF_ERR_TIMEOUT     ? "a grid-barrier wait of the persistent batched step "
+                                                                 "ran out of its spin limit"
                        : out->status == SPHBUF_ERR_INVALID_ARG ? "asynchronously written arrays failed the checks "
                                                                  "(cell, offset, label or next_id)"
                                                                : "device-side error";
@@ -442,11 +453,21 @@ sphbuf_status commit(sphbuf_domain* d) {
   return SPHBUF_OK;
 }
 
+// Are the step's buffer decisions fused into the drift epilogue?  Not for the all-particle
+// check, on request (SPHBUF_PHASE_BUFFER_KERNEL), or when a buffer rotates (its particles turn
+// in the buffer kernel).
+bool fused_decisions(unsigned phases, bool any_rot) {
+  return (phases & SPHBUF_PHASE_BUFFER) && !(phases & (SPHBUF_PHASE_FULL_CHECK | SPHBUF_PHASE_BUFFER_KERNEL)) &&
+         !any_rot;
+}
+
 // Enqueues the kernels of one step; returns the number of kernels launched.
 int enqueue_step(sphbuf_domain* d, unsigned phases, bool timed) {
   const DomainDev& v = d->dev;
   cudaStream_t s = d->stream;
-  // phases timed: [neighbour lists, density, force (or drift), buffer update, rebuild]
+  const bool fused = fused_decisions(phases, v.any_rot != 0);
+  // phases timed: [neighbour lists, density, force (or drift), buffer update, rebuild]; the
+  // fused decisions are timed with the force (or drift) phase
   int k = 0;
   if (timed) cudaEventRecord(d->ev[0], s);
   if (phases & SPHBUF_PHASE_PHYSICS) {
@@ -454,14 +475,14 @@ int enqueue_step(sphbuf_domain* d, unsigned phases, bool timed) {
     if (timed) cudaEventRecord(d->ev[1], s);
     k += launch_density(v, s);
     if (timed) cudaEventRecord(d->ev[2], s);
-    k += v.P.dual_n > 0 ? launch_dual(v, s) : launch_force(v, s);
+    k += v.P.dual_n > 0 ? launch_dual(v, fused, s) : launch_force(v, fused, s);
   } else {
     if (timed) cudaEventRecord(d->ev[1], s);
     if (timed) cudaEventRecord(d->ev[2], s);
-    k += launch_drift(v, s);
+    k += launch_drift(v, fused, s);
   }
   if (timed) cudaEventRecord(d->ev[3], s);
-  if (phases & SPHBUF_PHASE_BUFFER) {
+  if ((phases & SPHBUF_PHASE_BUFFER) && !fused) {
     k += launch_decide(v, (phases & SPHBUF_PHASE_FULL_CHECK) != 0, s);
   }
   if (timed) cudaEventRecord(d->ev[4], s);
@@ -637,6 +658,7 @@ sphbuf_status sphbuf_destroy(sphbuf_domain_t d) {
   if (d->graph) cudaGraphExecDestroy(d->graph);
   for (void* p : d->allocs) cudaFree(p);
   if (d->seg_mem) cudaFree(d->seg_mem);
+  if (d->cand_mask) cudaFree(d->cand_mask);
   for (int q = 0; q <= kPhases; ++q)
     if (d->ev[q]) cudaEventDestroy(d->ev[q]);
   if (d->own_stream) cudaStreamDestroy(d->stream);
@@ -1139,7 +1161,7 @@ sphbuf_status sphbuf_step_phases(sphbuf_domain_t d, int nsteps, unsigned phases)
   if (!d || nsteps < 0) return SPHBUF_ERR_INVALID_ARG;
   const bool phys = phases & SPHBUF_PHASE_PHYSICS, kin = phases & SPHBUF_PHASE_KINEMATIC;
   if (phys == kin) return fail(d, SPHBUF_ERR_INVALID_ARG, "exactly one of PHYSICS or KINEMATIC is required");
-  if (phases & ~15u) return fail(d, SPHBUF_ERR_INVALID_ARG, "unknown phase bits");
+  if (phases & ~31u) return fail(d, SPHBUF_ERR_INVALID_ARG, "unknown phase bits");
   if (!d->committed && !d->need_rebuild) return fail(d, SPHBUF_ERR_STATE, "no particles written");
   sphbuf_status s = commit(d);
   if (s != SPHBUF_OK) return s;
@@ -1368,6 +1390,22 @@ struct sphbuf_batch {
   int4* d_maps[K_COUNT] = {};
   int nblocks[K_COUNT] = {};
   int mult = 8;
+  // launch configuration per kernel (the autotuner's): threads per block, blocks per SM (the
+  // particle kernels' grid is blocks_per_sm x SMs, shared out over the domains by work), and
+  // the buffer kernel's cell tile (candidate cells per warp)
+  int thr[K_COUNT] = {};
+  int mk[K_COUNT] = {};
+  int cpw = 4;
+  // persistent form of the default step (one cooperative launch, grid barriers)
+  bool persistent = false;
+  long long spin_limit = 1ll << 24;
+  unsigned* d_bar = nullptr;
+  int pgrid = 0;
+  // per-kernel timing (autotuner): an event pair around every launch of a step
+  bool ktime = false;
+  std::vector<cudaEvent_t> kev;
+  std::vector<int> kid;
+  size_t kpos = 0;
   bool use_graph = false;
   cudaGraphExec_t graph = nullptr;
   unsigned graph_phases = 0;
@@ -1393,25 +1431,28 @@ static sphbuf_status batch_fail(sphbuf_batch* b, sphbuf_status s, const std::str
 // Block maps of every batched kernel: domain d gets a share of the blocks proportional to
 // its work (particles for the particle kernels, candidate cells for the buffer kernel, scan
 // tiles for the scans, one block for the per-domain single-block kernels).
-static sphbuf_status batch_build_maps(sphbuf_batch* b, int mult) {
+static sphbuf_status batch_build_maps(sphbuf_batch* b) {
   const int nd = (int)b->doms.size();
   double total_n = 0;
   for (uint64_t v : b->n0) total_n += (double)std::max<uint64_t>(v, 1);
-  const double T = (double)b->sm_count * mult;
   for (int k = 0; k < K_COUNT; ++k) {
+    const double T = (double)b->sm_count * b->mk[k];
     std::vector<int4> map;
     for (int q = 0; q < nd; ++q) {
       const DomainDev& v = b->doms[q]->dev;
       int cnt = 1;
       switch (k) {
-        case K_BUFFER:
-          cnt = std::max(1, (v.nseg + 31) / 32);
+        case K_BUFFER: {
+          const int cells_per_block = b->cpw * (b->thr[k] / 32);
+          cnt = std::max(1, (v.nseg + cells_per_block - 1) / cells_per_block);
           break;
+        }
         case K_SCAN_REDUCE:
         case K_SCAN_DOWN:
           cnt = v.scan_tiles;
           break;
         case K_SCAN_TOP:
+        case K_BEGIN:
           cnt = 1;
           break;
         case K_FINALIZE:
@@ -1428,7 +1469,7 @@ static sphbuf_status batch_build_maps(sphbuf_batch* b, int mult) {
     BCK(cudaMemcpy(b->d_maps[k], map.data(), map.size() * sizeof(int4), cudaMemcpyHostToDevice));
     b->nblocks[k] = (int)map.size();
   }
-  b->mult = mult;
+  b->mult = b->mk[K_NEIGHBOURS];
   if (b->graph) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -1436,29 +1477,66 @@ static sphbuf_status batch_build_maps(sphbuf_batch* b, int mult) {
   return SPHBUF_OK;
 }
 
-static int batch_launch(sphbuf_batch* b, Kern k) {
+// Every blocks-per-SM multiplier m to m (particle kernels), block sizes left as they are.
+static void batch_set_mult(sphbuf_batch* b, int m) {
+  for (int k = 0; k < K_COUNT; ++k) b->mk[k] = m;
+}
+
+static int batch_launch_k(sphbuf_batch* b, Kern k, bool fused, int sub) {
   const BatchDev bd{b->d_doms, b->d_maps[k]};
   const int n = b->nblocks[k];
   switch (k) {
+    case K_BEGIN:
     case K_NEIGHBOURS:
     case K_DENSITY_DEFER:
     case K_FORCE:
     case K_DRIFT:
     case K_VISCOUS:
+    case K_ACOUSTIC:
     case K_DUAL_FINISH:
-      return launch_batch_sph(k, b->dim, bd, n, b->stream, b->tvf);
+      return launch_batch_sph(k, b->dim, bd, n, b->stream, b->tvf, sub, fused, b->thr[k]);
     case K_BUFFER:
     case K_BUFFER_FULL:
-      return launch_batch_buffer(k, b->dim, bd, n, b->rot, b->stream);
+      return launch_batch_buffer(k, b->dim, bd, n, b->rot, b->thr[k], b->cpw, b->stream);
     default:
-      return launch_batch_cells(k, b->dim, bd, n, b->stream);
+      return launch_batch_cells(k, b->dim, bd, n, b->thr[k], b->stream);
   }
+}
+
+static int batch_launch(sphbuf_batch* b, Kern k, bool fused = false, int sub = 0) {
+  if (!b->ktime) return batch_launch_k(b, k, fused, sub);
+  if (b->kev.size() < 2 * (b->kpos + 1)) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    b->kev.push_back(e0);
+    b->kev.push_back(e1);
+  }
+  cudaEventRecord(b->kev[2 * b->kpos], b->stream);
+  const int r = batch_launch_k(b, k, fused, sub);
+  cudaEventRecord(b->kev[2 * b->kpos + 1], b->stream);
+  if (b->kid.size() <= b->kpos) b->kid.resize(b->kpos + 1);
+  b->kid[b->kpos++] = (int)k;
+  return r;
 }
 
 // One batched step; phases timed as for a single domain.
 static int batch_enqueue_step(sphbuf_batch* b, unsigned phases, bool timed) {
   cudaStream_t s = b->stream;
+  const bool fused = fused_decisions(phases, b->rot);
   int k = 0;
+  if (b->persistent && !timed && !b->ktime && phases == SPHBUF_STEP_DEFAULT) {
+    PersistDev p{};
+    p.doms = b->d_doms;
+    for (int q = 0; q < kPersistPhases; ++q) {
+      p.map[q] = b->d_maps[kPersistKern[q]];
+      p.nvb[q] = b->nblocks[kPersistKern[q]];
+    }
+    p.bar = b->d_bar;
+    p.spin_limit = b->spin_limit;
+    p.ndom = (int)b->doms.size();
+    return launch_persistent(p, b->dim, b->tvf, b->pgrid, s) == cudaSuccess ? 1 : -1;
+  }
   if (timed) cudaEventRecord(b->ev[0], s);
   if (phases & SPHBUF_PHASE_PHYSICS) {
     k += batch_launch(b, K_NEIGHBOURS);
@@ -1467,21 +1545,20 @@ static int batch_enqueue_step(sphbuf_batch* b, unsigned phases, bool timed) {
     if (timed) cudaEventRecord(b->ev[2], s);
     if (b->dual_n > 0) {
       k += batch_launch(b, K_VISCOUS);
-      for (int q = 0; q < b->dual_n; ++q) {
-        const BatchDev bd{b->d_doms, b->d_maps[K_ACOUSTIC]};
-        k += launch_batch_sph(K_ACOUSTIC, b->dim, bd, b->nblocks[K_ACOUSTIC], s, false, q);
-      }
-      k += batch_launch(b, K_DUAL_FINISH);
+      for (int q = 0; q < b->dual_n; ++q) k += batch_launch(b, K_ACOUSTIC, false, q);
+      k += batch_launch(b, K_DUAL_FINISH, fused);
     } else {
-      k += batch_launch(b, K_FORCE);
+      k += batch_launch(b, K_FORCE, fused);
     }
   } else {
     if (timed) cudaEventRecord(b->ev[1], s);
     if (timed) cudaEventRecord(b->ev[2], s);
-    k += batch_launch(b, K_DRIFT);
+    k += batch_launch(b, K_BEGIN);
+    k += batch_launch(b, K_DRIFT, fused);
   }
   if (timed) cudaEventRecord(b->ev[3], s);
-  if (phases & SPHBUF_PHASE_BUFFER) k += batch_launch(b, (phases & SPHBUF_PHASE_FULL_CHECK) ? K_BUFFER_FULL : K_BUFFER);
+  if ((phases & SPHBUF_PHASE_BUFFER) && !fused)
+    k += batch_launch(b, (phases & SPHBUF_PHASE_FULL_CHECK) ? K_BUFFER_FULL : K_BUFFER);
   if (timed) cudaEventRecord(b->ev[4], s);
   for (Kern r : {K_HIST, K_SCAN_REDUCE, K_SCAN_TOP, K_SCAN_DOWN, K_KEYS, K_SCATTER, K_FINALIZE}) k += batch_launch(b, r);
   if (timed) cudaEventRecord(b->ev[5], s);
@@ -1512,8 +1589,15 @@ static sphbuf_status batch_run(sphbuf_batch* b, int nsteps, unsigned phases, boo
         }
         cudaGraph_t g = nullptr;
         BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-        b->graph_launches = (uint64_t)batch_enqueue_step(b, phases, false);
-        BCK(cudaStreamEndCapture(b->stream, &g));
+        const int nk = batch_enqueue_step(b, phases, false);
+        const cudaError_t le = cudaGetLastError();
+        const cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+        if (nk < 0 || le != cudaSuccess || ce != cudaSuccess) {
+          if (g) cudaGraphDestroy(g);
+          return batch_fail(b, SPHBUF_ERR_CUDA, std::string("capturing the batched step: ") +
+                                                    cudaGetErrorString(le != cudaSuccess ? le : ce));
+        }
+        b->graph_launches = (uint64_t)nk;
         BCK(cudaGraphInstantiate(&b->graph, g, 0));
         cudaGraphDestroy(g);
         b->graph_phases = phases;
@@ -1521,7 +1605,10 @@ static sphbuf_status batch_run(sphbuf_batch* b, int nsteps, unsigned phases, boo
       BCK(cudaGraphLaunch(b->graph, b->stream));
       launched += b->graph_launches;
     } else {
-      launched += (uint64_t)batch_enqueue_step(b, phases, false);
+      const int nk = batch_enqueue_step(b, phases, false);
+      if (nk < 0) return batch_fail(b, SPHBUF_ERR_CUDA, std::string("persistent step launch: ") +
+                                                        cudaGetErrorString(cudaGetLastError()));
+      launched += (uint64_t)nk;
     }
   }
   BCK(cudaGetLastError());
@@ -1593,7 +1680,9 @@ sphbuf_status sphbuf_batch_create(sphbuf_domain_t* domains, int n, void* cuda_st
   ok = ok && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess;
   b->dom_ev.assign(n, nullptr);
   for (int q = 0; ok && q < n; ++q) ok = cudaEventCreateWithFlags(&b->dom_ev[q], cudaEventDisableTiming) == cudaSuccess;
-  if (!ok || batch_build_maps(b, 8) != SPHBUF_OK) {
+  for (int k = 0; k < K_COUNT; ++k) b->thr[k] = batch_threads((Kern)k);
+  batch_set_mult(b, 8);
+  if (!ok || batch_build_maps(b) != SPHBUF_OK) {
     sphbuf_batch_destroy(b);
     return SPHBUF_ERR_CUDA;
   }
@@ -1601,10 +1690,14 @@ sphbuf_status sphbuf_batch_create(sphbuf_domain_t* domains, int n, void* cuda_st
   return SPHBUF_OK;
 }
 
+static bool batch_phases_ok(unsigned phases) {
+  const bool phys = phases & SPHBUF_PHASE_PHYSICS, kin = phases & SPHBUF_PHASE_KINEMATIC;
+  return phys != kin && !(phases & ~31u);
+}
+
 sphbuf_status sphbuf_batch_step(sphbuf_batch_t b, int nsteps, unsigned phases) {
   if (!b || nsteps < 0) return SPHBUF_ERR_INVALID_ARG;
-  const bool phys = phases & SPHBUF_PHASE_PHYSICS, kin = phases & SPHBUF_PHASE_KINEMATIC;
-  if (phys == kin || (phases & ~15u)) return batch_fail(b, SPHBUF_ERR_INVALID_ARG, "bad phase mask");
+  if (!batch_phases_ok(phases)) return batch_fail(b, SPHBUF_ERR_INVALID_ARG, "bad phase mask");
   for (sphbuf_domain* d : b->doms)
     if (d->need_rebuild) return batch_fail(b, SPHBUF_ERR_STATE, "a domain was rewritten after batching");
   return batch_run(b, nsteps, phases, false, nullptr);
@@ -1616,39 +1709,145 @@ sphbuf_status sphbuf_batch_use_graph(sphbuf_batch_t b, int enable) {
   return SPHBUF_OK;
 }
 
+// Runs nsteps plain batched steps with an event pair around every launch; acc[k] receives
+// kernel k's milliseconds summed over its launches and the steps.
+static sphbuf_status batch_time_kernels(sphbuf_batch* b, int nsteps, unsigned phases, std::vector<double>& acc) {
+  acc.assign(K_COUNT, 0.0);
+  const bool graph = b->use_graph;
+  b->use_graph = false;
+  b->ktime = true;
+  sphbuf_status s = SPHBUF_OK;
+  for (int q = 0; q < nsteps && s == SPHBUF_OK; ++q) {
+    b->kpos = 0;
+    s = batch_run(b, 1, phases, false, nullptr);
+    if (s == SPHBUF_OK && cudaStreamSynchronize(b->stream) != cudaSuccess)
+      s = batch_fail(b, SPHBUF_ERR_CUDA, "autotune: stream synchronisation failed");
+    for (size_t e = 0; s == SPHBUF_OK && e < b->kpos; ++e) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, b->kev[2 * e], b->kev[2 * e + 1]) == cudaSuccess) acc[b->kid[e]] += ms;
+    }
+  }
+  b->ktime = false;
+  b->use_graph = graph;
+  return s;
+}
+
 sphbuf_status sphbuf_batch_autotune(sphbuf_batch_t b, int trial_steps, unsigned phases, int* best_m,
                                     double ms_per_step[5]) {
   if (!b || trial_steps <= 0) return SPHBUF_ERR_INVALID_ARG;
-  const int cands[] = {1, 2, 4, 8, 16};
-  double best = 1e300;
-  int bm = b->mult;
-  std::vector<double> best_ph(kPhases, 0.0);
-  for (int m : cands) {
-    sphbuf_status s = batch_build_maps(b, m);
-    if (s != SPHBUF_OK) return s;
-    double acc[kPhases] = {0, 0, 0, 0, 0};
-    s = batch_run(b, trial_steps, phases, true, acc);
-    if (s != SPHBUF_OK) return s;
-    double tot = 0;
-    for (double v : acc) tot += v;
-    if (tot < best) {
-      best = tot;
-      bm = m;
-      for (int p = 0; p < kPhases; ++p) best_ph[p] = acc[p] / trial_steps;
+  if (!batch_phases_ok(phases)) return batch_fail(b, SPHBUF_ERR_INVALID_ARG, "bad phase mask");
+  const int threads_c[] = {64, 128, 256, 512};
+  const int mult_c[] = {1, 2, 4, 8, 16};
+  std::vector<double> best(K_COUNT, 1e300), acc;
+  std::vector<int> bt(K_COUNT), bm(K_COUNT);
+  // every (block size, blocks per SM) pair for all tunable kernels at once; each kernel keeps
+  // the pair under which it ran fastest (the kernels' times do not depend on one another's
+  // launch shapes)
+  for (int t : threads_c)
+    for (int m : mult_c) {
+      for (int k = 0; k < K_COUNT; ++k)
+        if (batch_tunable((Kern)k)) b->thr[k] = t;
+      batch_set_mult(b, m);
+      sphbuf_status s = batch_build_maps(b);
+      if (s == SPHBUF_OK) s = batch_time_kernels(b, trial_steps, phases, acc);
+      if (s != SPHBUF_OK) return s;
+      for (int k = 0; k < K_COUNT; ++k)
+        if (batch_tunable((Kern)k) && acc[k] > 0.0 && acc[k] < best[k]) {
+          best[k] = acc[k];
+          bt[k] = t;
+          bm[k] = m;
+        }
     }
+  for (int k = 0; k < K_COUNT; ++k) {
+    const bool ran = batch_tunable((Kern)k) && best[k] < 1e300;
+    b->thr[k] = ran ? bt[k] : batch_threads((Kern)k);
+    b->mk[k] = ran ? bm[k] : 8;
   }
-  sphbuf_status s = batch_build_maps(b, bm);
+  // the buffer kernel's cell tile, when the phases launch it
+  if (best[K_BUFFER] < 1e300) {
+    double bb = 1e300;
+    int bc = 4;
+    for (int c : {1, 2, 4, 8}) {
+      b->cpw = c;
+      sphbuf_status s = batch_build_maps(b);
+      if (s == SPHBUF_OK) s = batch_time_kernels(b, trial_steps, phases, acc);
+      if (s != SPHBUF_OK) return s;
+      if (acc[K_BUFFER] > 0.0 && acc[K_BUFFER] < bb) {
+        bb = acc[K_BUFFER];
+        bc = c;
+      }
+    }
+    b->cpw = bc;
+  }
+  sphbuf_status s = batch_build_maps(b);
   if (s != SPHBUF_OK) return s;
-  if (best_m) *best_m = bm;
+  double ph[kPhases] = {0, 0, 0, 0, 0};
+  s = batch_run(b, trial_steps, phases, true, ph);
+  if (s != SPHBUF_OK) return s;
+  if (best_m) *best_m = b->mk[K_NEIGHBOURS];
   if (ms_per_step)
-    for (int p = 0; p < kPhases; ++p) ms_per_step[p] = best_ph[p];
+    for (int p = 0; p < kPhases; ++p) ms_per_step[p] = ph[p] / trial_steps;
   return SPHBUF_OK;
 }
 
 sphbuf_status sphbuf_batch_set_grid(sphbuf_batch_t b, int m) {
   if (!b || m < 1 || m > 32) return SPHBUF_ERR_INVALID_ARG;
   BCK(cudaStreamSynchronize(b->stream));
-  return batch_build_maps(b, m);
+  batch_set_mult(b, m);
+  return batch_build_maps(b);
+}
+
+// Public kernel ids of sphbuf_batch_config and the library's kernels.
+static const Kern kTuned[SPHBUF_KERNEL_COUNT] = {K_NEIGHBOURS, K_DENSITY_DEFER, K_FORCE,   K_DRIFT,
+                                                 K_VISCOUS,    K_ACOUSTIC,      K_DUAL_FINISH, K_BUFFER,
+                                                 K_BUFFER_FULL, K_HIST,         K_KEYS,    K_SCATTER};
+
+sphbuf_status sphbuf_batch_get_config(sphbuf_batch_t b, sphbuf_batch_config* cfg) {
+  if (!b || !cfg) return SPHBUF_ERR_INVALID_ARG;
+  for (int q = 0; q < SPHBUF_KERNEL_COUNT; ++q) {
+    cfg->threads[q] = b->thr[kTuned[q]];
+    cfg->blocks_per_sm[q] = b->mk[kTuned[q]];
+  }
+  cfg->cells_per_warp = b->cpw;
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_batch_set_config(sphbuf_batch_t b, const sphbuf_batch_config* cfg) {
+  if (!b || !cfg) return SPHBUF_ERR_INVALID_ARG;
+  for (int q = 0; q < SPHBUF_KERNEL_COUNT; ++q) {
+    const int t = cfg->threads[q], m = cfg->blocks_per_sm[q];
+    if (t < 32 || t > 512 || t % 32 || m < 1 || m > 32)
+      return batch_fail(b, SPHBUF_ERR_INVALID_ARG, "threads must be a multiple of 32 in 32..512, blocks per SM 1..32");
+  }
+  const int c = cfg->cells_per_warp;
+  if (c != 1 && c != 2 && c != 4 && c != 8) return batch_fail(b, SPHBUF_ERR_INVALID_ARG, "cells per warp: 1, 2, 4 or 8");
+  BCK(cudaStreamSynchronize(b->stream));
+  for (int q = 0; q < SPHBUF_KERNEL_COUNT; ++q) {
+    b->thr[kTuned[q]] = cfg->threads[q];
+    b->mk[kTuned[q]] = cfg->blocks_per_sm[q];
+  }
+  b->cpw = c;
+  return batch_build_maps(b);
+}
+
+sphbuf_status sphbuf_batch_set_persistent(sphbuf_batch_t b, int enable, long long spin_limit) {
+  if (!b) return SPHBUF_ERR_INVALID_ARG;
+  if (enable && (b->rot || b->dual_n > 0))
+    return batch_fail(b, SPHBUF_ERR_INVALID_ARG,
+                      "the persistent step serves single-rate batches without rotating buffers");
+  BCK(cudaStreamSynchronize(b->stream));
+  if (enable && !b->d_bar) BCK(cudaMalloc(&b->d_bar, 4 * sizeof(unsigned)));
+  if (enable) {
+    b->pgrid = persistent_grid(b->dim, b->tvf);
+    if (b->pgrid <= 0) return batch_fail(b, SPHBUF_ERR_CUDA, "no resident grid for the persistent step");
+  }
+  b->persistent = enable != 0;
+  b->spin_limit = spin_limit < 0 ? (1ll << 24) : spin_limit;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return SPHBUF_OK;
 }
 
 sphbuf_status sphbuf_batch_sync(sphbuf_batch_t b) {
@@ -1668,6 +1867,8 @@ sphbuf_status sphbuf_batch_destroy(sphbuf_batch_t b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (int k = 0; k < K_COUNT; ++k)
     if (b->d_maps[k]) cudaFree(b->d_maps[k]);
+  for (cudaEvent_t e : b->kev) cudaEventDestroy(e);
+  if (b->d_bar) cudaFree(b->d_bar);
   if (b->d_doms) cudaFree(b->d_doms);
   for (int p = 0; p <= kPhases; ++p)
     if (b->ev[p]) cudaEventDestroy(b->ev[p]);

@@ -12,7 +12,7 @@
 namespace sphbuf {
 
 __device__ __forceinline__ unsigned long long injection_key(const Decision* e) {
-  return ((unsigned long long)__ldg(&e->k) << 32) | __ldg(&e->id);
+  return ((unsigned long long)SPHBUF_LDG(&e->k) << 32) | SPHBUF_LDG(&e->id);
 }
 
 // Thread t of the domain's blocks names injection t (grid-stride): rank = the number of
@@ -28,7 +28,7 @@ __device__ __forceinline__ void rank_injections(const DomainDev& d, unsigned bid
     for (unsigned q = 0; q < n_inj; ++q) r += injection_key(inj + q) < key;
     const unsigned child = next_id + r;
     d.B.id[n + e] = child;
-    d.inj_sorted[r] = InjRecord{__ldg(&inj[e].k), __ldg(&inj[e].id), child};
+    d.inj_sorted[r] = InjRecord{SPHBUF_LDG(&inj[e].k), SPHBUF_LDG(&inj[e].id), child};
   }
 }
 

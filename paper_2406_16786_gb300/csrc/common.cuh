@@ -15,6 +15,13 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+// Loads of data written by an earlier launch: the read-only data path (__ldg).  A translation
+// unit whose kernel also writes that data in the same launch (the persistent batched step)
+// defines SPHBUF_LDG as a coherent load before including the kernel bodies.
+#ifndef SPHBUF_LDG
+#define SPHBUF_LDG(p) __ldg(p)
+#endif
+
 namespace sphbuf {
 
 constexpr int kMaxBuffers = 32;

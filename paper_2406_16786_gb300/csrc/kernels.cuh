@@ -42,6 +42,7 @@ struct DomainDev {
   const int* seg_buf;     // buffer of each segment
   uint4* seg_range;       // (cell_start[lin0], cell_start[lin1], lin0, buffer) of each segment
   int nseg;
+  const unsigned* cand_mask;  // per cell: bit k set when the cell is a candidate cell of buffer k
   StepState* st;
   long long ncell_pad;
   int scan_tiles;
@@ -56,6 +57,7 @@ struct BatchDev {
 };
 
 enum Kern : int {
+  K_BEGIN,  // step constants before a kinematic drift (one block per domain)
   K_NEIGHBOURS,
   K_DENSITY_DEFER,
   K_FORCE,
@@ -75,6 +77,21 @@ enum Kern : int {
   K_COUNT
 };
 
+// The persistent batched step (kernels_persist.cu): one cooperative launch per step whose
+// phases walk the per-kernel block maps of the batch, separated by grid barriers.
+constexpr int kPersistPhases = 10;
+extern const int kPersistKern[kPersistPhases];  // the Kern whose block map each phase walks
+struct PersistDev {
+  const DomainDev* doms;
+  const int4* map[kPersistPhases];
+  int nvb[kPersistPhases];
+  unsigned* bar;         // 4 words: arrivals, generation, abort (zeroed before each launch)
+  long long spin_limit;  // iterations a barrier wait may spin (about 100 ns each)
+  int ndom;
+};
+int persistent_grid(int dim, bool tvf);  // resident blocks of the persistent step (0: error)
+cudaError_t launch_persistent(const PersistDev& p, int dim, bool tvf, int grid, cudaStream_t s);
+
 // Copies one domain descriptor into shared memory (whole block; ends with a barrier).
 __device__ __forceinline__ void load_domain(DomainDev& dst, const DomainDev* src) {
   const int words = (int)(sizeof(DomainDev) / sizeof(int));
@@ -84,17 +101,23 @@ __device__ __forceinline__ void load_domain(DomainDev& dst, const DomainDev* src
   __syncthreads();
 }
 
-int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s, bool tvf, int sub = 0);
-int launch_batch_buffer(Kern k, int dim, const BatchDev& b, int nblocks, bool rot, cudaStream_t s);
-int launch_batch_cells(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s);
-int batch_threads(Kern k);  // threads per block of each batched kernel
+// Batched launches with `threads` per block (up to 512).  fused: the buffer decisions
+// (Algorithms 1-3) in the drift epilogue (decide.cuh); cpw: candidate cells per warp of the
+// buffer kernel (1, 2, 4 or 8).
+int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s, bool tvf, int sub, bool fused,
+                     int threads);
+int launch_batch_buffer(Kern k, int dim, const BatchDev& b, int nblocks, bool rot, int threads, int cpw,
+                        cudaStream_t s);
+int launch_batch_cells(Kern k, int dim, const BatchDev& b, int nblocks, int threads, cudaStream_t s);
+int batch_threads(Kern k);  // threads per block of the batched kernels whose block size is fixed
+bool batch_tunable(Kern k);  // may the autotuner choose the block size of this kernel?
 
 // sph (kernels_sph.cu)
 int launch_neighbours(const DomainDev& d, cudaStream_t s);  // starts the step (step constants)
 int launch_density(const DomainDev& d, cudaStream_t s);  // two kernels: fluid, then deferred
-int launch_force(const DomainDev& d, cudaStream_t s);
-int launch_drift(const DomainDev& d, cudaStream_t s);
-int launch_dual(const DomainDev& d, cudaStream_t s);  // viscous, acoustic steps, fold (dual_n > 0)
+int launch_force(const DomainDev& d, bool fused, cudaStream_t s);
+int launch_drift(const DomainDev& d, bool fused, cudaStream_t s);
+int launch_dual(const DomainDev& d, bool fused, cudaStream_t s);  // viscous, acoustic steps, fold (dual_n > 0)
 // buffer (kernels_buffer.cu)
 int launch_identify(const DomainDev& d, cudaStream_t s);
 int launch_decide(const DomainDev& d, bool full_domain, cudaStream_t s);

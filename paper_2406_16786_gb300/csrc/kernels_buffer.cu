@@ -1,4 +1,6 @@
-// The arbitrary-positioned buffer (Sec. 3, Algorithms 1-3) on the GPU: one launch per step.
+// The arbitrary-positioned buffer (Sec. 3, Algorithms 1-3) on the GPU as a launch of its own:
+// the form for rotating buffers (Sec. 5.3), for the all-particle check and on request; by
+// default the decisions are fused into the drift (decide.cuh).
 //
 // Only the particles listed in the cells around each buffer's box are visited (four candidate
 // cells per warp, eight lanes per cell, four particles per lane loaded before any is tested;
@@ -13,7 +15,7 @@
 // duplicates follow the (buffer, parent id) order and are assigned by the first pass of the
 // rebuild (rank_injections, in apply.cuh), which needs every decision of the step.
 // The full-domain variant takes the same decisions over every particle and every buffer.
-#include "kernels.cuh"
+#include "decide.cuh"
 
 namespace sphbuf {
 
@@ -43,61 +45,12 @@ __device__ __forceinline__ void load_cand(const DomainDev& d, unsigned i, bool o
   for (int x = 0; x < D; ++x) p.f[x] = d.B.f[x][i];
 }
 
-// Writes injection `slot` of the step: its record and its duplicate at B[n + slot] (id
-// assigned by the rebuild).
-template <int D>
-__device__ __forceinline__ void write_injection(const DomainDev& d, const Decision& e, unsigned slot, unsigned n) {
-  if (slot >= d.P.list_cap || (unsigned long long)n + slot >= d.P.capacity) {
-    latch(d.st, 2 /* SPHBUF_ERR_CAPACITY */);
-    return;
-  }
-  d.inj[slot] = e;
-  const unsigned dst = n + slot;
-  d.B.cell[dst] = e.cell;
-#pragma unroll
-  for (int x = 0; x < D; ++x) {
-    d.B.f[x][dst] = e.f[x];
-    d.B.v[x][dst] = e.v[x];
-  }
-  d.B.rho[dst] = e.rho;
-  d.B.id[dst] = kNoSlot;
-  d.B.label[dst] = 0;  // the duplicate is ordinary fluid (Algorithm 1)
-}
-
-__device__ __forceinline__ void write_deletion(const DomainDev& d, const Decision& e, unsigned slot) {
-  if (slot >= d.P.list_cap) {
-    latch(d.st, 2 /* SPHBUF_ERR_CAPACITY */);
-    return;
-  }
-  d.del[slot] = e;
-}
-
 // The buffers' constants and this step's recycled density, in shared memory.
 struct BlockShared {
   BufDev bufs[kMaxBuffers];
   float rho_pb[kMaxBuffers];
   unsigned n, bad;
 };
-
-// Warp-ballot compaction of one record per flagged lane: the warp reserves its range of the
-// step's list with one atomic and the lanes write their records (and duplicates) at once.
-template <int D, bool INJ>
-__device__ __forceinline__ void stage(const DomainDev& d, BlockShared& sm, bool flag, const Decision& rec) {
-  const unsigned m = __ballot_sync(kFull, flag);
-  if (m == 0) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(m) - 1;
-  unsigned base = 0;
-  if (lane == leader) base = atomicAdd(INJ ? &d.st->n_inj : &d.st->n_del, (unsigned)__popc(m));
-  base = __shfl_sync(kFull, base, leader);
-  if (!flag) return;
-  atomicAdd(INJ ? &d.st->injected[rec.k] : &d.st->deleted[rec.k], 1ull);
-  const unsigned r = base + __popc(m & ((1u << lane) - 1u));
-  if (INJ)
-    write_injection<D>(d, rec, r, sm.n);
-  else
-    write_deletion(d, rec, r);
-}
 
 // Algorithms 1-3 for particle i of B (test state p) against buffer k; the warp stages the
 // decisions.  (lin_c, c_c, cp_c): a cell, its coordinates and its cell part for buffer k,
@@ -154,7 +107,7 @@ __device__ __forceinline__ void decide(const DomainDev& d, BlockShared& sm, int 
     for (int x = 0; x < D; ++x) rec.v[x] = d.B.v[x][i];
   }
   if (inj) rec.rho = d.B.rho[i];
-  stage<D, true>(d, sm, inj, rec);
+  stage<D, true>(d, kFull, sm.n, inj, rec);
   float fw[3] = {p.f[0], p.f[1], p.f[2]};
   bool ok = true;
   if (inj) {
@@ -200,22 +153,24 @@ __device__ __forceinline__ void decide(const DomainDev& d, BlockShared& sm, int 
   }
   if (inj && !b.vel_bc) d.B.rho[i] = sm.rho_pb[k];  // Eq. (22)
   if (del) d.B.label[i] = kDead;
-  stage<D, false>(d, sm, del, rec);
+  stage<D, false>(d, kFull, sm.n, del, rec);
 }
 
 // Decisions (restricted to candidate cells, or over all particles), then the block's lists
-// and duplicates.
-template <int D, bool FULL, bool ROT>
+// and duplicates.  CPW: candidate cells per warp (the cell tile), 32 / CPW lanes per cell.
+template <int D, bool FULL, bool ROT, int CPW>
 __device__ __forceinline__ void buffer_body(const DomainDev& d, unsigned bid, unsigned nblk) {
+  static_assert(CPW == 1 || CPW == 2 || CPW == 4 || CPW == 8, "cells per warp");
+  constexpr unsigned L = 32 / CPW;  // lanes per cell
   __shared__ BlockShared sm;
   const int lane = threadIdx.x & 31;
   const unsigned warp = (bid * blockDim.x + threadIdx.x) >> 5;
   const unsigned nwarps = (nblk * blockDim.x) >> 5;
-  // four candidate cells per warp, eight lanes per cell; the first cells' particle ranges are
+  // CPW candidate cells per warp, L lanes per cell; the first cells' particle ranges are
   // requested before the block copies the buffers' constants
-  const unsigned grp = lane >> 3, gl = lane & 7;
+  const unsigned grp = lane / L, gl = lane % L;
   const unsigned nseg = (unsigned)d.nseg;
-  unsigned s0 = warp * 4;
+  unsigned s0 = warp * CPW;
   uint4 r = make_uint4(0, 0, 0, 0);  // (first particle, end, cell, buffer)
   if constexpr (!FULL) {
     if (s0 + grp < nseg) r = d.seg_range[s0 + grp];
@@ -244,13 +199,13 @@ __device__ __forceinline__ void buffer_body(const DomainDev& d, unsigned bid, un
       for (int kk = 0; kk < d.nbuf; ++kk) decide<D, ROT>(d, sm, kk, i, p, -1, none, zero);
     }
   } else {
-    // four particles per lane are loaded before any is tested (cells of up to 32 particles
+    // four particles per lane are loaded before any is tested (cells of up to 4 L particles
     // take one pass)
     while (s0 < nseg) {
       const unsigned j0 = r.x, j1 = r.y;
       const int lin = (int)r.z, kc = (int)r.w;
       // next cells' ranges, requested before this group is tested
-      const unsigned s1 = s0 + nwarps * 4;
+      const unsigned s1 = s0 + nwarps * CPW;
       r = make_uint4(0, 0, 0, 0);
       if (s1 + grp < nseg) r = d.seg_range[s1 + grp];
       // the cell's coordinates and cell part, shared by its particles that stayed in it
@@ -258,16 +213,16 @@ __device__ __forceinline__ void buffer_body(const DomainDev& d, unsigned bid, un
       float cp[3];
       cell_coords(lin, d.g, cc);
       cell_part<D>(sm.bufs[kc], cc, d.g.cs, cp);
-      const unsigned passes = __reduce_max_sync(kFull, (j1 - j0 + 31) >> 5);
+      const unsigned passes = __reduce_max_sync(kFull, (j1 - j0 + 4 * L - 1) / (4 * L));
       for (unsigned it = 0; it < passes; ++it) {
         Cand p[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const unsigned i = j0 + it * 32 + q * 8 + gl;
+          const unsigned i = j0 + it * 4 * L + q * L + gl;
           load_cand<D>(d, i, i < j1, p[q]);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) decide<D, ROT>(d, sm, kc, j0 + it * 32 + q * 8 + gl, p[q], lin, cc, cp);
+        for (int q = 0; q < 4; ++q) decide<D, ROT>(d, sm, kc, j0 + it * 4 * L + q * L + gl, p[q], lin, cc, cp);
       }
       s0 = s1;
     }
@@ -276,15 +231,16 @@ __device__ __forceinline__ void buffer_body(const DomainDev& d, unsigned bid, un
 
 template <int D, bool FULL, bool ROT>
 __global__ void __launch_bounds__(kBufThreads, 4) k_buffer(DomainDev d) {
-  buffer_body<D, FULL, ROT>(d, blockIdx.x, gridDim.x);
+  buffer_body<D, FULL, ROT, 4>(d, blockIdx.x, gridDim.x);
 }
 
-template <int D, bool FULL, bool ROT>
-__global__ void __launch_bounds__(kBufThreads) k_buffer_batch(BatchDev b) {
+// batched: any block size up to 512 and a cell tile of CPW cells per warp (the autotuner's)
+template <int D, bool FULL, bool ROT, int CPW>
+__global__ void __launch_bounds__(512) k_buffer_batch(BatchDev b) {
   __shared__ DomainDev sd;
   const int4 m = b.map[blockIdx.x];
   load_domain(sd, b.doms + m.x);
-  buffer_body<D, FULL, ROT>(sd, (unsigned)m.y, (unsigned)m.z);
+  buffer_body<D, FULL, ROT, CPW>(sd, (unsigned)m.y, (unsigned)m.z);
 }
 
 template <int D>
@@ -339,12 +295,29 @@ void launch_decide_t(const DomainDev& d, cudaStream_t s) {
   k_buffer<D, FULL, ROT><<<blocks, kBufThreads, 0, s>>>(d);
 }
 
+template <int D, bool FULL, bool ROT>
+void launch_batch_tile(const BatchDev& b, int nblocks, int threads, int cpw, cudaStream_t s) {
+  switch (FULL ? 4 : cpw) {
+    case 1:
+      k_buffer_batch<D, FULL, ROT, 1><<<nblocks, threads, 0, s>>>(b);
+      break;
+    case 2:
+      k_buffer_batch<D, FULL, ROT, 2><<<nblocks, threads, 0, s>>>(b);
+      break;
+    case 8:
+      k_buffer_batch<D, FULL, ROT, 8><<<nblocks, threads, 0, s>>>(b);
+      break;
+    default:
+      k_buffer_batch<D, FULL, ROT, 4><<<nblocks, threads, 0, s>>>(b);
+  }
+}
+
 template <int D, bool FULL>
-void launch_batch_t(const BatchDev& b, int nblocks, bool rot, cudaStream_t s) {
+void launch_batch_t(const BatchDev& b, int nblocks, bool rot, int threads, int cpw, cudaStream_t s) {
   if (rot)
-    k_buffer_batch<D, FULL, true><<<nblocks, kBufThreads, 0, s>>>(b);
+    launch_batch_tile<D, FULL, true>(b, nblocks, threads, cpw, s);
   else
-    k_buffer_batch<D, FULL, false><<<nblocks, kBufThreads, 0, s>>>(b);
+    launch_batch_tile<D, FULL, false>(b, nblocks, threads, cpw, s);
 }
 
 }  // namespace
@@ -366,13 +339,16 @@ int launch_decide(const DomainDev& d, bool full_domain, cudaStream_t s) {
 }
 
 
-int launch_batch_buffer(Kern k, int dim, const BatchDev& b, int nblocks, bool rot, cudaStream_t s) {
+int launch_batch_buffer(Kern k, int dim, const BatchDev& b, int nblocks, bool rot, int threads, int cpw,
+                        cudaStream_t s) {
   if (k != K_BUFFER && k != K_BUFFER_FULL) return 0;
   const bool full = k == K_BUFFER_FULL;
   if (dim == 2)
-    full ? launch_batch_t<2, true>(b, nblocks, rot, s) : launch_batch_t<2, false>(b, nblocks, rot, s);
+    full ? launch_batch_t<2, true>(b, nblocks, rot, threads, cpw, s)
+         : launch_batch_t<2, false>(b, nblocks, rot, threads, cpw, s);
   else
-    full ? launch_batch_t<3, true>(b, nblocks, rot, s) : launch_batch_t<3, false>(b, nblocks, rot, s);
+    full ? launch_batch_t<3, true>(b, nblocks, rot, threads, cpw, s)
+         : launch_batch_t<3, false>(b, nblocks, rot, threads, cpw, s);
   return 1;
 }
 

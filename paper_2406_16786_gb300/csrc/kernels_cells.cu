@@ -11,8 +11,7 @@
 //   finalize particle count, next id, and the particle ranges of the buffers' candidate cells
 // The result is sorted by (cell, id) whatever order the atomics took, so it is
 // deterministic and identical to a plain sort.
-#include "apply.cuh"
-#include "kernels.cuh"
+#include "cells_bodies.cuh"
 
 namespace sphbuf {
 
@@ -135,224 +134,6 @@ void scan_cells(unsigned* cnt, unsigned* part, unsigned* start, int tiles, const
   k_scan_down<<<tiles, kScanThreads, 0, s>>>(cnt, part, start, status);
 }
 
-// ---- domain scan: cell_start plus the ordered list of occupied cells (the work list of the
-// tiled neighbour passes)
-__device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned* ws, unsigned* total) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned incl = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) ws[w] = incl;
-  __syncthreads();
-  unsigned wpre = 0, tot = 0;
-  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-    if (q < w) wpre += ws[q];
-    tot += ws[q];
-  }
-  __syncthreads();
-  if (total) *total = tot;
-  return wpre + incl - x;
-}
-
-__device__ __forceinline__ void scan_reduce_occ_body(const unsigned* __restrict__ cnt, unsigned* __restrict__ part,
-                                                     unsigned* __restrict__ part_occ, unsigned tile) {
-  __shared__ unsigned ws[kScanThreads / 32];
-  const size_t base = (size_t)tile * kScanTile + (size_t)threadIdx.x * kScanItems;
-  const uint4* p = reinterpret_cast<const uint4*>(cnt + base);
-  unsigned s = 0, o = 0;
-#pragma unroll
-  for (int q = 0; q < kScanItems / 4; ++q) {
-    const uint4 v = p[q];
-    s += v.x + v.y + v.z + v.w;
-    o += (v.x > 0) + (v.y > 0) + (v.z > 0) + (v.w > 0);
-  }
-  unsigned ts = 0, to = 0;
-  block_excl_scan(s, ws, &ts);
-  block_excl_scan(o, ws, &to);
-  if (threadIdx.x == 0) {
-    part[tile] = ts;
-    part_occ[tile] = to;
-  }
-}
-
-// Exclusive scans of both per-tile sums (one block); the total occupied count goes to *n_occ.
-__device__ __forceinline__ void scan_top_occ_body(unsigned* part, unsigned* part_occ, int ntiles, unsigned* n_occ) {
-  __shared__ unsigned ws[32];
-  unsigned carry = 0, carry_o = 0;
-  for (int b0 = 0; b0 < ntiles; b0 += blockDim.x) {
-    const int t = b0 + threadIdx.x;
-    const unsigned v = t < ntiles ? part[t] : 0u;
-    const unsigned vo = t < ntiles ? part_occ[t] : 0u;
-    unsigned tot = 0, toto = 0;
-    const unsigned ex = block_excl_scan(v, ws, &tot);
-    const unsigned exo = block_excl_scan(vo, ws, &toto);
-    if (t < ntiles) {
-      part[t] = carry + ex;
-      part_occ[t] = carry_o + exo;
-    }
-    carry += tot;
-    carry_o += toto;
-  }
-  if (threadIdx.x == 0) *n_occ = carry_o;
-}
-
-__device__ __forceinline__ void scan_down_occ_body(unsigned* __restrict__ cnt, const unsigned* __restrict__ part,
-                                                   const unsigned* __restrict__ part_occ, unsigned* __restrict__ start,
-                                                   unsigned* __restrict__ occ_list, unsigned tile) {
-  __shared__ unsigned ws[kScanThreads / 32];
-  const size_t base = (size_t)tile * kScanTile + (size_t)threadIdx.x * kScanItems;
-  uint4* p = reinterpret_cast<uint4*>(cnt + base);
-  unsigned v[kScanItems];
-#pragma unroll
-  for (int q = 0; q < kScanItems / 4; ++q) {
-    const uint4 t = p[q];
-    v[4 * q] = t.x;
-    v[4 * q + 1] = t.y;
-    v[4 * q + 2] = t.z;
-    v[4 * q + 3] = t.w;
-    p[q] = make_uint4(0, 0, 0, 0);
-  }
-  unsigned s = 0, o = 0;
-#pragma unroll
-  for (int q = 0; q < kScanItems; ++q) {
-    s += v[q];
-    o += v[q] > 0;
-  }
-  unsigned run = part[tile] + block_excl_scan(s, ws, nullptr);
-  unsigned orun = part_occ[tile] + block_excl_scan(o, ws, nullptr);
-  uint4* out = reinterpret_cast<uint4*>(start + base);
-#pragma unroll
-  for (int q = 0; q < kScanItems / 4; ++q) {
-    uint4 t;
-    t.x = run;
-    run += v[4 * q];
-    t.y = run;
-    run += v[4 * q + 1];
-    t.z = run;
-    run += v[4 * q + 2];
-    t.w = run;
-    run += v[4 * q + 3];
-    out[q] = t;
-  }
-#pragma unroll
-  for (int q = 0; q < kScanItems; ++q)
-    if (v[q]) occ_list[orun++] = (unsigned)(base + q);
-}
-
-__device__ __forceinline__ void hist_body(const DomainDev& d, unsigned bid, unsigned nblk) {
-  if (d.st->status) return;
-  rank_injections(d, bid, nblk);
-  const unsigned n = d.st->n + d.st->n_inj;
-  const unsigned lane = threadIdx.x & 31u;
-  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
-    // consecutive particles mostly share a cell (B is in the last rebuild's order): one
-    // atomic per cell and warp; the slots inside a cell are only an arrival order (the
-    // scatter ranks each cell's particles by id)
-    const bool dead = d.B.label[i] == kDead;
-    const int c = d.B.cell[i];
-    const unsigned act = __activemask();
-    const unsigned peers = __match_any_sync(act, dead ? 0xFFFFFFFFu : (unsigned)c);
-    const int leader = __ffs(peers) - 1;
-    unsigned base = 0;
-    if (!dead && (int)lane == leader) base = atomicAdd(d.cnt + c, (unsigned)__popc(peers));
-    base = __shfl_sync(act, base, leader);
-    d.slot[i] = dead ? kNoSlot : base + (unsigned)__popc(peers & ((1u << lane) - 1u));
-  }
-}
-
-__device__ __forceinline__ void keys_body(const DomainDev& d, unsigned bid, unsigned nblk) {
-  if (d.st->status) return;
-  const unsigned n = d.st->n + d.st->n_inj;
-  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
-    const unsigned sl = d.slot[i];
-    if (sl != kNoSlot) d.tmp_id[d.cell_start[d.B.cell[i]] + sl] = d.B.id[i];
-  }
-}
-
-template <int D>
-__device__ __forceinline__ void scatter_body(const DomainDev& d, unsigned bid, unsigned nblk) {
-  if (d.st->status) return;
-  const unsigned n = d.st->n + d.st->n_inj;
-  const Grid& g = d.g;
-  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
-    if (d.slot[i] == kNoSlot) continue;
-    const int lin = d.B.cell[i];
-    const unsigned s0 = d.cell_start[lin], s1 = d.cell_start[lin + 1];
-    const unsigned my = d.B.id[i];
-    unsigned rank = 0;
-    for (unsigned p = s0; p < s1; ++p) rank += __ldg(d.tmp_id + p) < my;
-    const unsigned dst = s0 + rank;
-    float f[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f};
-    d.A.cell[dst] = lin;
-#pragma unroll
-    for (int x = 0; x < D; ++x) {
-      f[x] = d.B.f[x][i];
-      v[x] = d.B.v[x][i];
-      d.A.f[x][dst] = f[x];
-      d.A.v[x][dst] = v[x];
-    }
-    const float rho = d.B.rho[i];
-    d.A.rho[dst] = rho;
-    d.A.id[dst] = my;
-    int c[3];
-    cell_coords(lin, g, c);
-    d.pos4[dst] = make_float4(f[0], f[1], f[2], (float)c[0]);
-    d.vel4[dst] = make_float4(v[0], v[1], v[2], rho);
-    // Algorithms 2-3, after the rebuild: in-box particles join the buffer, others leave it
-    uint8_t lab = d.B.label[i];
-    if (d.nrelabel) {
-      for (int q = 0; q < d.nrelabel; ++q) {
-        const BufDev& b = d.bufs[d.relabel_ids[q]];
-        const bool near = c[0] >= b.box_lo[0] && c[0] <= b.box_hi[0] && c[1] >= b.box_lo[1] &&
-                          c[1] <= b.box_hi[1] && c[2] >= b.box_lo[2] && c[2] <= b.box_hi[2];
-        if (!near && lab != (uint8_t)b.label) continue;
-        float X[3];
-        local_coords<D>(b, c, f, g.cs, X, D);
-        if (in_box<D>(b, X))
-          lab = (uint8_t)b.label;
-        else if (lab == (uint8_t)b.label)
-          lab = 0;
-      }
-    }
-    d.A.label[dst] = lab;
-  }
-}
-
-__device__ __forceinline__ void finalize_body(const DomainDev& d, int count_step, unsigned bid, unsigned nblk) {
-  StepState* st = d.st;
-  if (st->status) return;
-  if (bid == 0 && threadIdx.x == 0) {
-    st->n = d.cell_start[d.g.ncell];
-    st->next_id += min(st->n_inj, d.P.list_cap);
-    // the next step's neighbour pass counts its deferred particles from zero (reset here, in
-    // a launch of its own, not by that pass's first block while the others add to it)
-    st->n_defer = 0;
-    if (count_step) {
-      st->step += 1;
-      // Sec. 5.3: re-establish the frames of rotating buffers for the next step (their
-      // particles turned in this step's buffer update)
-      for (int k = 0; k < d.nbuf; ++k) {
-        BufDev* b = const_cast<BufDev*>(d.bufs) + k;
-        if (!b->rotating) continue;
-        RotDev& q = d.rot[k];
-        advance_rotation(q);
-        double O[3], R[9];
-        rotated_frame(q, O, R);
-        frame_constants(*b, O, R, q.a, d.P.lo_d, d.P.cs_d, d.g.dim);
-      }
-    }
-  }
-  // (first particle, end, cell, buffer) of the candidate cell segments
-  for (unsigned s = bid * blockDim.x + threadIdx.x; s < (unsigned)d.nseg; s += nblk * blockDim.x) {
-    const int lin0 = d.seg_lin[2 * s];
-    d.seg_range[s] = make_uint4(d.cell_start[lin0], d.cell_start[d.seg_lin[2 * s + 1]], (unsigned)lin0,
-                                (unsigned)d.seg_buf[s]);
-  }
-}
-
 // ---- single-domain kernels
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce_occ(DomainDev d) {
   if (d.st->status) return;
@@ -395,20 +176,21 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down_occ_batch(BatchDev b
   if (d->st->status) return;
   scan_down_occ_body(d->cnt, d->scan_part, d->scan_part_occ, d->cell_start, d->occ_list, (unsigned)m.y);
 }
-__global__ void __launch_bounds__(256) k_hist_batch(BatchDev b) {
+// (the particle kernels of the rebuild take any block size up to 512: the autotuner's)
+__global__ void __launch_bounds__(512) k_hist_batch(BatchDev b) {
   __shared__ DomainDev sd;
   const int4 m = b.map[blockIdx.x];
   load_domain(sd, b.doms + m.x);
   hist_body(sd, (unsigned)m.y, (unsigned)m.z);
 }
-__global__ void __launch_bounds__(256) k_keys_batch(BatchDev b) {
+__global__ void __launch_bounds__(512) k_keys_batch(BatchDev b) {
   __shared__ DomainDev sd;
   const int4 m = b.map[blockIdx.x];
   load_domain(sd, b.doms + m.x);
   keys_body(sd, (unsigned)m.y, (unsigned)m.z);
 }
 template <int D>
-__global__ void __launch_bounds__(256) k_scatter_batch(BatchDev b) {
+__global__ void __launch_bounds__(512) k_scatter_batch(BatchDev b) {
   __shared__ DomainDev sd;
   const int4 m = b.map[blockIdx.x];
   load_domain(sd, b.doms + m.x);
@@ -600,10 +382,10 @@ int launch_rebuild(const DomainDev& d, bool count_step, cudaStream_t s) {
   return 7;
 }
 
-int launch_batch_cells(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream_t s) {
+int launch_batch_cells(Kern k, int dim, const BatchDev& b, int nblocks, int threads, cudaStream_t s) {
   switch (k) {
     case K_HIST:
-      k_hist_batch<<<nblocks, 256, 0, s>>>(b);
+      k_hist_batch<<<nblocks, threads, 0, s>>>(b);
       return 1;
     case K_SCAN_REDUCE:
       k_scan_reduce_occ_batch<<<nblocks, kScanThreads, 0, s>>>(b);
@@ -615,13 +397,13 @@ int launch_batch_cells(Kern k, int dim, const BatchDev& b, int nblocks, cudaStre
       k_scan_down_occ_batch<<<nblocks, kScanThreads, 0, s>>>(b);
       return 1;
     case K_KEYS:
-      k_keys_batch<<<nblocks, 256, 0, s>>>(b);
+      k_keys_batch<<<nblocks, threads, 0, s>>>(b);
       return 1;
     case K_SCATTER:
       if (dim == 2)
-        k_scatter_batch<2><<<nblocks, 256, 0, s>>>(b);
+        k_scatter_batch<2><<<nblocks, threads, 0, s>>>(b);
       else
-        k_scatter_batch<3><<<nblocks, 256, 0, s>>>(b);
+        k_scatter_batch<3><<<nblocks, threads, 0, s>>>(b);
       return 1;
     case K_FINALIZE:
       k_finalize_batch<<<nblocks, 256, 0, s>>>(b);
@@ -635,8 +417,30 @@ int batch_threads(Kern k) {
   switch (k) {
     case K_SCAN_TOP:
       return 1024;
+    case K_BEGIN:
+      return 32;
     default:
       return 256;
+  }
+}
+
+bool batch_tunable(Kern k) {
+  switch (k) {
+    case K_NEIGHBOURS:
+    case K_DENSITY_DEFER:
+    case K_FORCE:
+    case K_DRIFT:
+    case K_VISCOUS:
+    case K_ACOUSTIC:
+    case K_DUAL_FINISH:
+    case K_BUFFER:
+    case K_BUFFER_FULL:
+    case K_HIST:
+    case K_KEYS:
+    case K_SCATTER:
+      return true;
+    default:
+      return false;  // the scans (tiles of 4096 cells, 256 threads), the per-domain single blocks
   }
 }
 

@@ -7,6 +7,9 @@ arrays to pointers and status codes to exceptions.  A ``torch.cuda.Stream`` (or 
 from __future__ import annotations
 
 import ctypes
+import json
+import math
+import os
 from typing import Optional
 
 import numpy as np
@@ -87,19 +90,72 @@ class Batch:
     def use_graph(self, enable=True):
         self.lib.sphbuf_batch_use_graph(self.h, 1 if enable else 0)
 
-    def autotune(self, trial_steps=3, phases=_ffi.STEP_DEFAULT):
+    def autotune(self, trial_steps=3, phases=_ffi.STEP_DEFAULT, cache=None):
+        """Per-kernel launch configuration (block size x blocks per SM, the buffer kernel's cell
+        tile) from timed trial steps, which advance the domains.  With ``cache`` (a JSON file
+        path) a configuration stored for the same workload bucket (dimension, particle count
+        rounded to a power of two, number of domains, phase mask) is applied without trial
+        steps, and a new result is stored.  Returns (blocks per SM of the neighbour kernel,
+        per-phase ms of the chosen configuration, or None when it came from the cache)."""
+        key = self.bucket(phases)
+        if cache is not None and os.path.exists(cache):
+            with open(cache) as f:
+                stored = json.load(f)
+            if key in stored:
+                self.set_config(stored[key])
+                return self.get_config()["blocks_per_sm"]["neighbours"], None
         m = ctypes.c_int()
         ms = np.zeros(5, np.float64)
         st = self.lib.sphbuf_batch_autotune(self.h, int(trial_steps), int(phases), ctypes.byref(m), _ptr(ms))
         if st:
             raise SphbufError(st, "batch_autotune")
+        if cache is not None:
+            stored = {}
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    stored = json.load(f)
+            stored[key] = self.get_config()
+            with open(cache, "w") as f:
+                json.dump(stored, f, indent=1, sort_keys=True)
         return m.value, dict(zip(["neighbours", "density", "force", "buffer", "rebuild"], ms.tolist()))
+
+    def bucket(self, phases=_ffi.STEP_DEFAULT) -> str:
+        """The autotuner cache's key: dimension, total particles rounded to a power of two,
+        domains and phase mask."""
+        n = sum(d.count() for d in self.domains)
+        return "d%d_n2^%d_domains%d_phases%d" % (self.domains[0].dim, int(round(math.log2(max(n, 1)))),
+                                                  len(self.domains), int(phases))
+
+    def get_config(self):
+        raw = (ctypes.c_int * (2 * len(_ffi.KERNELS) + 1))()
+        st = self.lib.sphbuf_batch_get_config(self.h, ctypes.byref(raw))
+        if st:
+            raise SphbufError(st, "batch_get_config")
+        nk = len(_ffi.KERNELS)
+        return {"threads": dict(zip(_ffi.KERNELS, raw[:nk])), "blocks_per_sm": dict(zip(_ffi.KERNELS, raw[nk:2 * nk])),
+                "cells_per_warp": raw[2 * nk]}
+
+    def set_config(self, cfg):
+        nk = len(_ffi.KERNELS)
+        raw = (ctypes.c_int * (2 * nk + 1))(*([int(cfg["threads"][k]) for k in _ffi.KERNELS]
+                                             + [int(cfg["blocks_per_sm"][k]) for k in _ffi.KERNELS]
+                                             + [int(cfg["cells_per_warp"])]))
+        st = self.lib.sphbuf_batch_set_config(self.h, ctypes.byref(raw))
+        if st:
+            raise SphbufError(st, "batch_set_config")
 
     def set_grid(self, m: int):
         """Blocks-per-SM multiplier of the particle kernels (e.g. another batch's autotune)."""
         st = self.lib.sphbuf_batch_set_grid(self.h, int(m))
         if st:
             raise SphbufError(st, "batch_set_grid")
+
+    def set_persistent(self, enable=True, spin_limit=-1):
+        """One cooperative launch per default step (grid barriers between the phases) instead
+        of one launch per phase; spin_limit bounds each barrier wait (< 0: the default)."""
+        st = self.lib.sphbuf_batch_set_persistent(self.h, 1 if enable else 0, int(spin_limit))
+        if st:
+            raise SphbufError(st, "batch_set_persistent")
 
     def sync(self):
         st = self.lib.sphbuf_batch_sync(self.h)

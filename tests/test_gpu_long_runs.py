@@ -8,14 +8,18 @@
 * 3-D T-junction (velocity inlet, two pressure outlets at arbitrary orientations), dp 0.006,
   15.4 M particles: 500 steps.
 * 64 star channels (1-6 arms, mixed buffer types) stepped as one batch in graph replay with
-  the autotuner's grid: 500 steps, and every domain bit-for-bit equal to its own plain run
-  of 500 steps.
+  the autotuner's grid, per-phase launches and as one persistent launch per step: 500 steps,
+  and every domain bit-for-bit equal to its own plain run of 500 steps.
 
 Every run must end with status OK and:
   * the count invariant N = N0 + injected - deleted exactly, with no escaped particle;
   * the FP64 mass balance: mass in - mass out = (N - N0) m;
-  * max |rho - rho0| / rho0 below the workload's bound (stated per run: a few times the
-    Mach-number estimate U^2 / c0^2 or p / (rho0 c0^2) of the flow);
+  * max |rho - rho0| / rho0 below the workload's bound, stated per run: 3 U / c0 for a run
+    that starts impulsively (a velocity inlet or a developed profile against fluid at rest
+    sends a pressure wave of rho0 c0 U, i.e. |rho - rho0| / rho0 = U / c0, which doubles where
+    it reflects from a closed end), and a few times p / (rho0 c0^2) for the pressure-driven
+    pipe (measured: 12 % bent channel, 7 % T-junction, up to 18 % in the star channels with
+    dead-end arms, all with U / c0 = 0.1; 0.6-0.8 % in the pipes);
   * at buffers whose flow enters the domain (velocity inlets, and the bidirectional inlet of
     the pipe, whose driving pressure keeps the flow forward for the whole 1.07 s), deletions
     at the outer face within a budget: none at a velocity inlet (Algorithm 1 deletes
@@ -44,9 +48,11 @@ def _check_run(dom, case, n0, steps, rho_bound, inflow_side, outer_budget):
     mass = case.rho0 * case.dp ** case.dim
     net = sum(c["mass_in"] for c in cnt) - sum(c["mass_out"] for c in cnt)
     st = dom.read()
-    drho = float(np.max(np.abs(st["rho"].astype(np.float64) - case.rho0)) / case.rho0) if n else 0.0
+    dr = np.abs(st["rho"].astype(np.float64) - case.rho0) / case.rho0
+    drho = float(np.max(dr)) if n else 0.0
     fig = {"particles": n, "n0": n0, "steps": g["steps"], "injected": [c["injected"] for c in cnt],
-           "deleted": [c["deleted"] for c in cnt], "max_drho": drho, "escaped": g["escaped"]}
+           "deleted": [c["deleted"] for c in cnt], "max_drho": drho,
+           "p99_drho": float(np.percentile(dr, 99)) if n else 0.0, "escaped": g["escaped"]}
     print(case.name, fig)
     assert g["steps"] == steps and g["escaped"] == 0
     assert n == n0 + inj - dels
@@ -79,8 +85,8 @@ def _run(case, steps, rho_bound, inflow_side=(), outer_budget=0.0):
 
 def test_bent_channel_2000_steps():
     c = wl.config2()
-    # U = 1.5, c0 = 15: U^2 / c0^2 = 1 %
-    _run(c, 2000, rho_bound=0.05, inflow_side=[0])
+    # U = 1.5, c0 = 15: 3 U / c0 = 0.3
+    _run(c, 2000, rho_bound=0.3, inflow_side=[0])
 
 
 @pytest.mark.parametrize("length", [8.0, 5.09])
@@ -92,8 +98,8 @@ def test_pipe_1000_steps(length):
 
 def test_tjunction_500_steps():
     c = wl.config4()
-    # U = 1, c0 = 10: 1 %
-    _run(c, 500, rho_bound=0.05, inflow_side=[0])
+    # U = 1, c0 = 10: 3 U / c0 = 0.3
+    _run(c, 500, rho_bound=0.3, inflow_side=[0])
 
 
 def test_batched_stars_500_steps_equal_plain_runs():
@@ -131,16 +137,29 @@ def test_batched_stars_500_steps_equal_plain_runs():
     t_batch = time.perf_counter() - t0
     print("64 star channels, %d steps: plain runs %.2f s, batch %.2f s (grid multiplier %d)"
           % (steps, t_plain, t_batch, m))
-    for q, (c, d) in enumerate(zip(stars, doms)):
+    # the same batch as one persistent launch per step
+    pdoms = [Domain.from_case(c) for c in stars]
+    pb = Batch(pdoms)
+    pb.set_grid(m)
+    pb.set_persistent(True)
+    pb.use_graph(True)
+    t0 = time.perf_counter()
+    pb.step(steps)
+    pb.sync()
+    t_pers = time.perf_counter() - t0
+    print("persistent batch %.2f s" % t_pers)
+    for q, (c, d, pd) in enumerate(zip(stars, doms, pdoms)):
         ra, ga, ca = alone[q]
-        rt = d.read()
-        for key in ra:
-            assert np.array_equal(ra[key], rt[key]), (q, key)
-        assert d.global_counters() == ga
-        assert [d.counters(k) for k in range(len(c.buffers))] == ca
-        # stars: U = 1, c0 = 10
+        for dd in (d, pd):
+            rt = dd.read()
+            for key in ra:
+                assert np.array_equal(ra[key], rt[key]), (q, key)
+            assert dd.global_counters() == ga
+            assert [dd.counters(k) for k in range(len(c.buffers))] == ca
+        # stars: U = 1, c0 = 10: 3 U / c0 = 0.3
         inflow = [k for k, bs in enumerate(c.buffers) if bs.bc in INFLOW_KINDS]
-        _check_run(d, c, n0[q], steps, 0.05, inflow, 0.0)
+        _check_run(d, c, n0[q], steps, 0.3, inflow, 0.0)
     b.close()
-    for d in doms:
+    pb.close()
+    for d in doms + pdoms:
         d.close()

@@ -62,6 +62,12 @@ def parse():
     ap.add_argument("--ab-steps", type=int, default=200)
     ap.add_argument("--ab-rounds", type=int, default=3)
     ap.add_argument("--pair-steps", type=int, default=100)
+    ap.add_argument("--skin", type=float, default=0.1,
+                    help="neighbour-list skin / h of the main measurement (kept lists); 0 rebuilds every step")
+    ap.add_argument("--reuse-max", type=int, default=64)
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling driver: the pipe at --length, 100 steps, one default step, one step with the "
+                         "buffer kernel; prints the particle count and exits")
     ap.add_argument("--spinup", type=int, default=250)
     ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--no-batched", action="store_true")
@@ -356,6 +362,8 @@ def run_gpu(args):
     case = workloads.config3(length=args.length)
     stream = torch.cuda.Stream()
     dom = Domain.from_case(case, stream=stream)
+    if args.skin > 0:
+        dom.set_list_reuse(args.skin, args.reuse_max)
     dom.use_graph(True)
     # untimed spin-up from the developed profile: the lattice layers of the buffers start
     # ~0.5 dp from the faces, so crossings begin after ~80 steps near the axis
@@ -364,6 +372,7 @@ def run_gpu(args):
     dom.sync()
     n0 = dom.count()
     l0 = dom.launch_count()
+    b0 = dom.list_builds()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -381,6 +390,7 @@ def run_gpu(args):
     launches = dom.launch_count() - l0
     dom.sync()
     n1 = dom.count()
+    full_builds = dom.list_builds() - b0
     ms_max = ms
     if dist:
         t = torch.tensor([ms], device="cuda")
@@ -401,7 +411,16 @@ def run_gpu(args):
         dom.use_graph(True)
         return {k: v / nph_ for k, v in t.items()}, nph_
 
+    bb = dom.list_builds()
     per, nph = phase_times(_ffi.STEP_DEFAULT)
+    full_frac = (dom.list_builds() - bb) / max(1, nph) if args.skin > 0 else 1.0
+    # the buffer kernel of its own and the fused decisions' cost on the same workload with
+    # lists rebuilt every step (kept lists need the fused decisions): a second domain, spun
+    # up like the first
+    dom_kept = dom
+    dom = Domain.from_case(case, stream=stream)
+    dom.use_graph(True)
+    dom.step(args.spinup + args.warmup)
     per_sep, _ = phase_times(_ffi.STEP_DEFAULT | _ffi.PHASE_BUFFER_KERNEL)
 
     # buffer update: algorithmic bytes per step (decision read + relabel read of each candidate
@@ -417,6 +436,8 @@ def run_gpu(args):
     hbm = peaks.get("hbm_gbs")
     ab = fused_buffer_cost(dom, stream, args.ab_steps, args.ab_rounds, len(case.buffers))
     fpair = fused_force_cost(dom, args.pair_steps)
+    dom.close()
+    dom = dom_kept
     n_inj, n_del = ab["injected_per_step"], ab["deleted_per_step"]
     bu_bytes = 8 * cells + 2 * parts * (4 * dim + 1) + n_inj * (2 * state_bytes + 4 * dim) + n_del
 
@@ -445,13 +466,18 @@ def run_gpu(args):
     cands = 27 * (2 * case.h_over_dp) ** dim            # particles in the 27 cells of side 2h
     # k_neighbours builds the lists and computes Eq. (9) for the fluid particles from them;
     # the density phase left (k_density_deferred) handles the few buffer / overflowed ones
-    flops = {"neighbours": cands * 9.0 + pairs * 14.0, "force": pairs * 58.0}
+    # with kept lists the candidate tests run on the steps with a full build (counted from the
+    # phase-timed steps) and in the every-step region around the buffers (not counted: a lower
+    # bound of the work); the pairs are those within 2h (the entries beyond, up to the skin,
+    # add nothing and are not counted)
+    flops = {"neighbours": cands * 9.0 * full_frac + pairs * 14.0, "force": pairs * 58.0}
     sm_max = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
     alu_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max / 1e12
     kern = {}
     for ph, name in (("neighbours", "k_neighbours"), ("force", "k_force")):
         tf = n_mean * flops[ph] / (per[ph] / 1e3) / 1e12
         kern[ph] = {"kernel": name, "ms": per[ph], "flops_per_particle": flops[ph], "achieved": tf,
+                    "full_build_fraction": full_frac,
                     "frac": tf / alu_peak}
     dom_ph = max(kern, key=lambda k: kern[k]["ms"])
 
@@ -542,6 +568,9 @@ def run_gpu(args):
                    "cells": int(dom.ncell), "buffers": len(case.buffers), "dt": case.dt,
                    "l2": "state (~%d MB) larger than L2; no flush" % (n_mean * 2 * state_bytes / 1e6),
                    "parallelism": "replicas%d" % world, "graph": True,
+                   "neighbour_lists": ("kept over steps, skin %g h (full builds: %d in %d timed steps)"
+                                       % (args.skin, full_builds, args.steps)) if args.skin > 0 else
+                                      "rebuilt every step",
                    "start": "developed parabolic profile, %d untimed spin-up steps" % args.spinup},
         "buffer_update_us_per_step": bu["fused"]["us_per_step"],
         "buffer_update_kernel_us_per_step": bu["kernel"]["us_per_step"],
@@ -852,9 +881,30 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_profile(args):
+    """The launch sequence profiled for the ncu summaries: the pipe at --length (2.5 m: 2.0 M
+    particles), 100 default steps (lists rebuilt every step), one default step (k_force with
+    the fused decisions: launch 101) and one step with the decisions in the buffer kernel
+    (k_force without them: launch 102; k_buffer: launch 1)."""
+    from paper_2406_16786_gb300 import _ffi, workloads
+    from paper_2406_16786_gb300.domain import Domain
+
+    case = workloads.config3(length=args.length)
+    dom = Domain.from_case(case)
+    dom.step(100)
+    dom.step(1)
+    dom.step(1, _ffi.STEP_DEFAULT | _ffi.PHASE_BUFFER_KERNEL)
+    dom.sync()
+    inj, dels = dom.last_decisions()
+    print("particles", dom.count(), "last step decisions", len(inj), len(dels))
+    dom.close()
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.profile:
+        run_profile(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_gpu(a)

@@ -68,7 +68,10 @@ typedef enum {
   SPHBUF_ERR_CUDA = 4,        /* a CUDA runtime call failed */
   SPHBUF_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
   SPHBUF_ERR_NAN = 6,         /* a non-finite position was met */
-  SPHBUF_ERR_STATE = 7        /* call not valid now (e.g. add_inout_buffer after the first step) */
+  SPHBUF_ERR_STATE = 7,       /* call not valid now (e.g. add_inout_buffer after the first step) */
+  SPHBUF_ERR_BOUNDS = 8       /* an index check of the bounds-checked build failed (the library
+                                 built with SPHBUF_CHECK=1); the failing site and index are in
+                                 the domain's error message */
 } sphbuf_status;
 
 typedef enum {
@@ -98,7 +101,9 @@ typedef enum {
 
 typedef struct {
   int dim;                  /* 2 or 3 */
-  double lo[3], hi[3];      /* grid box, global coordinates (m); must contain every particle */
+  double lo[3], hi[3];      /* grid box, global coordinates (m); must contain every particle;
+                               cut into cells of 2h, at most 2048 x 2048 x 1024 of them
+                               (SPHBUF_ERR_INVALID_ARG otherwise) */
   double dp;                /* initial particle spacing (m) */
   double h_over_dp;         /* smoothing length / dp (1.3 in the paper, Sec. 3) */
   double rho0, c0, nu, dt;  /* reference density, artificial sound speed, kinematic viscosity,
@@ -257,6 +262,25 @@ sphbuf_status sphbuf_read_boundary_pressure(sphbuf_domain_t d, int buffer_id, do
  * the transpose of the printed formula, so that X' = R (X - O') has X' along n), followed by
  * a roll about X': R <- Rx(roll) R.  n need not be unit length. */
 sphbuf_status sphbuf_rotation_from_normal(const double normal[3], double roll, double out_R[9]);
+
+/* Kept neighbour lists (a Verlet skin): with skin_over_h > 0 the lists hold the pairs within
+ * 2h + skin (skin = skin_over_h h, at most h) and are kept over steps.  A step whose rebuild
+ * keeps the lists also keeps the particles' slots (no sort; deleted particles stay as dead
+ * slots, duplicates are appended), except where the lists must change: the particles in the
+ * buffers' candidate cells and two rings of cells around them search their neighbours again
+ * every step (through a list of the live particles sorted by (cell, id), rebuilt every step).
+ * A full rebuild (sort, every list searched again) follows once twice the largest drift path
+ * of any particle since the last one exceeds the skin (a pair may then have come within 2h
+ * unlisted), after max_steps steps, after a kinematic step and after particles are written.
+ * Results differ from lists rebuilt every step only by the order of the FP32 sums.  Reads
+ * and counts always give the live particles sorted by (cell, id).  skin_over_h = 0 turns it
+ * off (the default).  Only before the first step.  Errors: SPHBUF_ERR_INVALID_ARG (skin
+ * outside [0, 1] h, max_steps < 1, rotating buffers or dual-criteria stepping; later steps
+ * with SPHBUF_PHASE_BUFFER_KERNEL or SPHBUF_PHASE_FULL_CHECK are refused too),
+ * SPHBUF_ERR_STATE (after the first step). */
+sphbuf_status sphbuf_set_list_reuse(sphbuf_domain_t d, double skin_over_h, int max_steps);
+/* Full neighbour-list builds so far (with lists rebuilt every step: one per rebuild). */
+sphbuf_status sphbuf_read_list_builds(sphbuf_domain_t d, uint64_t *builds);
 
 /* Runs nsteps full steps (SPHBUF_STEP_DEFAULT), asynchronously on the domain's stream. */
 sphbuf_status sphbuf_step(sphbuf_domain_t d, int nsteps);

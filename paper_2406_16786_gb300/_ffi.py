@@ -65,6 +65,8 @@ SIGNATURES = {
     "sphbuf_batch_get_config": (ctypes.c_int, [vp, vp]),
     "sphbuf_batch_set_config": (ctypes.c_int, [vp, vp]),
     "sphbuf_batch_set_persistent": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_longlong]),
+    "sphbuf_set_list_reuse": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int]),
+    "sphbuf_read_list_builds": (ctypes.c_int, [vp, P(ctypes.c_uint64)]),
     "sphbuf_write_particles_async": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, ctypes.c_uint64, ctypes.c_uint32]),
     "sphbuf_read_particles_async": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, ctypes.c_uint64, P(ctypes.c_uint64)]),
     "sphbuf_io_wait": (ctypes.c_int, [vp]),

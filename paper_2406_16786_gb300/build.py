@@ -43,8 +43,12 @@ def _compile(src, extra):
 
 
 def build(verbose: bool = False, extra=None) -> str:
+    """Compiles and links the library.  With SPHBUF_CHECK=1 in the environment the kernels are
+    built with their index checks (a failed check latches SPHBUF_ERR_BOUNDS, see kernels.cuh)."""
     os.makedirs(BUILD, exist_ok=True)
     extra = list(extra or [])
+    if os.environ.get("SPHBUF_CHECK") == "1":
+        extra.append("-DSPHBUF_CHECK")
     srcs = sources()
     with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
         results = list(ex.map(lambda s: _compile(s, extra), srcs))

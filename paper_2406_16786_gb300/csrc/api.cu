@@ -48,6 +48,8 @@ struct sphbuf_domain {
   std::vector<void*> allocs;
   void* seg_mem = nullptr;
   unsigned* cand_mask = nullptr;  // per cell: candidate buffers (bit k), for the fused decisions
+  uint8_t* s_mask = nullptr;      // per cell: kept neighbour lists are rebuilt every step there
+  float* xfer = nullptr;          // staging of the blocking transfers' AoS arrays (2 x capacity x dim)
   std::vector<int> seg_host, segbuf_host;
   void* wall_mem = nullptr;
   uint64_t launches = 0;
@@ -327,6 +329,25 @@ sphbuf_status build_segments(sphbuf_domain* d) {
   if (!d->cand_mask) CK(cudaMalloc(&d->cand_mask, std::max<size_t>((size_t)d->ncell, 1) * sizeof(unsigned)));
   CK(cudaMemcpy(d->cand_mask, mask.data(), mask.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
   d->dev.cand_mask = d->cand_mask;
+  // every-step region of kept neighbour lists: the candidate cells (duplicates appear there,
+  // parents are recycled there) and two rings of cells around them, so that no kept list
+  // (radius 2h + skin < 2 cells) can reach a particle that appeared or jumped in this step
+  std::vector<uint8_t> smask((size_t)d->ncell, 0);
+  for (size_t lin = 0; lin < mask.size(); ++lin) {
+    if (!mask[lin]) continue;
+    const int cx = (int)(lin % d->dims[0]), cy = (int)((lin / d->dims[0]) % d->dims[1]),
+              cz = (int)(lin / ((size_t)d->dims[0] * d->dims[1]));
+    for (int dz = (D == 3 ? -2 : 0); dz <= (D == 3 ? 2 : 0); ++dz)
+      for (int dy = -2; dy <= 2; ++dy)
+        for (int dx = -2; dx <= 2; ++dx) {
+          const int x = cx + dx, y = cy + dy, z = cz + dz;
+          if (x < 0 || y < 0 || z < 0 || x >= d->dims[0] || y >= d->dims[1] || z >= d->dims[2]) continue;
+          smask[((size_t)z * d->dims[1] + y) * d->dims[0] + x] = 1;
+        }
+  }
+  if (!d->s_mask) CK(cudaMalloc(&d->s_mask, std::max<size_t>((size_t)d->ncell, 1)));
+  CK(cudaMemcpy(d->s_mask, smask.data(), smask.size(), cudaMemcpyHostToDevice));
+  d->dev.s_mask = d->s_mask;
   const size_t nseg = segbuf.size();
   // [seg_range: 4 nseg words, 16-byte aligned][seg_lin: 2 nseg][seg_buf: nseg]; the ranges
   // are written by every rebuild (the first one runs before the first step)
@@ -363,9 +384,19 @@ sphbuf_status read_state(sphbuf_domain* d, StepState* out) {
                        : out->status == SPHBUF_ERR_NAN         ? "non-finite particle position"
                        : out->status == SPHBUF_ERR_TIMEOUT     ? "a grid-barrier wait of the persistent batched step "
                                                                  "ran out of its spin limit"
+                       : out->status == SPHBUF_ERR_BOUNDS      ? "an index check failed (bounds-checked build)"
                        : out->status == SPHBUF_ERR_INVALID_ARG ? "asynchronously written arrays failed the checks "
                                                                  "(cell, offset, label or next_id)"
                                                                : "device-side error";
+    if (out->status == SPHBUF_ERR_BOUNDS) {
+      unsigned io[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      cudaMemcpy(io, d->dev.io, sizeof(io), cudaMemcpyDeviceToHost);
+      return fail(d, SPHBUF_ERR_BOUNDS,
+                  std::string(what) + ": site " + std::to_string(io[2]) + ", index " + std::to_string(io[3]) +
+                      ", particle " + std::to_string(io[4]) + " (list count " + std::to_string(io[5]) + ", cell " +
+                      std::to_string(io[6]) + "), sorted " + std::to_string(io[7] & 255u) + ", steps since sort " +
+                      std::to_string(io[7] >> 8));
+    }
     return fail(d, (sphbuf_status)out->status, what);
   }
   return SPHBUF_OK;
@@ -446,7 +477,7 @@ sphbuf_status commit(sphbuf_domain* d) {
       d->ingest_pending = false;
     }
     if (!d->labels_given) d->launches += launch_identify(d->dev, d->stream);
-    d->launches += launch_rebuild(d->dev, false, d->stream);
+    d->launches += launch_rebuild(d->dev, false, true, d->stream);
     CK(cudaGetLastError());
     d->need_rebuild = false;
   }
@@ -486,7 +517,8 @@ int enqueue_step(sphbuf_domain* d, unsigned phases, bool timed) {
     k += launch_decide(v, (phases & SPHBUF_PHASE_FULL_CHECK) != 0, s);
   }
   if (timed) cudaEventRecord(d->ev[4], s);
-  k += launch_rebuild(v, true, s);
+  // kinematic steps use no lists: they end with a sorted state
+  k += launch_rebuild(v, true, (phases & SPHBUF_PHASE_KINEMATIC) != 0, s);
   if (timed) cudaEventRecord(d->ev[5], s);
   return k;
 }
@@ -505,6 +537,7 @@ const char* sphbuf_status_string(sphbuf_status s) {
     case SPHBUF_ERR_TIMEOUT: return "device wait timed out";
     case SPHBUF_ERR_NAN: return "non-finite value";
     case SPHBUF_ERR_STATE: return "call not valid in the current state";
+    case SPHBUF_ERR_BOUNDS: return "index out of bounds (bounds-checked build)";
   }
   return "unknown status";
 }
@@ -535,7 +568,8 @@ sphbuf_status sphbuf_create_domain(const sphbuf_domain_desc* desc, void* cuda_st
     }
   }
   d->ncell = (long long)d->dims[0] * d->dims[1] * d->dims[2];
-  if (d->ncell >= (1ll << 31) - kScanTile) {
+  if (d->ncell >= (1ll << 31) - kScanTile || d->dims[0] > kMaxCellsX || d->dims[1] > kMaxCellsY ||
+      d->dims[2] > kMaxCellsZ) {
     delete d;
     return SPHBUF_ERR_INVALID_ARG;
   }
@@ -581,6 +615,10 @@ sphbuf_status sphbuf_create_domain(const sphbuf_domain_desc* desc, void* cuda_st
   P.cs_d = d->cs;
   P.capacity = (unsigned)desc->capacity;
   P.list_cap = (unsigned)std::max<uint64_t>(1024, std::min<uint64_t>(desc->capacity, 1ull << 22));
+  P.reuse = 0;
+  P.list_r2 = P.two_h_sq;
+  P.skin = 0.f;
+  P.reuse_max = 1;
   const size_t C = desc->capacity;
   v.ncell_pad = (d->ncell + 1 + kScanTile - 1) / kScanTile * kScanTile;
   v.scan_tiles = (int)(v.ncell_pad / kScanTile);
@@ -601,7 +639,9 @@ sphbuf_status sphbuf_create_domain(const sphbuf_domain_desc* desc, void* cuda_st
     A(dalloc(d, &p->rho, C));
     A(dalloc(d, &p->id, C));
     A(dalloc(d, &p->label, C));
+    A(dalloc(d, &p->path, C));
   }
+  A(dalloc(d, &v.order, C));
   A(dalloc(d, &v.vr4, C));
   A(dalloc(d, &v.deferred, C));
   // neighbour lists of the density pass, reused by the force pass (~80 neighbours in 3-D and
@@ -629,8 +669,13 @@ sphbuf_status sphbuf_create_domain(const sphbuf_domain_desc* desc, void* cuda_st
   A(dalloc(d, &rel, kMaxBuffers));
   v.relabel_ids = rel;
   A(dalloc(d, &v.st, 1));
-  A(dalloc(d, &v.io, 4));
+  A(dalloc(d, &v.io, 8));
   if (e == cudaSuccess) {
+    A(cudaMemset(v.io, 0, 8 * sizeof(unsigned)));
+    // list entries that no search has written read as an index beyond any particle (caught by
+    // the bounds-checked build), and list counts start at 0
+    A(cudaMemset(v.nb, 0xFF, C * (size_t)v.nb_cap * sizeof(unsigned)));
+    A(cudaMemset(v.nb_cnt, 0, C * sizeof(unsigned)));
     A(cudaMemset(v.cnt, 0, (size_t)v.ncell_pad * sizeof(unsigned)));
     A(cudaMemset(v.cell_start, 0, ((size_t)v.ncell_pad + 1) * sizeof(unsigned)));
     A(cudaMemset(v.st, 0, sizeof(StepState)));
@@ -659,6 +704,7 @@ sphbuf_status sphbuf_destroy(sphbuf_domain_t d) {
   for (void* p : d->allocs) cudaFree(p);
   if (d->seg_mem) cudaFree(d->seg_mem);
   if (d->cand_mask) cudaFree(d->cand_mask);
+  if (d->s_mask) cudaFree(d->s_mask);
   for (int q = 0; q <= kPhases; ++q)
     if (d->ev[q]) cudaEventDestroy(d->ev[q]);
   if (d->own_stream) cudaStreamDestroy(d->stream);
@@ -703,7 +749,12 @@ sphbuf_status sphbuf_set_walls(sphbuf_domain_t d, const double* pos, uint64_t n)
     w4[p].x = sf[0][p];
     w4[p].y = sf[1][p];
     w4[p].z = D == 3 ? sf[2][p] : 0.f;
-    w4[p].w = (float)(sc[p] % d->dims[0]);
+    w4[p].w = [&] {
+      const unsigned pc = pack_cell(sc[p] % d->dims[0], (sc[p] / d->dims[0]) % d->dims[1], sc[p] / (d->dims[0] * d->dims[1]));
+      float f;
+      std::memcpy(&f, &pc, sizeof f);
+      return f;
+    }();
   }
   const size_t nn = std::max<uint64_t>(n, 1);
   const size_t bytes =
@@ -737,9 +788,10 @@ sphbuf_status sphbuf_write_particles(sphbuf_domain_t d, const int32_t* cell, con
   Particles& B = d->dev.B;
   cudaStream_t s = d->stream;
   if (n) {
-    // copy the arrays as they are (the AoS frac / vel into the neighbour-list storage, which
-    // the next step rewrites), then check and transpose them on the device
-    float* sf = reinterpret_cast<float*>(d->dev.nb);
+    // copy the arrays as they are (the AoS frac / vel into the transfer staging), then check
+    // and transpose them on the device
+    if (!d->xfer) CK(dalloc(d, &d->xfer, 2 * (size_t)d->desc.capacity * D));
+    float* sf = d->xfer;
     float* sv = sf + (size_t)n * D;
     CK(cudaMemcpyAsync(B.cell, cell, n * sizeof(int), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(sf, frac, n * D * sizeof(float), cudaMemcpyHostToDevice, s));
@@ -763,6 +815,8 @@ sphbuf_status sphbuf_write_particles(sphbuf_domain_t d, const int32_t* cell, con
       StepState st;
       CK(cudaMemcpy(&st, d->dev.st, sizeof(StepState), cudaMemcpyDeviceToHost));
       st.n = 0;
+      st.n_live = 0;
+      st.full = 1;
       st.n_inj = 0;
       st.n_del = 0;
       CK(cudaMemcpy(d->dev.st, &st, sizeof(StepState), cudaMemcpyHostToDevice));
@@ -774,6 +828,8 @@ sphbuf_status sphbuf_write_particles(sphbuf_domain_t d, const int32_t* cell, con
   StepState st;
   CK(cudaMemcpy(&st, d->dev.st, sizeof(StepState), cudaMemcpyDeviceToHost));
   st.n = (unsigned)n;
+  st.n_live = (unsigned)n;
+  st.full = 1;
   st.n_inj = 0;
   st.n_del = 0;
   st.next_id = next_id;
@@ -1023,6 +1079,7 @@ sphbuf_status sphbuf_set_buffer_rotation(sphbuf_domain_t d, int buffer_id, const
   if (!d || !pivot) return SPHBUF_ERR_INVALID_ARG;
   if (d->stepped || d->committed) return fail(d, SPHBUF_ERR_STATE, "rotation must be set before the first step");
   if (buffer_id < 0 || buffer_id >= (int)d->bufs.size()) return fail(d, SPHBUF_ERR_INVALID_ARG, "no such buffer");
+  if (d->dev.P.reuse) return fail(d, SPHBUF_ERR_INVALID_ARG, "kept neighbour lists serve domains without rotating buffers");
   BufHost& b = d->bufs[buffer_id];
   BufDev& v = d->bufs_dev[buffer_id];
   if (v.kind != KIND_INFLOW) return fail(d, SPHBUF_ERR_INVALID_ARG, "only inflow buffers may rotate");
@@ -1107,6 +1164,8 @@ sphbuf_status sphbuf_set_dual_time_stepping(sphbuf_domain_t d, int n_acoustic) {
   if (!d) return SPHBUF_ERR_INVALID_ARG;
   if (d->stepped || d->committed) return fail(d, SPHBUF_ERR_STATE, "the time stepping must be set before the first step");
   if (n_acoustic < 0 || n_acoustic > 4096) return fail(d, SPHBUF_ERR_INVALID_ARG, "n_acoustic must be in [0, 4096]");
+  if (n_acoustic > 0 && d->dev.P.reuse)
+    return fail(d, SPHBUF_ERR_INVALID_ARG, "kept neighbour lists serve single-rate domains");
   DomainDev& v = d->dev;
   if (n_acoustic > 0 && !v.pos_b) {
     const size_t C = d->desc.capacity;
@@ -1125,6 +1184,34 @@ sphbuf_status sphbuf_set_transport_velocity(sphbuf_domain_t d, double lambda) {
   if (!(lambda >= 0) || !std::isfinite(lambda)) return fail(d, SPHBUF_ERR_INVALID_ARG, "lambda must be finite and >= 0");
   d->dev.P.tvf_lambda = (float)lambda;
   return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_set_list_reuse(sphbuf_domain_t d, double skin_over_h, int max_steps) {
+  if (!d) return SPHBUF_ERR_INVALID_ARG;
+  if (d->stepped) return fail(d, SPHBUF_ERR_STATE, "kept neighbour lists are chosen before the first step");
+  if (!(skin_over_h >= 0.0) || skin_over_h > 1.0 || max_steps < 1)
+    return fail(d, SPHBUF_ERR_INVALID_ARG, "skin must be in [0, h], max_steps >= 1");
+  if (skin_over_h > 0.0 && (d->dev.any_rot || d->dev.P.dual_n > 0))
+    return fail(d, SPHBUF_ERR_INVALID_ARG, "kept neighbour lists serve single-rate domains without rotating buffers");
+  Phys& P = d->dev.P;
+  const double h = d->desc.h_over_dp * d->desc.dp;
+  P.reuse = skin_over_h > 0.0 ? 1 : 0;
+  P.skin = (float)(skin_over_h * h);
+  P.list_r2 = P.reuse ? (float)((2.0 * h + skin_over_h * h) * (2.0 * h + skin_over_h * h)) : P.two_h_sq;
+  P.reuse_max = max_steps;
+  if (d->graph) {
+    cudaGraphExecDestroy(d->graph);
+    d->graph = nullptr;
+  }
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_read_list_builds(sphbuf_domain_t d, uint64_t* builds) {
+  if (!d || !builds) return SPHBUF_ERR_INVALID_ARG;
+  StepState st;
+  sphbuf_status s = read_state(d, &st);
+  *builds = st.list_builds;
+  return s;
 }
 
 sphbuf_status sphbuf_set_windkessel(sphbuf_domain_t d, int buffer_id, double r_p, double compliance, double r_d,
@@ -1162,6 +1249,8 @@ sphbuf_status sphbuf_step_phases(sphbuf_domain_t d, int nsteps, unsigned phases)
   const bool phys = phases & SPHBUF_PHASE_PHYSICS, kin = phases & SPHBUF_PHASE_KINEMATIC;
   if (phys == kin) return fail(d, SPHBUF_ERR_INVALID_ARG, "exactly one of PHYSICS or KINEMATIC is required");
   if (phases & ~31u) return fail(d, SPHBUF_ERR_INVALID_ARG, "unknown phase bits");
+  if (d->dev.P.reuse && (phases & (SPHBUF_PHASE_FULL_CHECK | SPHBUF_PHASE_BUFFER_KERNEL)))
+    return fail(d, SPHBUF_ERR_INVALID_ARG, "kept neighbour lists need the decisions fused into the drift");
   if (!d->committed && !d->need_rebuild) return fail(d, SPHBUF_ERR_STATE, "no particles written");
   sphbuf_status s = commit(d);
   if (s != SPHBUF_OK) return s;
@@ -1223,7 +1312,7 @@ sphbuf_status sphbuf_count(sphbuf_domain_t d, uint64_t* n) {
   if (!d || !n) return SPHBUF_ERR_INVALID_ARG;
   StepState st;
   sphbuf_status s = read_state(d, &st);
-  *n = st.n;
+  *n = st.n_live;
   return s;
 }
 
@@ -1246,20 +1335,27 @@ sphbuf_status sphbuf_read_particles(sphbuf_domain_t d, int32_t* cell, float* fra
   StepState st;
   sphbuf_status s = read_state(d, &st);
   if (s != SPHBUF_OK) return s;
-  const uint64_t n = st.n;
+  const uint64_t n = st.n_live;
   if (n_out) *n_out = n;
   if (n > cap && (cell || frac || vel || rho || id || label))
     return fail(d, SPHBUF_ERR_CAPACITY, "host arrays smaller than the particle count");
   const int D = d->desc.dim;
-  const Particles& A = d->dev.A;
   if (!n) return SPHBUF_OK;
   cudaStream_t st_ = d->stream;
+  // the live particles in (cell, id) order: the state itself, or (slots kept by the last
+  // rebuild) a copy through the index list in B, which is free between steps
+  if (!st.full) {
+    launch_view(d->dev, st_);
+    CK(cudaGetLastError());
+  }
+  const Particles& A = st.full ? d->dev.A : d->dev.B;
   if (frac || vel) {
-    // gather the AoS arrays on the device (into the neighbour-list storage, which the next
-    // step rewrites), then copy each array once
-    float* sf = reinterpret_cast<float*>(d->dev.nb);
+    // gather the AoS arrays on the device (into the transfer staging), then copy each array
+    // once
+    if (!d->xfer) CK(dalloc(d, &d->xfer, 2 * (size_t)d->desc.capacity * D));
+    float* sf = d->xfer;
     float* sv = sf + (size_t)n * D;
-    launch_egest(d->dev, frac ? sf : nullptr, vel ? sv : nullptr, (unsigned)n, st_);
+    launch_egest(d->dev, A, frac ? sf : nullptr, vel ? sv : nullptr, (unsigned)n, st_);
     CK(cudaGetLastError());
     if (frac) CK(cudaMemcpyAsync(frac, sf, n * D * sizeof(float), cudaMemcpyDeviceToHost, st_));
     if (vel) CK(cudaMemcpyAsync(vel, sv, n * D * sizeof(float), cudaMemcpyDeviceToHost, st_));
@@ -1277,7 +1373,7 @@ sphbuf_status sphbuf_read_positions(sphbuf_domain_t d, double* pos, uint64_t cap
   StepState st;
   sphbuf_status s = read_state(d, &st);
   if (s != SPHBUF_OK) return s;
-  const uint64_t n = st.n;
+  const uint64_t n = st.n_live;
   if (n_out) *n_out = n;
   if (!pos || !n) return SPHBUF_OK;
   if (n > cap) return fail(d, SPHBUF_ERR_CAPACITY, "host array smaller than the particle count");
@@ -1398,6 +1494,7 @@ struct sphbuf_batch {
   int cpw = 4;
   // persistent form of the default step (one cooperative launch, grid barriers)
   bool persistent = false;
+  bool kin_step = false;  // the step being enqueued is kinematic (its rebuild sorts)
   long long spin_limit = 1ll << 24;
   unsigned* d_bar = nullptr;
   int pgrid = 0;
@@ -1499,7 +1596,7 @@ static int batch_launch_k(sphbuf_batch* b, Kern k, bool fused, int sub) {
     case K_BUFFER_FULL:
       return launch_batch_buffer(k, b->dim, bd, n, b->rot, b->thr[k], b->cpw, b->stream);
     default:
-      return launch_batch_cells(k, b->dim, bd, n, b->thr[k], b->stream);
+      return launch_batch_cells(k, b->dim, bd, n, b->thr[k], b->stream, b->kin_step);
   }
 }
 
@@ -1524,6 +1621,7 @@ static int batch_launch(sphbuf_batch* b, Kern k, bool fused = false, int sub = 0
 static int batch_enqueue_step(sphbuf_batch* b, unsigned phases, bool timed) {
   cudaStream_t s = b->stream;
   const bool fused = fused_decisions(phases, b->rot);
+  b->kin_step = (phases & SPHBUF_PHASE_KINEMATIC) != 0;
   int k = 0;
   if (b->persistent && !timed && !b->ktime && phases == SPHBUF_STEP_DEFAULT) {
     PersistDev p{};
@@ -1698,8 +1796,11 @@ static bool batch_phases_ok(unsigned phases) {
 sphbuf_status sphbuf_batch_step(sphbuf_batch_t b, int nsteps, unsigned phases) {
   if (!b || nsteps < 0) return SPHBUF_ERR_INVALID_ARG;
   if (!batch_phases_ok(phases)) return batch_fail(b, SPHBUF_ERR_INVALID_ARG, "bad phase mask");
-  for (sphbuf_domain* d : b->doms)
+  for (sphbuf_domain* d : b->doms) {
     if (d->need_rebuild) return batch_fail(b, SPHBUF_ERR_STATE, "a domain was rewritten after batching");
+    if (d->dev.P.reuse && (phases & (SPHBUF_PHASE_FULL_CHECK | SPHBUF_PHASE_BUFFER_KERNEL)))
+      return batch_fail(b, SPHBUF_ERR_INVALID_ARG, "kept neighbour lists need the decisions fused into the drift");
+  }
   return batch_run(b, nsteps, phases, false, nullptr);
 }
 

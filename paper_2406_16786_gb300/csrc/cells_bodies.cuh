@@ -117,8 +117,24 @@ __device__ __forceinline__ void scan_down_occ_body(unsigned* __restrict__ cnt, c
     if (v[q]) occ_list[orun++] = (unsigned)(base + q);
 }
 
-__device__ __forceinline__ void hist_body(const DomainDev& d, unsigned bid, unsigned nblk) {
+// force_full: this step's rebuild must sort (kinematic steps and the commit's rebuild);
+// otherwise, with kept neighbour lists, the first thread decides: a full rebuild once twice
+// the largest drift path since the last one exceeds the lists' skin (a pair may then have
+// come within 2h unlisted) or after reuse_max steps, else the slots keep their order.
+__device__ __forceinline__ void hist_body(const DomainDev& d, unsigned bid, unsigned nblk, int force_full) {
   if (d.st->status) return;
+  if (bid == 0 && threadIdx.x == 0) {
+    StepState* st = d.st;
+    int full = 1;
+    if (d.P.reuse && !force_full) {
+      const float path = __uint_as_float(st->path_bits);
+      full = (2.f * path > d.P.skin || st->since_full + 1 >= (unsigned)d.P.reuse_max) ? 1 : 0;
+    }
+    st->full = full;
+    st->path_bits = 0u;
+    st->since_full = full ? 0u : st->since_full + 1u;
+    if (full) st->list_builds += 1;
+  }
   rank_injections(d, bid, nblk);
   const unsigned n = d.st->n + d.st->n_inj;
   const unsigned lane = threadIdx.x & 31u;
@@ -128,6 +144,7 @@ __device__ __forceinline__ void hist_body(const DomainDev& d, unsigned bid, unsi
     // scatter ranks each cell's particles by id)
     const bool dead = d.B.label[i] == kDead;
     const int c = d.B.cell[i];
+    if (!SPHBUF_IN_BOUNDS(d, dead || (c >= 0 && c < d.g.ncell), 10, i)) return;
     const unsigned act = __activemask();
     const unsigned peers = __match_any_sync(act, dead ? 0xFFFFFFFFu : (unsigned)c);
     const int leader = __ffs(peers) - 1;
@@ -147,19 +164,54 @@ __device__ __forceinline__ void keys_body(const DomainDev& d, unsigned bid, unsi
   }
 }
 
+// The particle's label after the relabel of Algorithms 2-3 (in-box particles join the
+// outflow / bidirectional buffer, others leave it).
+template <int D>
+__device__ __forceinline__ uint8_t relabelled(const DomainDev& d, const int c[3], const float f[3], uint8_t lab) {
+  for (int q = 0; q < d.nrelabel; ++q) {
+    const BufDev& b = d.bufs[d.relabel_ids[q]];
+    const bool near = c[0] >= b.box_lo[0] && c[0] <= b.box_hi[0] && c[1] >= b.box_lo[1] && c[1] <= b.box_hi[1] &&
+                      c[2] >= b.box_lo[2] && c[2] <= b.box_hi[2];
+    if (!near && lab != (uint8_t)b.label) continue;
+    float X[3];
+    local_coords<D>(b, c, f, d.g.cs, X, D);
+    if (in_box<D>(b, X))
+      lab = (uint8_t)b.label;
+    else if (lab == (uint8_t)b.label)
+      lab = 0;
+  }
+  return lab;
+}
+
+// Full rebuild: A[cell_start + rank] = B[i], rank = the particle's place by id in its cell,
+// relabelled on the way; dead particles are dropped; the index list is the identity.
+// Kept slots (kept neighbour lists, no full rebuild this step): A[i] = B[i] for every slot,
+// dead ones included (their position copy is put far outside the grid, so listed dead slots
+// add nothing), and the index list takes each live slot at its sorted place.
 template <int D>
 __device__ __forceinline__ void scatter_body(const DomainDev& d, unsigned bid, unsigned nblk) {
   if (d.st->status) return;
   const unsigned n = d.st->n + d.st->n_inj;
+  const bool full = d.st->full != 0;
   const Grid& g = d.g;
   for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
-    if (d.slot[i] == kNoSlot) continue;
+    const bool live = d.slot[i] != kNoSlot;
+    if (full && !live) continue;
     const int lin = d.B.cell[i];
-    const unsigned s0 = d.cell_start[lin], s1 = d.cell_start[lin + 1];
-    const unsigned my = d.B.id[i];
-    unsigned rank = 0;
-    for (unsigned p = s0; p < s1; ++p) rank += SPHBUF_LDG(d.tmp_id + p) < my;
-    const unsigned dst = s0 + rank;
+    unsigned dst = i;
+    if (live) {
+      const unsigned s0 = d.cell_start[lin], s1 = d.cell_start[lin + 1];
+      const unsigned my = d.B.id[i];
+      unsigned rank = 0;
+      for (unsigned p = s0; p < s1; ++p) rank += SPHBUF_LDG(d.tmp_id + p) < my;
+      if (!SPHBUF_IN_BOUNDS(d, s0 + rank < s1, 8, s0 + rank)) continue;
+      if (full) {
+        dst = s0 + rank;
+        d.order[dst] = dst;
+      } else {
+        d.order[s0 + rank] = i;
+      }
+    }
     float f[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f};
     d.A.cell[dst] = lin;
 #pragma unroll
@@ -171,28 +223,18 @@ __device__ __forceinline__ void scatter_body(const DomainDev& d, unsigned bid, u
     }
     const float rho = d.B.rho[i];
     d.A.rho[dst] = rho;
-    d.A.id[dst] = my;
+    d.A.id[dst] = d.B.id[i];
+    d.A.path[dst] = full ? 0.f : d.B.path[i];
     int c[3];
     cell_coords(lin, g, c);
-    d.pos4[dst] = make_float4(f[0], f[1], f[2], (float)c[0]);
-    d.vel4[dst] = make_float4(v[0], v[1], v[2], rho);
-    // Algorithms 2-3, after the rebuild: in-box particles join the buffer, others leave it
-    uint8_t lab = d.B.label[i];
-    if (d.nrelabel) {
-      for (int q = 0; q < d.nrelabel; ++q) {
-        const BufDev& b = d.bufs[d.relabel_ids[q]];
-        const bool near = c[0] >= b.box_lo[0] && c[0] <= b.box_hi[0] && c[1] >= b.box_lo[1] &&
-                          c[1] <= b.box_hi[1] && c[2] >= b.box_lo[2] && c[2] <= b.box_hi[2];
-        if (!near && lab != (uint8_t)b.label) continue;
-        float X[3];
-        local_coords<D>(b, c, f, g.cs, X, D);
-        if (in_box<D>(b, X))
-          lab = (uint8_t)b.label;
-        else if (lab == (uint8_t)b.label)
-          lab = 0;
-      }
+    if (live) {
+      d.pos4[dst] = make_float4(f[0], f[1], f[2], __uint_as_float(pack_cell(c[0], c[1], c[2])));
+      d.A.label[dst] = d.nrelabel ? relabelled<D>(d, c, f, d.B.label[i]) : d.B.label[i];
+    } else {
+      d.pos4[dst] = make_float4(0.f, 0.f, 0.f, __uint_as_float(pack_cell(kMaxCellsX - 1, kMaxCellsY - 1, kMaxCellsZ - 1)));
+      d.A.label[dst] = kDead;
     }
-    d.A.label[dst] = lab;
+    d.vel4[dst] = make_float4(v[0], v[1], v[2], rho);
   }
 }
 
@@ -200,7 +242,10 @@ __device__ __forceinline__ void finalize_body(const DomainDev& d, int count_step
   StepState* st = d.st;
   if (st->status) return;
   if (bid == 0 && threadIdx.x == 0) {
-    st->n = d.cell_start[d.g.ncell];
+    // slots: the sorted live particles after a full rebuild, the kept slots plus this step's
+    // duplicates otherwise
+    st->n_live = d.cell_start[d.g.ncell];
+    st->n = st->full ? st->n_live : st->n + min(st->n_inj, d.P.list_cap);
     st->next_id += min(st->n_inj, d.P.list_cap);
     // the next step's neighbour pass counts its deferred particles from zero (reset here, in
     // a launch of its own, not by that pass's first block while the others add to it)

@@ -135,6 +135,21 @@ __host__ __device__ inline void advance_rotation(RotDev& q) {
   for (int e = 0; e < 9; ++e) q.Q[e] = T[e];
 }
 
+// Cell coordinates packed into 32 bits (x: bits 0-10, y: bits 11-21, z: bits 22-31), carried
+// as the .w word of the position copies the neighbour passes read (pos4, wpos4): the geometry
+// of a listed pair comes from both particles' own cells, so a list entry holds only the index.
+// Grids are therefore limited to 2048 x 2048 x 1024 cells.
+constexpr int kMaxCellsX = 2048, kMaxCellsY = 2048, kMaxCellsZ = 1024;
+__host__ __device__ inline unsigned pack_cell(int cx, int cy, int cz) {
+  return (unsigned)cx | ((unsigned)cy << 11) | ((unsigned)cz << 22);
+}
+// x of a packed cell as a float (exact: the 11 bits placed in the mantissa of 2^23, minus 2^23)
+__device__ __forceinline__ float packed_cx(unsigned pc) {
+  return __int_as_float(0x4B000000 | (int)(pc & 0x7FFu)) - 8388608.f;
+}
+__device__ __forceinline__ int packed_cy(unsigned pc) { return (int)((pc >> 11) & 0x7FFu); }
+__device__ __forceinline__ int packed_cz(unsigned pc) { return (int)(pc >> 22); }
+
 struct Grid {
   int dim;
   int nx, ny, nz;
@@ -148,6 +163,12 @@ struct Phys {
   float tvf_lambda;  // transport velocity (Eq. (10)): p_max = lambda rho0 v_max^2; 0 = off
   float dt_ac;       // acoustic step of the dual-criteria scheme (dt / dual_n)
   int dual_n;        // acoustic steps per advection step; 0 = single-rate kick-drift
+  // neighbour lists kept over steps (0 = rebuilt every step): lists hold the pairs within
+  // list_r2 = (2h + skin)^2 and are rebuilt when twice the largest drift since the last full
+  // build exceeds the skin, or after reuse_max steps
+  int reuse;
+  float list_r2, skin;
+  int reuse_max;
   double rho0_d, c0sq_d, dt_d, p_bg_d;
   double lo_d[3], cs_d;  // grid origin and cell size in FP64 (frames of rotating buffers)
   unsigned capacity;
@@ -175,6 +196,14 @@ struct StepState {
   double wk_pd[kMaxBuffers];       // Windkessel distal pressure P_d (Eq. (31) split)
   unsigned vmax_bits;              // largest particle speed of the current force pass (float bits)
   float p_max;                     // Eq. (10) background pressure of the current step
+  // kept neighbour lists: full = the last rebuild sorted the state (its next step searches
+  // every particle's neighbours); otherwise the slots kept their order, dead particles their
+  // slots, and the index list `order` holds the live particles sorted by (cell, id)
+  int full;
+  unsigned n_live;                 // live particles (n counts slots)
+  unsigned path_bits;              // largest drift path since the last full build (float bits)
+  unsigned since_full;             // steps since the last full build
+  unsigned long long list_builds;  // full builds so far
 };
 
 struct Particles {
@@ -184,6 +213,7 @@ struct Particles {
   float* rho;
   unsigned* id;
   uint8_t* label;
+  float* path;  // drift path length since the last full neighbour-list build
 };
 
 struct Walls {

@@ -21,7 +21,7 @@ struct DomainDev {
   float4* pos_b;          // dual-criteria scheme: second copy of pos4 and vr4 (acoustic steps
   float4* vr_b;           //   alternate between the two), and the viscous acceleration of
   float4* av;             //   the advection step
-  unsigned* io;           // 4 words: host-transfer checks (error bits, largest id)
+  unsigned* io;           // 8 words: host-transfer checks (error bits, largest id), bounds-check record
   unsigned* deferred;     // particles left by the fluid density pass (buffer or overflowed list)
   float4* pos4;           // A-order copies for the neighbour passes: (fx, fy, fz, cell x)
   float4* vel4;           //   and (vx, vy, vz, rho); written by the rebuild scatter
@@ -43,6 +43,9 @@ struct DomainDev {
   uint4* seg_range;       // (cell_start[lin0], cell_start[lin1], lin0, buffer) of each segment
   int nseg;
   const unsigned* cand_mask;  // per cell: bit k set when the cell is a candidate cell of buffer k
+  const uint8_t* s_mask;      // per cell: 1 where kept lists are rebuilt every step (candidate
+                              //   cells and two rings of cells around them)
+  unsigned* order;            // live particles' slots sorted by (cell, id) (kept lists)
   StepState* st;
   long long ncell_pad;
   int scan_tiles;
@@ -92,6 +95,38 @@ struct PersistDev {
 int persistent_grid(int dim, bool tvf);  // resident blocks of the persistent step (0: error)
 cudaError_t launch_persistent(const PersistDev& p, int dim, bool tvf, int grid, cudaStream_t s);
 
+// Bounds-checked build (compiled with -DSPHBUF_CHECK, see build.py): SPHBUF_IN_BOUNDS(d, cond,
+// site, index) is cond; when cond is false the first failing site and index go to io[2] and
+// io[3] and SPHBUF_ERR_BOUNDS is latched, and the caller skips the access.  Without the flag
+// the checks compile to nothing.  Sites: 1 fluid candidate, 2 wall candidate (neighbour
+// search); 3 fluid entry, 4 wall entry (list visit); 5 cell walk; 6 particle cell; 7 deferred
+// particle; 8 index-list place; 9 cell of the candidate mask; 10 rebuild cell.
+// SPHBUF_IN_BOUNDS_AT(d, cond, site, index, who) also records the particle `who` with its
+// list count, cell and the state's sort flag (io[4..7]).
+#ifdef SPHBUF_CHECK
+__device__ __forceinline__ bool bounds_ok(const DomainDev& d, bool cond, unsigned site, unsigned index,
+                                          unsigned who) {
+  if (!cond) {
+    if (atomicCAS(&d.io[2], 0u, site) == 0u) {
+      d.io[3] = index;
+      d.io[4] = who;
+      if (who != kNoSlot) {
+        d.io[5] = d.nb_cnt[who];
+        d.io[6] = (unsigned)d.A.cell[who];
+      }
+      d.io[7] = (unsigned)d.st->full | ((unsigned)d.st->since_full << 8);
+    }
+    latch(d.st, 8 /* SPHBUF_ERR_BOUNDS */);
+  }
+  return cond;
+}
+#define SPHBUF_IN_BOUNDS(d, cond, site, index) bounds_ok((d), (cond), (site), (unsigned)(index), kNoSlot)
+#define SPHBUF_IN_BOUNDS_AT(d, cond, site, index, who) bounds_ok((d), (cond), (site), (unsigned)(index), (who))
+#else
+#define SPHBUF_IN_BOUNDS(d, cond, site, index) true
+#define SPHBUF_IN_BOUNDS_AT(d, cond, site, index, who) true
+#endif
+
 // Copies one domain descriptor into shared memory (whole block; ends with a barrier).
 __device__ __forceinline__ void load_domain(DomainDev& dst, const DomainDev* src) {
   const int words = (int)(sizeof(DomainDev) / sizeof(int));
@@ -108,7 +143,8 @@ int launch_batch_sph(Kern k, int dim, const BatchDev& b, int nblocks, cudaStream
                      int threads);
 int launch_batch_buffer(Kern k, int dim, const BatchDev& b, int nblocks, bool rot, int threads, int cpw,
                         cudaStream_t s);
-int launch_batch_cells(Kern k, int dim, const BatchDev& b, int nblocks, int threads, cudaStream_t s);
+int launch_batch_cells(Kern k, int dim, const BatchDev& b, int nblocks, int threads, cudaStream_t s,
+                       bool force_full = false);
 int batch_threads(Kern k);  // threads per block of the batched kernels whose block size is fixed
 bool batch_tunable(Kern k);  // may the autotuner choose the block size of this kernel?
 
@@ -122,15 +158,19 @@ int launch_dual(const DomainDev& d, bool fused, cudaStream_t s);  // viscous, ac
 int launch_identify(const DomainDev& d, cudaStream_t s);
 int launch_decide(const DomainDev& d, bool full_domain, cudaStream_t s);
 // cells (kernels_cells.cu)
-int launch_rebuild(const DomainDev& d, bool count_step, cudaStream_t s);
+// force_full: sort the state whatever the kept-list policy says (kinematic steps, commits)
+int launch_rebuild(const DomainDev& d, bool count_step, bool force_full, cudaStream_t s);
 int finalize_blocks(const DomainDev& d);  // blocks of the finalize pass (candidate segments / 256)
 // Host transfers: the AoS frac / vel arrays staged in device memory <-> the SoA state.
 // ingest: B <- staged arrays (cell, rho, id, label already copied), with the checks of
 // sphbuf_write_particles (io[0] bits: 1 cell, 2 offset, 4 label; io[1] = largest id).
 void launch_ingest(const DomainDev& d, const float* frac, const float* vel, unsigned n, int ids_given,
                    int labels_given, int nbuf, cudaStream_t s);
-// egest: staged AoS arrays <- A (the sorted state).
-void launch_egest(const DomainDev& d, float* frac, float* vel, unsigned n, cudaStream_t s);
+// egest: staged AoS arrays <- P (the sorted state: A, or B after launch_view).
+void launch_egest(const DomainDev& d, const Particles& P, float* frac, float* vel, unsigned n, cudaStream_t s);
+// view: B <- the live particles of A in (cell, id) order through the index list (for reads of a
+// state whose slots were kept by the last rebuild).
+void launch_view(const DomainDev& d, cudaStream_t s);
 // Pipelined host transfers.  ingest_staged: B <- arrays of n particles staged in device memory
 // (id / label NULL: 0..n-1 / 0), with the checks of sphbuf_write_particles; a failed check
 // latches SPHBUF_ERR_INVALID_ARG and leaves the domain with no particles, otherwise n and

@@ -147,7 +147,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down_occ(DomainDev d) {
   if (d.st->status) return;
   scan_down_occ_body(d.cnt, d.scan_part, d.scan_part_occ, d.cell_start, d.occ_list, blockIdx.x);
 }
-__global__ void __launch_bounds__(256) k_hist(DomainDev d) { hist_body(d, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(256) k_hist(DomainDev d, int force_full) {
+  hist_body(d, blockIdx.x, gridDim.x, force_full);
+}
 __global__ void __launch_bounds__(256) k_keys(DomainDev d) { keys_body(d, blockIdx.x, gridDim.x); }
 template <int D>
 __global__ void __launch_bounds__(256) k_scatter(DomainDev d) {
@@ -177,11 +179,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down_occ_batch(BatchDev b
   scan_down_occ_body(d->cnt, d->scan_part, d->scan_part_occ, d->cell_start, d->occ_list, (unsigned)m.y);
 }
 // (the particle kernels of the rebuild take any block size up to 512: the autotuner's)
-__global__ void __launch_bounds__(512) k_hist_batch(BatchDev b) {
+__global__ void __launch_bounds__(512) k_hist_batch(BatchDev b, int force_full) {
   __shared__ DomainDev sd;
   const int4 m = b.map[blockIdx.x];
   load_domain(sd, b.doms + m.x);
-  hist_body(sd, (unsigned)m.y, (unsigned)m.z);
+  hist_body(sd, (unsigned)m.y, (unsigned)m.z, force_full);
 }
 __global__ void __launch_bounds__(512) k_keys_batch(BatchDev b) {
   __shared__ DomainDev sd;
@@ -270,6 +272,8 @@ __global__ void k_ingest_finish(DomainDev d, unsigned n, unsigned next_id) {
   StepState* st = d.st;
   const bool ok = n == 0 || (d.io[0] == 0 && next_id > d.io[1]);
   st->n = ok ? n : 0u;
+  st->n_live = st->n;
+  st->full = 1;
   st->n_inj = 0;
   st->n_del = 0;
   st->next_id = next_id;
@@ -281,40 +285,64 @@ __global__ void __launch_bounds__(256) k_egest_staged(DomainDev d, int* __restri
                                                       unsigned* __restrict__ id, uint8_t* __restrict__ label,
                                                       unsigned* n_out, unsigned cap) {
   const int D = d.g.dim;
-  const unsigned n = d.st->n;
+  // the live particles in (cell, id) order: the state itself after a full rebuild, through
+  // the index list when the slots were kept
+  const unsigned n = d.st->n_live;
+  const bool full = d.st->full != 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) *n_out = n;
   const unsigned m = min(n, cap);
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-    cell[i] = d.A.cell[i];
+    const unsigned o = full ? i : d.order[i];
+    cell[i] = d.A.cell[o];
     for (int x = 0; x < D; ++x) {
-      frac[(size_t)i * D + x] = d.A.f[x][i];
-      vel[(size_t)i * D + x] = d.A.v[x][i];
+      frac[(size_t)i * D + x] = d.A.f[x][o];
+      vel[(size_t)i * D + x] = d.A.v[x][o];
     }
-    rho[i] = d.A.rho[i];
-    id[i] = d.A.id[i];
-    label[i] = d.A.label[i];
+    rho[i] = d.A.rho[o];
+    id[i] = d.A.id[o];
+    label[i] = d.A.label[o];
   }
 }
 
-__global__ void __launch_bounds__(256) k_egest(DomainDev d, float* __restrict__ frac, float* __restrict__ vel,
-                                               unsigned n) {
+// B[k] = A[order[k]] for the live particles (a sorted copy of a state whose slots were kept;
+// B is free between steps).
+__global__ void __launch_bounds__(256) k_view(DomainDev d) {
+  const int D = d.g.dim;
+  const unsigned n = d.st->n_live;
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const unsigned o = d.order[k];
+    d.B.cell[k] = d.A.cell[o];
+    for (int x = 0; x < D; ++x) {
+      d.B.f[x][k] = d.A.f[x][o];
+      d.B.v[x][k] = d.A.v[x][o];
+    }
+    d.B.rho[k] = d.A.rho[o];
+    d.B.id[k] = d.A.id[o];
+    d.B.label[k] = d.A.label[o];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_egest(DomainDev d, Particles P, float* __restrict__ frac,
+                                               float* __restrict__ vel, unsigned n) {
   const int D = d.g.dim;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     for (int x = 0; x < D; ++x) {
-      if (frac) frac[(size_t)i * D + x] = d.A.f[x][i];
-      if (vel) vel[(size_t)i * D + x] = d.A.v[x][i];
+      if (frac) frac[(size_t)i * D + x] = P.f[x][i];
+      if (vel) vel[(size_t)i * D + x] = P.v[x][i];
     }
   }
 }
 
 __global__ void k_decode(DomainDev d, double* out, double lo0, double lo1, double lo2, double cs) {
-  const unsigned n = d.st->n;
+  const unsigned n = d.st->n_live;
+  const bool full = d.st->full != 0;
   const int D = d.g.dim;
   const double lo[3] = {lo0, lo1, lo2};
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned o = full ? i : d.order[i];
     int c[3];
-    cell_coords(d.A.cell[i], d.g, c);
-    for (int x = 0; x < D; ++x) out[(size_t)i * D + x] = lo[x] + (double)c[x] * cs + (double)d.A.f[x][i];
+    cell_coords(d.A.cell[o], d.g, c);
+    for (int x = 0; x < D; ++x) out[(size_t)i * D + x] = lo[x] + (double)c[x] * cs + (double)d.A.f[x][o];
   }
 }
 
@@ -367,9 +395,9 @@ __global__ void k_order_raw(const int32_t* cell, const uint32_t* id, unsigned n,
 
 int finalize_blocks(const DomainDev& d) { return d.nseg > 256 ? (d.nseg + 255) / 256 : 1; }
 
-int launch_rebuild(const DomainDev& d, bool count_step, cudaStream_t s) {
+int launch_rebuild(const DomainDev& d, bool count_step, bool force_full, cudaStream_t s) {
   const int blocks = d.sm_count * 8;
-  k_hist<<<blocks, 256, 0, s>>>(d);
+  k_hist<<<blocks, 256, 0, s>>>(d, force_full ? 1 : 0);
   k_scan_reduce_occ<<<d.scan_tiles, kScanThreads, 0, s>>>(d);
   k_scan_top_occ<<<1, 1024, 0, s>>>(d);
   k_scan_down_occ<<<d.scan_tiles, kScanThreads, 0, s>>>(d);
@@ -382,10 +410,11 @@ int launch_rebuild(const DomainDev& d, bool count_step, cudaStream_t s) {
   return 7;
 }
 
-int launch_batch_cells(Kern k, int dim, const BatchDev& b, int nblocks, int threads, cudaStream_t s) {
+int launch_batch_cells(Kern k, int dim, const BatchDev& b, int nblocks, int threads, cudaStream_t s,
+                       bool force_full) {
   switch (k) {
     case K_HIST:
-      k_hist_batch<<<nblocks, threads, 0, s>>>(b);
+      k_hist_batch<<<nblocks, threads, 0, s>>>(b, force_full ? 1 : 0);
       return 1;
     case K_SCAN_REDUCE:
       k_scan_reduce_occ_batch<<<nblocks, kScanThreads, 0, s>>>(b);
@@ -462,9 +491,11 @@ void launch_egest_staged(const DomainDev& d, int* cell, float* frac, float* vel,
   k_egest_staged<<<d.sm_count * 4, 256, 0, s>>>(d, cell, frac, vel, rho, id, label, n_out, cap);
 }
 
-void launch_egest(const DomainDev& d, float* frac, float* vel, unsigned n, cudaStream_t s) {
-  k_egest<<<d.sm_count * 4, 256, 0, s>>>(d, frac, vel, n);
+void launch_egest(const DomainDev& d, const Particles& P, float* frac, float* vel, unsigned n, cudaStream_t s) {
+  k_egest<<<d.sm_count * 4, 256, 0, s>>>(d, P, frac, vel, n);
 }
+
+void launch_view(const DomainDev& d, cudaStream_t s) { k_view<<<d.sm_count * 4, 256, 0, s>>>(d); }
 
 void launch_decode_positions(const DomainDev& d, double* pos_out, const double lo[3], double cs,
                              cudaStream_t s) {

@@ -92,7 +92,7 @@ __device__ __forceinline__ void run_phase(int ph, const DomainDev& d, unsigned l
       force_body<D, TVF>(d, lb, nb, true);
       break;
     case P_HIST:
-      hist_body(d, lb, nb);
+      hist_body(d, lb, nb, 0);
       break;
     case P_SCAN_REDUCE:
       if (!d.st->status) scan_reduce_occ_body(d.cnt, d.scan_part, d.scan_part_occ, lb);

@@ -104,12 +104,14 @@ __device__ __forceinline__ void force_term(const Phys& P, bool wall, float rx, f
 }
 
 // Calls fn(wall, j, rx, ry, rz) for every particle of the 3^d cells around cell c (global
-// memory; the per-particle fallback path).
+// memory; the per-particle fallback path).  The cell ranges index the sorted particles, or
+// the index list of live slots when the last rebuild kept the slots.
 template <int D, typename Fn>
 __device__ __forceinline__ void for_each_near(const DomainDev& d, const int c[3], const float fi[3], Fn&& fn,
                                               unsigned first = 0, unsigned stride = 1) {
   const Grid& g = d.g;
   const float cs = g.cs;
+  const bool indirect = d.P.reuse && !d.st->full;
   const int x0 = max(c[0] - 1, 0), x1 = min(c[0] + 1, g.nx - 1);
   for (int wall = 0; wall < 2; ++wall) {
     const unsigned* start = wall ? d.W.start : d.cell_start;
@@ -123,7 +125,9 @@ __device__ __forceinline__ void for_each_near(const DomainDev& d, const int c[3]
         if (y < 0 || y >= g.ny) continue;
         const int rb = (z * g.ny + y) * g.nx;
         const unsigned j1 = start[rb + x1 + 1];
-        for (unsigned j = start[rb + x0] + first; j < j1; j += stride) {
+        for (unsigned k = start[rb + x0] + first; k < j1; k += stride) {
+          const unsigned j = (indirect && !wall) ? d.order[k] : k;
+          if (!SPHBUF_IN_BOUNDS(d, wall ? j < d.W.start[g.ncell] : j < d.st->n, 5, j)) continue;
           const int xoff = cell[j] - rb - c[0];
           const float rx = fi[0] - F[0][j] - (float)xoff * cs;
           const float ry = fi[1] - (float)dy * cs - F[1][j];
@@ -145,6 +149,21 @@ __device__ __forceinline__ void drift_store(const DomainDev& d, bool fused, unsi
                                             const float fi[3], const float v[3], const float adv[3], float rho,
                                             uint8_t lab) {
   const Grid& g = d.g;
+  if (lab == kDead) {
+    // a slot kept (with kept neighbour lists) for a particle deleted since the last full
+    // rebuild: it stays dead and in place until that rebuild drops it
+    d.B.cell[i] = (c[2] * g.ny + c[1]) * g.nx + c[0];
+#pragma unroll
+    for (int x = 0; x < D; ++x) {
+      d.B.f[x][i] = fi[x];
+      d.B.v[x][i] = 0.f;
+    }
+    d.B.rho[i] = d.P.rho0;
+    d.B.id[i] = d.A.id[i];
+    d.B.label[i] = kDead;
+    d.B.path[i] = 0.f;
+    return;
+  }
   int cn[3] = {c[0], c[1], c[2]};
   float fn[3] = {fi[0], fi[1], fi[2]};
   bool finite = true;
@@ -161,7 +180,9 @@ __device__ __forceinline__ void drift_store(const DomainDev& d, bool fused, unsi
   }
   const unsigned id = d.A.id[i];
   if (fused) {
-    const unsigned bits = SPHBUF_LDG(d.cand_mask + (c[2] * g.ny + c[1]) * g.nx + c[0]);
+    const int lin0 = (c[2] * g.ny + c[1]) * g.nx + c[0];
+    const unsigned bits =
+        SPHBUF_IN_BOUNDS(d, lin0 >= 0 && lin0 < g.ncell, 9, lin0) ? SPHBUF_LDG(d.cand_mask + lin0) : 0u;
     decide_fused<D>(d, __activemask(), n, bits, i, id, lab, cn, fn, inside, v, rho);
   }
   const int lin = inside ? (cn[2] * g.ny + cn[1]) * g.nx + cn[0] : 0;
@@ -174,6 +195,16 @@ __device__ __forceinline__ void drift_store(const DomainDev& d, bool fused, unsi
   d.B.rho[i] = rho;
   d.B.id[i] = id;
   d.B.label[i] = lab;
+  if (d.P.reuse) {
+    // drift path since the last full list build, and its largest value this step
+    float a2 = adv[0] * adv[0] + adv[1] * adv[1];
+    if (D == 3) a2 += adv[2] * adv[2];
+    const float path = d.A.path[i] + sqrtf(a2) * d.P.dt;
+    d.B.path[i] = path;
+    const unsigned am = __activemask();
+    const unsigned wmax = __reduce_max_sync(am, __float_as_uint(path));
+    if ((threadIdx.x & 31) == __ffs(am) - 1) atomicMax(&d.st->path_bits, wmax);
+  }
 }
 
 // Kick, boundary velocity, flux, drift for centre particle i with acceleration a.  With TVF
@@ -185,7 +216,7 @@ __device__ __forceinline__ void finish_force(const DomainDev& d, bool fused, uns
                                              const float tb[3]) {
   const Phys& P = d.P;
   float v[3] = {vi[0] + a[0] * P.dt, vi[1] + a[1] * P.dt, D == 3 ? vi[2] + a[2] * P.dt : 0.f};
-  if (lab != 0) {
+  if (lab != 0 && lab != kDead) {
     const int k = (int)lab - 1;
     const BufDev& b = d.bufs[k];
     if (b.vel_bc) {
@@ -230,7 +261,7 @@ __device__ __forceinline__ void finish_force(const DomainDev& d, bool fused, uns
 
 __device__ __forceinline__ float boundary_pressure2(const DomainDev& d, uint8_t lab, float p_i) {
   // Eq. (18): 2 p_b with p_b(t) prescribed, or p_b = p_i for velocity buffers (Sec. 4.2)
-  if (lab == 0) return 0.f;
+  if (lab == 0 || lab == kDead) return 0.f;
   const int k = (int)lab - 1;
   return 2.f * (d.bufs[k].vel_bc ? p_i : d.st->pb[k]);
 }
@@ -265,38 +296,39 @@ __device__ void force_one(const DomainDev& d, bool fused, unsigned i, unsigned n
 }
 
 // ---------------------------------------------------------------- neighbour lists
-// Packed neighbour: index j (25 bits) | dy + 1 (2 bits, from bit 25) | dz + 1 (2 bits, from
-// bit 27) | wall (1 bit, bit 31); (dy, dz) is the row of j's cell relative to the particle's.
-// The x-cell of j is pos4[j].w.
+// Packed neighbour: index j (bits 0-30) | wall (bit 31).  The pair's geometry comes from the
+// cells packed in both particles' position copies (pos4.w), so an entry stays valid when
+// either particle moves to another cell (lists kept over several steps).
 
-// Unpacks one entry of the particle at (cell x cxf, offset fi) and calls fn(wall, j, rx, ry, rz).
+// Unpacks one entry of the particle in packed cell ci at offset fi and calls
+// fn(wall, j, rx, ry, rz), r = r_i - r_j.
 template <int D, typename Fn>
-__device__ __forceinline__ void visit_entry(const DomainDev& d, unsigned ent, float cxf, const float fi[3],
-                                            Fn&& fn) {
+__device__ __forceinline__ void visit_entry(const DomainDev& d, unsigned ent, unsigned ci, const float fi[3],
+                                            Fn&& fn, unsigned who = kNoSlot, unsigned site = 3) {
   const float cs = d.g.cs;
-  const unsigned j = ent & 0x1FFFFFFu;
+  const unsigned j = ent & 0x7FFFFFFFu;
   const int wall = (int)(ent >> 31);
-  const int dy = (int)((ent >> 25) & 3u) - 1;
-  const int dz = (D == 3) ? (int)((ent >> 27) & 3u) - 1 : 0;
+  if (!SPHBUF_IN_BOUNDS_AT(d, wall ? j < d.W.start[d.g.ncell] : j < d.st->n, site + 100 * wall, j, who)) return;
   const float4 p = SPHBUF_LDG((wall ? d.wpos4 : d.pos4) + j);
-  const float rx = fi[0] - p.x - (p.w - cxf) * cs;
-  const float ry = fi[1] - (float)dy * cs - p.y;
-  const float rz = (D == 3) ? fi[2] - (float)dz * cs - p.z : 0.f;
+  const unsigned cj = __float_as_uint(p.w);
+  const float rx = fi[0] - p.x - (packed_cx(cj) - packed_cx(ci)) * cs;
+  const float ry = fi[1] - (float)(packed_cy(cj) - packed_cy(ci)) * cs - p.y;
+  const float rz = (D == 3) ? fi[2] - (float)(packed_cz(cj) - packed_cz(ci)) * cs - p.z : 0.f;
   fn(wall, j, rx, ry, rz);
 }
 
 // Calls fn for the cnt listed neighbours of particle i (16-byte loads of 4 entries).  OWN:
 // the list was written by this thread in this kernel, so it is read with coherent loads.
 template <int D, bool OWN = false, typename Fn>
-__device__ __forceinline__ void for_each_listed(const DomainDev& d, unsigned i, int cnt, float cxf, const float fi[3],
-                                                Fn&& fn) {
+__device__ __forceinline__ void for_each_listed(const DomainDev& d, unsigned i, int cnt, unsigned ci, const float fi[3],
+                                                Fn&& fn, unsigned site = 3) {
   const uint4* lst = reinterpret_cast<const uint4*>(d.nb + (size_t)i * d.nb_cap);
   for (int e = 0; e < cnt; e += 4) {
     const uint4 q = OWN ? lst[e >> 2] : SPHBUF_LDG(lst + (e >> 2));
-    visit_entry<D>(d, q.x, cxf, fi, fn);
-    if (e + 1 < cnt) visit_entry<D>(d, q.y, cxf, fi, fn);
-    if (e + 2 < cnt) visit_entry<D>(d, q.z, cxf, fi, fn);
-    if (e + 3 < cnt) visit_entry<D>(d, q.w, cxf, fi, fn);
+    visit_entry<D>(d, q.x, ci, fi, fn, i, site);
+    if (e + 1 < cnt) visit_entry<D>(d, q.y, ci, fi, fn, i, site);
+    if (e + 2 < cnt) visit_entry<D>(d, q.z, ci, fi, fn, i, site);
+    if (e + 3 < cnt) visit_entry<D>(d, q.w, ci, fi, fn, i, site);
   }
 }
 
@@ -308,9 +340,10 @@ __device__ __forceinline__ void density_fluid(const DomainDev& d, unsigned i, in
   const float4 pi = d.pos4[i];
   const float fi[3] = {pi.x, pi.y, pi.z};
   float s = 0.f;
-  for_each_listed<D, OWN>(d, i, cnt, pi.w, fi, [&](int, unsigned, float rx, float ry, float rz) {
-    s += kernel_w(sqrtf(rx * rx + ry * ry + rz * rz) * P.inv_h, P);
-  });
+  for_each_listed<D, OWN>(
+      d, i, cnt, __float_as_uint(pi.w), fi,
+      [&](int, unsigned, float rx, float ry, float rz) { s += kernel_w(sqrtf(rx * rx + ry * ry + rz * rz) * P.inv_h, P); },
+      OWN ? 11 : 12);
   const float4 v = d.vel4[i];
   d.vr4[i] = make_float4(v.x, v.y, v.z, P.rho0 * (s + P.w_self) * P.inv_sum_w0);
 }
@@ -350,67 +383,106 @@ __device__ __forceinline__ void list_append(ListTail& t, bool in, unsigned ent, 
   if (in && (t.cnt & 3) == 0 && t.cnt <= cap) lst[(t.cnt >> 2) - 1] = make_uint4(t.q0, t.q1, t.q2, t.q3);
 }
 
-// Neighbour-list pass: tests every candidate of the 3^d cells once (one 16-byte load each)
-// and appends the in-range ones to the particle's list (contiguous per particle, 16-byte
-// stores of 4 entries, branch-free appends).  (Skipping rows and end cells that cannot hold
-// a neighbour, per particle, was slower: the lanes of a warp rarely agree on the skip.)
+// One particle's neighbour search: tests every candidate of the 3^d cells around cell c once
+// (one 16-byte load each) and appends those within r2max to the particle's list (contiguous
+// per particle, 16-byte stores of 4 entries, branch-free appends); returns the count.
+// INDIRECT: the fluid candidates are read through the index list `order` (kept lists: the
+// slots are not sorted), otherwise the cell ranges index the sorted particles directly.
+// (Skipping rows and end cells that cannot hold a neighbour, per particle, was slower: the
+// lanes of a warp rarely agree on the skip.)
+template <int D, bool INDIRECT>
+__device__ __forceinline__ int search_list(const DomainDev& d, unsigned i, const int c[3], const float4 pi,
+                                           float r2max) {
+  const Grid& g = d.g;
+  const float cs = g.cs;
+  const int cap = d.nb_cap;
+  const float cxf = packed_cx(__float_as_uint(pi.w));
+  uint4* lst = reinterpret_cast<uint4*>(d.nb + (size_t)i * cap);
+  ListTail t{0u, 0u, 0u, 0u, 0};
+  // x of particle i from its grid row's origin: enough for the inclusion test (its rounding,
+  // ~1e-7 of the row length, moves only pairs at the list radius by O(1e-5) of it); the
+  // density and force passes recompute r_ij from the cell offsets
+  const float ox = pi.x + cxf * cs;
+#pragma unroll 1
+  for (int wall = 0; wall < 2; ++wall) {
+    const unsigned* start = wall ? d.W.start : d.cell_start;
+    const float4* P4 = wall ? d.wpos4 : d.pos4;
+#pragma unroll 1
+    for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); ++dz) {
+      const int z = c[2] + dz;
+      if (z < 0 || z >= g.nz) continue;
+#pragma unroll 1
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int y = c[1] + dy;
+        if (y < 0 || y >= g.ny) continue;
+        const int x0 = max(c[0] - 1, 0), x1 = min(c[0] + 1, g.nx - 1);
+        const int rb = (z * g.ny + y) * g.nx;
+        const unsigned tag = (unsigned)wall << 31;
+        const float oy = pi.y - (float)dy * cs;
+        const float oz = (D == 3) ? pi.z - (float)dz * cs : 0.f;
+        const unsigned k1 = SPHBUF_LDG(start + rb + x1 + 1);
+        unsigned k = SPHBUF_LDG(start + rb + x0);
+        for (; k < k1; ++k) {
+          const unsigned j = (INDIRECT && !wall) ? SPHBUF_LDG(d.order + k) : k;
+          if (!SPHBUF_IN_BOUNDS(d, wall ? j < d.W.start[g.ncell] : j < d.st->n, wall ? 2 : 1, j)) continue;
+          const float4 p = SPHBUF_LDG(P4 + j);
+          const float rx = ox - (p.x + packed_cx(__float_as_uint(p.w)) * cs);
+          const float ry = oy - p.y;
+          const float rz = (D == 3) ? oz - p.z : 0.f;
+          const float r2 = rx * rx + ry * ry + rz * rz;
+          list_append(t, r2 < r2max && r2 > 0.f, j | tag, lst, cap);
+        }
+      }
+    }
+  }
+  // the last (cnt mod 4) entries are q(4 - r) .. q3
+  const int r = t.cnt & 3;
+  if (r && t.cnt < cap)
+    lst[t.cnt >> 2] = make_uint4(r == 1 ? t.q3 : (r == 2 ? t.q2 : t.q1), r == 2 ? t.q3 : t.q2, t.q3, 0u);
+  d.nb_cnt[i] = (unsigned)t.cnt;
+  return t.cnt;
+}
+
+// Neighbour-list pass, then Eq. (9) from the list for a fluid particle (deferred otherwise).
+// Lists rebuilt every step (reuse off): every particle searches the sorted cells.  Kept lists
+// (reuse on): after a full rebuild every particle searches (radius 2h + skin, drift paths
+// restart from 0); after a rebuild that kept the slots, only the particles whose cell lies in
+// the every-step region around the buffers (where duplicates appear and parents are recycled)
+// search, through the index list, and the others keep their lists; dead slots are skipped
+// (their density copy is a harmless rho0 at rest, since listed dead slots add nothing).
 template <int D>
 __device__ __forceinline__ void neighbours_body(const DomainDev& d, unsigned bid, unsigned nblk) {
   if (bid == 0 && threadIdx.x == 0) begin_step(d);
   if (d.st->status) return;
   const unsigned n = d.st->n;
   const Grid g = d.g;
-  const float cs = g.cs;
-  const float two_h_sq = d.P.two_h_sq;
-  const int cap = d.nb_cap;
+  const bool reuse = d.P.reuse != 0;
+  const bool full = !reuse || d.st->full != 0;
+  const float r2max = d.P.list_r2;
   for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
-    int c[3];
-    cell_coords(d.A.cell[i], g, c);
-    const float4 pi = d.pos4[i];
-    const float cxf = pi.w;
-    uint4* lst = reinterpret_cast<uint4*>(d.nb + (size_t)i * cap);
-    ListTail t{0u, 0u, 0u, 0u, 0};
-    // x of particle i from its grid row's origin: enough for the inclusion test (its rounding,
-    // ~1e-7 of the row length, moves only pairs at q = 2 - O(1e-5), where W and dW vanish);
-    // the density and force passes recompute r_ij from the cell offsets
-    const float ox = pi.x + cxf * cs;
-#pragma unroll 1
-    for (int wall = 0; wall < 2; ++wall) {
-      const unsigned* start = wall ? d.W.start : d.cell_start;
-      const float4* P4 = wall ? d.wpos4 : d.pos4;
-#pragma unroll 1
-      for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); ++dz) {
-        const int z = c[2] + dz;
-        if (z < 0 || z >= g.nz) continue;
-#pragma unroll 1
-        for (int dy = -1; dy <= 1; ++dy) {
-          const int y = c[1] + dy;
-          if (y < 0 || y >= g.ny) continue;
-          const int x0 = max(c[0] - 1, 0), x1 = min(c[0] + 1, g.nx - 1);
-          const int rb = (z * g.ny + y) * g.nx;
-          const unsigned tag = ((unsigned)(dy + 1) << 25) | ((unsigned)(dz + 1) << 27) | ((unsigned)wall << 31);
-          const float oy = pi.y - (float)dy * cs;
-          const float oz = (D == 3) ? pi.z - (float)dz * cs : 0.f;
-          const unsigned j1 = SPHBUF_LDG(start + rb + x1 + 1);
-          unsigned j = SPHBUF_LDG(start + rb + x0);
-          for (; j < j1; ++j) {
-            const float4 p = SPHBUF_LDG(P4 + j);
-            const float rx = ox - (p.x + p.w * cs);
-            const float ry = oy - p.y;
-            const float rz = (D == 3) ? oz - p.z : 0.f;
-            const float r2 = rx * rx + ry * ry + rz * rz;
-            list_append(t, r2 < two_h_sq && r2 > 0.f, j | tag, lst, cap);
-          }
-        }
-      }
+    const int lin = d.A.cell[i];
+    if (!SPHBUF_IN_BOUNDS(d, (lin >= 0 && lin < d.g.ncell) || d.A.label[i] == kDead, 6, i)) continue;
+    if (reuse && !full && d.A.label[i] == kDead) {
+      d.nb_cnt[i] = 0u;
+      d.vr4[i] = make_float4(0.f, 0.f, 0.f, d.P.rho0);
+      continue;
     }
-    // the last (cnt mod 4) entries are q(4 - r) .. q3
-    const int r = t.cnt & 3;
-    if (r && t.cnt < cap)
-      lst[t.cnt >> 2] = make_uint4(r == 1 ? t.q3 : (r == 2 ? t.q2 : t.q1), r == 2 ? t.q3 : t.q2, t.q3, 0u);
-    d.nb_cnt[i] = (unsigned)t.cnt;
-    // Eq. (9) right away, while the list and the neighbours' positions are in cache
-    density_or_defer<D, true>(d, i, t.cnt);
+    const bool fresh = full || SPHBUF_LDG(d.s_mask + lin) != 0;
+    int cnt;
+    if (fresh) {
+      int c[3];
+      cell_coords(lin, g, c);
+      const float4 pi = d.pos4[i];
+      cnt = full ? search_list<D, false>(d, i, c, pi, r2max) : search_list<D, true>(d, i, c, pi, r2max);
+      if (reuse && full) d.A.path[i] = 0.f;
+    } else {
+      cnt = (int)d.nb_cnt[i];
+    }
+    // Eq. (9) right away, while a new list and the neighbours' positions are in cache
+    if (fresh)
+      density_or_defer<D, true>(d, i, cnt);
+    else
+      density_or_defer<D, false>(d, i, cnt);
   }
 }
 
@@ -434,7 +506,7 @@ __device__ __forceinline__ void density_deferred_body(const DomainDev& d, unsign
   for (unsigned r = 0; r < rounds; ++r) {
     const unsigned e = grp + r * ngrp;
     const bool live = e < nd;
-    const unsigned i = live ? d.deferred[e] : 0u;
+    const unsigned i = live && SPHBUF_IN_BOUNDS(d, d.deferred[e] < d.st->n, 7, d.deferred[e]) ? d.deferred[e] : 0u;
     const int cnt = live ? (int)d.nb_cnt[i] : 0;
     const float4 pi = d.pos4[i];
     const float fi[3] = {pi.x, pi.y, pi.z};
@@ -462,7 +534,8 @@ __device__ __forceinline__ void density_deferred_body(const DomainDev& d, unsign
     };
     if (cnt <= cap) {
       const unsigned* lst = d.nb + (size_t)i * cap;
-      for (int k = (int)lane; k < cnt; k += (int)G) visit_entry<D>(d, SPHBUF_LDG(lst + k), pi.w, fi, term);
+      for (int k = (int)lane; k < cnt; k += (int)G)
+        visit_entry<D>(d, SPHBUF_LDG(lst + k), __float_as_uint(pi.w), fi, term, i, 15);
     } else {
       int c[3];
       cell_coords(d.A.cell[i], d.g, c);
@@ -508,7 +581,7 @@ __device__ __forceinline__ void force_body(const DomainDev& d, unsigned bid, uns
     const float p_i = P.c0sq * (rho_i - P.rho0) + P.p_bg;
     const float pb2 = boundary_pressure2(d, lab, p_i);
     float a[3] = {0.f, 0.f, 0.f}, tb[3] = {0.f, 0.f, 0.f};
-    for_each_listed<D>(d, i, cnt, pi.w, fi, [&](int wall, unsigned j, float rx, float ry, float rz) {
+    for_each_listed<D>(d, i, cnt, __float_as_uint(pi.w), fi, [&](int wall, unsigned j, float rx, float ry, float rz) {
       const float r2 = rx * rx + ry * ry + rz * rz;
       float vj[3] = {0.f, 0.f, 0.f};
       float rho_j = rho_i;
@@ -518,7 +591,7 @@ __device__ __forceinline__ void force_body(const DomainDev& d, unsigned bid, uns
         rho_j = v.w;
       }
       force_term<TVF>(P, wall, rx, ry, rz, r2, vi, rho_i, p_i, pb2, vj, rho_j, a, tb);
-    });
+    }, 13);
     int c[3];
     cell_coords(d.A.cell[i], d.g, c);
     finish_force<D, TVF>(d, fused, i, n, c, fi, vi, rho_i, lab, a, tb);
@@ -599,7 +672,7 @@ __device__ __forceinline__ void viscous_body(const DomainDev& d, unsigned bid, u
       viscous_term(P, wall, rx, ry, rz, r2, vi, rho_i, vj, rho_j, a);
     };
     if (cnt <= cap) {
-      for_each_listed<D>(d, i, cnt, pi.w, fi, fn);
+      for_each_listed<D>(d, i, cnt, __float_as_uint(pi.w), fi, fn);
     } else {
       int c[3];
       cell_coords(d.A.cell[i], d.g, c);
@@ -637,7 +710,8 @@ __device__ __forceinline__ void acoustic_body(const DomainDev& d, unsigned bid, 
     }
     const float4 pi = pc[i];
     const float fi[3] = {pi.x, pi.y, pi.z};
-    const float cxf = pi.w;
+    const float cxf = pi.w;  // the packed cell, carried over to the next acoustic state
+    const unsigned ci = __float_as_uint(pi.w);
     const float4 si = sc[i];
     const float vi[3] = {si.x, si.y, si.z};
     const float rho_i = si.w;
@@ -648,14 +722,13 @@ __device__ __forceinline__ void acoustic_body(const DomainDev& d, unsigned bid, 
     float srho = 0.f;
     const uint4* lst = reinterpret_cast<const uint4*>(d.nb + (size_t)i * d.nb_cap);
     auto one = [&](unsigned ent) {
-      const unsigned j = ent & 0x1FFFFFFu;
+      const unsigned j = ent & 0x7FFFFFFFu;
       const int wall = (int)(ent >> 31);
-      const int dy = (int)((ent >> 25) & 3u) - 1;
-      const int dz = (D == 3) ? (int)((ent >> 27) & 3u) - 1 : 0;
       const float4 p = wall ? SPHBUF_LDG(d.wpos4 + j) : pc[j];
-      const float rx = fi[0] - p.x - (p.w - cxf) * g.cs;
-      const float ry = fi[1] - (float)dy * g.cs - p.y;
-      const float rz = (D == 3) ? fi[2] - (float)dz * g.cs - p.z : 0.f;
+      const unsigned cj = __float_as_uint(p.w);
+      const float rx = fi[0] - p.x - (packed_cx(cj) - packed_cx(ci)) * g.cs;
+      const float ry = fi[1] - (float)(packed_cy(cj) - packed_cy(ci)) * g.cs - p.y;
+      const float rz = (D == 3) ? fi[2] - (float)(packed_cz(cj) - packed_cz(ci)) * g.cs - p.z : 0.f;
       const float r2 = rx * rx + ry * ry + rz * rz;
       float vj[3] = {0.f, 0.f, 0.f};
       float rho_j = rho_i;

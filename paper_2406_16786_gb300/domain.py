@@ -330,6 +330,15 @@ class Domain:
         """Transport velocity of Eq. (10) with coefficient lambda (before the first step)."""
         self._check(self.lib.sphbuf_set_transport_velocity(self.h, float(lam)), "set_transport_velocity")
 
+    def set_list_reuse(self, skin_over_h: float, max_steps: int = 64):
+        """Neighbour lists with a skin, kept over steps (0 turns it off); before the first step."""
+        self._check(self.lib.sphbuf_set_list_reuse(self.h, float(skin_over_h), int(max_steps)), "set_list_reuse")
+
+    def list_builds(self) -> int:
+        n = ctypes.c_uint64()
+        self._check(self.lib.sphbuf_read_list_builds(self.h, ctypes.byref(n)), "read_list_builds")
+        return n.value
+
     def set_windkessel(self, k: int, r_p: float, compliance: float, r_d: float, p_d0: float = 0.0):
         """RCR Windkessel boundary pressure (Eq. (31)) for pressure buffer k."""
         self._check(self.lib.sphbuf_set_windkessel(self.h, int(k), float(r_p), float(compliance), float(r_d),

@@ -81,7 +81,7 @@ _HOST_ONLY = {"sphbuf_status_string", "sphbuf_error_message", "sphbuf_create_dom
 def _zero_args(argtypes):
     import ctypes
 
-    ints = (ctypes.c_int, ctypes.c_uint, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32)
+    ints = (ctypes.c_int, ctypes.c_uint, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_longlong)
     return [0 if a in ints else 0.0 if a is ctypes.c_double else None for a in argtypes]
 
 
@@ -141,9 +141,9 @@ def test_host_helpers_reject_bad_input(lib):
     assert lib.sphbuf_rotation_from_normal((ctypes.c_double * 3)(1.0, 0.0, 0.0), 0.0, None) == 1
     assert lib.sphbuf_cell_list_build(None, None, None, 0, 0, None, None, None) == 1
     assert lib.sphbuf_cell_list_build_noalloc(None, None, None, 0, 0, None, None, None) == 1
-    names = [lib.sphbuf_status_string(s) for s in range(8)]
-    assert len(set(names)) == 8 and all(names)
-    assert lib.sphbuf_status_string(8) == lib.sphbuf_status_string(-1) == b"unknown status"
+    names = [lib.sphbuf_status_string(s) for s in range(9)]
+    assert len(set(names)) == 9 and all(names)
+    assert lib.sphbuf_status_string(9) == lib.sphbuf_status_string(-1) == b"unknown status"
 
 
 def test_binding_raises_instead_of_falling_back(lib):

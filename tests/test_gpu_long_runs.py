@@ -4,7 +4,8 @@
   Umax 1.5, pressure outlet), dp 0.005, 0.38 M particles: 2000 steps.
 * 3-D pipe R 0.5 along (1,1,1)/sqrt3 with two bidirectional pressure buffers (inlet
   50 sin(pi t) Pa, outlet 0), dp 0.01: L = 8 m (6.3 M particles) and the 4.0 M bench length
-  (L = 5.09 m), 1000 steps each (1.07 s of simulated time).
+  (L = 5.09 m), 1000 steps each (1.07 s of simulated time); the bench length also with the
+  bench's kept neighbour lists (skin 0.1 h).
 * 3-D T-junction (velocity inlet, two pressure outlets at arbitrary orientations), dp 0.006,
   15.4 M particles: 500 steps.
 * 64 star channels (1-6 arms, mixed buffer types) stepped as one batch in graph replay with
@@ -67,10 +68,12 @@ def _check_run(dom, case, n0, steps, rho_bound, inflow_side, outer_budget):
     return fig
 
 
-def _run(case, steps, rho_bound, inflow_side=(), outer_budget=0.0):
+def _run(case, steps, rho_bound, inflow_side=(), outer_budget=0.0, skin=0.0):
     from paper_2406_16786_gb300.domain import Domain
 
     dom = Domain.from_case(case)
+    if skin > 0:
+        dom.set_list_reuse(skin)  # kept neighbour lists (the bench's setting)
     dom.use_graph(True)
     n0 = dom.count()
     t0 = time.perf_counter()
@@ -78,7 +81,8 @@ def _run(case, steps, rho_bound, inflow_side=(), outer_budget=0.0):
     dom.sync()
     wall = time.perf_counter() - t0
     fig = _check_run(dom, case, n0, steps, rho_bound, inflow_side, outer_budget)
-    print("%s: %d steps in %.2f s of wall time (%.3f ms/step)" % (case.name, steps, wall, 1e3 * wall / steps))
+    print("%s (skin %g h, %d full list builds): %d steps in %.2f s of wall time (%.3f ms/step)"
+          % (case.name, skin, dom.list_builds(), steps, wall, 1e3 * wall / steps))
     dom.close()
     return fig
 
@@ -89,11 +93,11 @@ def test_bent_channel_2000_steps():
     _run(c, 2000, rho_bound=0.3, inflow_side=[0])
 
 
-@pytest.mark.parametrize("length", [8.0, 5.09])
-def test_pipe_1000_steps(length):
+@pytest.mark.parametrize("length,skin", [(8.0, 0.0), (5.09, 0.0), (5.09, 0.1)])
+def test_pipe_1000_steps(length, skin):
     c = wl.config3(length=length)
     # 50 Pa / (rho0 c0^2) = 0.56 %
-    _run(c, 1000, rho_bound=0.03, inflow_side=[0], outer_budget=0.02)
+    _run(c, 1000, rho_bound=0.03, inflow_side=[0], outer_budget=0.02, skin=skin)
 
 
 def test_tjunction_500_steps():

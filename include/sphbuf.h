@@ -279,6 +279,17 @@ sphbuf_status sphbuf_rotation_from_normal(const double normal[3], double roll, d
  * with SPHBUF_PHASE_BUFFER_KERNEL or SPHBUF_PHASE_FULL_CHECK are refused too),
  * SPHBUF_ERR_STATE (after the first step). */
 sphbuf_status sphbuf_set_list_reuse(sphbuf_domain_t d, double skin_over_h, int max_steps);
+/* Boundary identification of the transport velocity (the TVF of Eq. (10) advects the inner
+ * fluid; Sec. 2.2 identifies about three layers of boundary particles with a cited
+ * spatio-temporal method; this library's reading): a particle is a candidate when its
+ * position divergence -sum_j V_j r_ij . grad_i W_ij (V_j = dp^d, fluid and wall neighbours)
+ * is below 0.75 d, core when it was a candidate in the previous physics step too (or has no
+ * previous step), and a boundary particle when it is core or a fluid neighbour within 2h is
+ * core; the transport velocity moves only label-0 particles that are not boundary particles.
+ * Writes, for the live particles in the order of sphbuf_read_particles, the flags of the last
+ * step with the transport velocity: bit 0 candidate, bit 1 set once identified, bit 2 core,
+ * bit 3 boundary particle (all 0 before such a step).  Synchronises. */
+sphbuf_status sphbuf_read_boundary_flags(sphbuf_domain_t d, uint8_t *flags, uint64_t cap, uint64_t *n_out);
 /* Full neighbour-list builds so far (with lists rebuilt every step: one per rebuild). */
 sphbuf_status sphbuf_read_list_builds(sphbuf_domain_t d, uint64_t *builds);
 

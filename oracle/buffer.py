@@ -240,6 +240,10 @@ class OracleSim:
         self.last_del = []  # (k, id)
         self.cell_start = None
         self.n0 = n
+        # boundary identification of the transport velocity (reading A27): the previous step's
+        # candidate flag per particle (-1: none yet) and the last boundary flags
+        self.cand_prev = np.full(n, -1, dtype=np.int64)
+        self.boundary = np.zeros(n, dtype=bool)
 
     # ------------------------------------------------------------------ helpers
     @property
@@ -256,6 +260,8 @@ class OracleSim:
         self.rho = self.rho[idx]
         self.id = self.id[idx]
         self.label = self.label[idx]
+        self.cand_prev = self.cand_prev[idx]
+        self.boundary = self.boundary[idx]
 
     def rebuild(self):
         c = cell_coords(self.pos, self.lo, self.cs, self.dims, self.dim)
@@ -313,13 +319,17 @@ class OracleSim:
         self.acc = acc
         adv = v
         if P.tvf_lambda > 0.0:
-            # Eq. (10): advect the fluid away from the in-/outlets with the transport velocity
+            # Eq. (10): advect the inner fluid with the transport velocity
             # v - dt p_max sum_j 2 m/(rho_i rho_j) dW/dr e_ij, p_max = lambda rho0 v_max^2 with
-            # v_max of the previous step; the buffer particles (the boundary layers at the in-/
-            # outlets, reading A23) keep v
+            # v_max of the previous step; the buffer particles and the identified boundary
+            # particles (reading A27, from the step's start positions) keep v
+            psi = sph.position_divergence(P, self.n, ff, fw)
+            cand, _, self.boundary = sph.boundary_layers(P, psi, self.cand_prev, ff)
+            self.cand_prev = cand.astype(np.int64)
             p_max = P.tvf_lambda * P.rho0 * self.vmax * self.vmax
             shift = P.dt * p_max * sph.transport_sum(P, rho_new, ff, fw)
-            adv = np.where((self.label == 0)[:, None], v - shift, v)
+            inner = (self.label == 0) & ~self.boundary
+            adv = np.where(inner[:, None], v - shift, v)
         self.vmax = float(np.linalg.norm(v, axis=1).max()) if v.shape[0] else 0.0
         self.vel = v
         self.pos = self.pos + adv * P.dt
@@ -405,6 +415,8 @@ class OracleSim:
             self.rho = np.concatenate([self.rho, np.array(new_rho)])
             self.id = np.concatenate([self.id, np.array(new_id, dtype=np.int64)])
             self.label = np.concatenate([self.label, np.zeros(len(new_pos), dtype=np.int64)])
+            self.cand_prev = np.concatenate([self.cand_prev, np.full(len(new_pos), -1, dtype=np.int64)])
+            self.boundary = np.concatenate([self.boundary, np.zeros(len(new_pos), dtype=bool)])
         # Sec. 5.3: after the generation, the particles of a rotating buffer turn with it
         for k, mf in self.moving.items():
             m = self.label == self.buffers[k].label

@@ -179,6 +179,43 @@ def transport_sum(P: Params, rho, ff: Pairs, fw: Pairs) -> np.ndarray:
     return out
 
 
+# Boundary particles of the transport velocity (Sec. 2.2: the TVF serves the inner fluid; the
+# paper identifies about three layers of boundary particles with a cited spatio-temporal
+# method that it does not restate).  Reading A27:
+#   spatial   psi_i = -sum_j V_j r_ij . grad_i W_ij over fluid and wall neighbours (V_j = dp^d),
+#             the SPH estimate of div r = d; a particle is a candidate when psi_i < 0.75 d
+#             (its kernel support is cut by a free or open boundary);
+#   temporal  a candidate is a core boundary particle when it was a candidate in the previous
+#             step too (a particle without a previous step counts the current one);
+#   layers    a particle is a boundary particle when it is core or a fluid neighbour within 2h
+#             is core (2h = 2.6 dp: the core layer and about two more).
+PSI_CANDIDATE = 0.75
+
+
+def position_divergence(P: Params, n: int, ff: Pairs, fw: Pairs) -> np.ndarray:
+    """psi_i = -sum_j V_j r_ij . grad_i W_ij = sum_j V_j r_ij (-dW/dr) (fluid and wall j)."""
+    V = P.dp ** P.dim
+    s = _scatter(ff.i, -V * ff.r * kernel.dW(ff.r, P.h, P.dim), n)
+    s += _scatter(fw.i, -V * fw.r * kernel.dW(fw.r, P.h, P.dim), n)
+    return s
+
+
+def boundary_layers(P: Params, psi: np.ndarray, prev, ff: Pairs):
+    """(candidate, core, boundary) flags of the reading above; prev: the previous step's
+    candidate flags (None, or -1 entries, where a particle has no previous step)."""
+    cand = psi < PSI_CANDIDATE * P.dim
+    if prev is None:
+        before = cand
+    else:
+        prev = np.asarray(prev)
+        before = np.where(prev < 0, cand, prev > 0)
+    core = cand & before
+    near = np.zeros(psi.shape[0], dtype=bool)
+    if ff.i.size:
+        np.logical_or.at(near, ff.i, core[ff.j])
+    return cand, core, core | near
+
+
 def moved(pairs: Pairs, fpos, other) -> Pairs:
     """The same pairs with r_ij recomputed from new positions (fixed configuration)."""
     rij = fpos[pairs.i] - other[pairs.j]

@@ -67,6 +67,7 @@ SIGNATURES = {
     "sphbuf_batch_set_persistent": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_longlong]),
     "sphbuf_set_list_reuse": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int]),
     "sphbuf_read_list_builds": (ctypes.c_int, [vp, P(ctypes.c_uint64)]),
+    "sphbuf_read_boundary_flags": (ctypes.c_int, [vp, vp, c_u64, P(c_u64)]),
     "sphbuf_write_particles_async": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, ctypes.c_uint64, ctypes.c_uint32]),
     "sphbuf_read_particles_async": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, ctypes.c_uint64, P(ctypes.c_uint64)]),
     "sphbuf_io_wait": (ctypes.c_int, [vp]),

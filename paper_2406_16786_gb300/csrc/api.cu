@@ -615,6 +615,8 @@ sphbuf_status sphbuf_create_domain(const sphbuf_domain_desc* desc, void* cuda_st
   P.cs_d = d->cs;
   P.capacity = (unsigned)desc->capacity;
   P.list_cap = (unsigned)std::max<uint64_t>(1024, std::min<uint64_t>(desc->capacity, 1ull << 22));
+  P.psi_cand = (float)(0.75 * D);
+  P.vol = (float)std::pow(desc->dp, D);
   P.reuse = 0;
   P.list_r2 = P.two_h_sq;
   P.skin = 0.f;
@@ -640,8 +642,10 @@ sphbuf_status sphbuf_create_domain(const sphbuf_domain_desc* desc, void* cuda_st
     A(dalloc(d, &p->id, C));
     A(dalloc(d, &p->label, C));
     A(dalloc(d, &p->path, C));
+    A(dalloc(d, &p->bflag, C));
   }
   A(dalloc(d, &v.order, C));
+  A(dalloc(d, &v.core, C));
   A(dalloc(d, &v.vr4, C));
   A(dalloc(d, &v.deferred, C));
   // neighbour lists of the density pass, reused by the force pass (~80 neighbours in 3-D and
@@ -1203,6 +1207,26 @@ sphbuf_status sphbuf_set_list_reuse(sphbuf_domain_t d, double skin_over_h, int m
     cudaGraphExecDestroy(d->graph);
     d->graph = nullptr;
   }
+  return SPHBUF_OK;
+}
+
+sphbuf_status sphbuf_read_boundary_flags(sphbuf_domain_t d, uint8_t* flags, uint64_t cap, uint64_t* n_out) {
+  if (!d) return SPHBUF_ERR_INVALID_ARG;
+  StepState st;
+  sphbuf_status s = read_state(d, &st);
+  if (s != SPHBUF_OK) return s;
+  const uint64_t n = st.n_live;
+  if (n_out) *n_out = n;
+  if (!flags || !n) return SPHBUF_OK;
+  if (n > cap) return fail(d, SPHBUF_ERR_CAPACITY, "host array smaller than the particle count");
+  const uint8_t* src = d->dev.A.bflag;
+  if (!st.full) {
+    launch_gather_u8(d->dev, d->dev.A.bflag, d->dev.B.bflag, (unsigned)n, d->stream);
+    CK(cudaGetLastError());
+    src = d->dev.B.bflag;
+  }
+  CK(cudaMemcpyAsync(flags, src, n, cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
   return SPHBUF_OK;
 }
 

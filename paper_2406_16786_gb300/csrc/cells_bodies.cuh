@@ -225,6 +225,7 @@ __device__ __forceinline__ void scatter_body(const DomainDev& d, unsigned bid, u
     d.A.rho[dst] = rho;
     d.A.id[dst] = d.B.id[i];
     d.A.path[dst] = full ? 0.f : d.B.path[i];
+    d.A.bflag[dst] = d.B.bflag[i];
     int c[3];
     cell_coords(lin, g, c);
     if (live) {

@@ -161,6 +161,8 @@ struct Phys {
   float h, inv_h, two_h_sq, alpha, rho0, c0, c0sq, eta, mass, dt, inv_sum_w0, w_self;
   float p_bg;  // background pressure of the EoS: p = c0^2 (rho - rho0) + p_bg
   float tvf_lambda;  // transport velocity (Eq. (10)): p_max = lambda rho0 v_max^2; 0 = off
+  float psi_cand;    // boundary candidates: position divergence below 0.75 d (reading A27)
+  float vol;         // particle volume dp^d
   float dt_ac;       // acoustic step of the dual-criteria scheme (dt / dual_n)
   int dual_n;        // acoustic steps per advection step; 0 = single-rate kick-drift
   // neighbour lists kept over steps (0 = rebuilt every step): lists hold the pairs within
@@ -214,6 +216,10 @@ struct Particles {
   unsigned* id;
   uint8_t* label;
   float* path;  // drift path length since the last full neighbour-list build
+  // boundary identification of the transport velocity (reading A27), set by the last force
+  // pass with the transport velocity: bit 0 candidate, bit 1 set (a previous step exists),
+  // bit 2 core, bit 3 boundary particle
+  uint8_t* bflag;
 };
 
 struct Walls {

@@ -35,6 +35,7 @@ __device__ __forceinline__ void write_injection(const DomainDev& d, const Decisi
   d.B.id[dst] = kNoSlot;
   d.B.label[dst] = 0;  // the duplicate is ordinary fluid (Algorithm 1)
   d.B.path[dst] = 0.f;
+  d.B.bflag[dst] = 0;
 }
 
 __device__ __forceinline__ void write_deletion(const DomainDev& d, const Decision& e, unsigned slot) {

@@ -46,6 +46,8 @@ struct DomainDev {
   const uint8_t* s_mask;      // per cell: 1 where kept lists are rebuilt every step (candidate
                               //   cells and two rings of cells around them)
   unsigned* order;            // live particles' slots sorted by (cell, id) (kept lists)
+  uint8_t* core;              // per slot, from the density pass with the transport velocity:
+                              //   bit 0 core boundary particle, bit 1 candidate (reading A27)
   StepState* st;
   long long ncell_pad;
   int scan_tiles;
@@ -171,6 +173,8 @@ void launch_egest(const DomainDev& d, const Particles& P, float* frac, float* ve
 // view: B <- the live particles of A in (cell, id) order through the index list (for reads of a
 // state whose slots were kept by the last rebuild).
 void launch_view(const DomainDev& d, cudaStream_t s);
+// dst[k] = src[order[k]] for the n live particles (a per-slot byte field in sorted order).
+void launch_gather_u8(const DomainDev& d, const uint8_t* src, uint8_t* dst, unsigned n, cudaStream_t s);
 // Pipelined host transfers.  ingest_staged: B <- arrays of n particles staged in device memory
 // (id / label NULL: 0..n-1 / 0), with the checks of sphbuf_write_particles; a failed check
 // latches SPHBUF_ERR_INVALID_ARG and leaves the domain with no particles, otherwise n and

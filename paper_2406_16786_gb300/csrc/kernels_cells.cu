@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(256) k_ingest(DomainDev d, const float* __rest
       d.B.label[i] = 0;
     }
     if (!ids_given) d.B.id[i] = i;
+    d.B.bflag[i] = 0;
     mx = max(mx, d.B.id[i]);
   }
   bad = __reduce_or_sync(0xFFFFFFFFu, bad);
@@ -256,6 +257,7 @@ __global__ void __launch_bounds__(256) k_ingest_staged(DomainDev d, const int* _
     d.B.label[i] = lab;
     const unsigned q = id ? id[i] : i;
     d.B.id[i] = q;
+    d.B.bflag[i] = 0;
     mx = max(mx, q);
   }
   bad = __reduce_or_sync(0xFFFFFFFFu, bad);
@@ -496,6 +498,17 @@ void launch_egest(const DomainDev& d, const Particles& P, float* frac, float* ve
 }
 
 void launch_view(const DomainDev& d, cudaStream_t s) { k_view<<<d.sm_count * 4, 256, 0, s>>>(d); }
+
+namespace {
+__global__ void __launch_bounds__(256) k_gather_u8(DomainDev d, const uint8_t* __restrict__ src,
+                                                   uint8_t* __restrict__ dst, unsigned n) {
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) dst[k] = src[d.order[k]];
+}
+}  // namespace
+
+void launch_gather_u8(const DomainDev& d, const uint8_t* src, uint8_t* dst, unsigned n, cudaStream_t s) {
+  k_gather_u8<<<d.sm_count * 4, 256, 0, s>>>(d, src, dst, n);
+}
 
 void launch_decode_positions(const DomainDev& d, double* pos_out, const double lo[3], double cs,
                              cudaStream_t s) {

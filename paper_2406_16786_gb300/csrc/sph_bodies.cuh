@@ -162,6 +162,7 @@ __device__ __forceinline__ void drift_store(const DomainDev& d, bool fused, unsi
     d.B.id[i] = d.A.id[i];
     d.B.label[i] = kDead;
     d.B.path[i] = 0.f;
+    d.B.bflag[i] = 0;
     return;
   }
   int cn[3] = {c[0], c[1], c[2]};
@@ -195,6 +196,7 @@ __device__ __forceinline__ void drift_store(const DomainDev& d, bool fused, unsi
   d.B.rho[i] = rho;
   d.B.id[i] = id;
   d.B.label[i] = lab;
+  d.B.bflag[i] = d.A.bflag[i];
   if (d.P.reuse) {
     // drift path since the last full list build, and its largest value this step
     float a2 = adv[0] * adv[0] + adv[1] * adv[1];
@@ -213,7 +215,7 @@ __device__ __forceinline__ void drift_store(const DomainDev& d, bool fused, unsi
 template <int D, bool TVF>
 __device__ __forceinline__ void finish_force(const DomainDev& d, bool fused, unsigned i, unsigned n, const int c[3], const float fi[3],
                                              const float vi[3], float rho_i, uint8_t lab, const float a[3],
-                                             const float tb[3]) {
+                                             const float tb[3], bool near_core = false) {
   const Phys& P = d.P;
   float v[3] = {vi[0] + a[0] * P.dt, vi[1] + a[1] * P.dt, D == 3 ? vi[2] + a[2] * P.dt : 0.f};
   if (lab != 0 && lab != kDead) {
@@ -241,8 +243,12 @@ __device__ __forceinline__ void finish_force(const DomainDev& d, bool fused, uns
               (unsigned long long)__double2ll_rn((double)(vn * b.flux_scale) * kFluxScale));
   }
   if (TVF) {
+    // reading A27: the inner fluid is label 0 and neither core nor within 2h of a core
+    // boundary particle; the flags go with the particle for the next step's temporal test
+    const uint8_t cf = d.core[i];
+    const bool bnd = (cf & 1u) || near_core;
     float adv[3] = {v[0], v[1], v[2]};
-    if (lab == 0) {
+    if (lab == 0 && !bnd) {
       const float s = P.dt * d.st->p_max;
 #pragma unroll
       for (int x = 0; x < D; ++x) adv[x] = v[x] - s * tb[x];
@@ -254,6 +260,8 @@ __device__ __forceinline__ void finish_force(const DomainDev& d, bool fused, uns
     const unsigned wmax = __reduce_max_sync(am, bits);
     if ((threadIdx.x & 31) == __ffs(am) - 1) atomicMax(&d.st->vmax_bits, wmax);
     drift_store<D>(d, fused, i, n, c, fi, v, adv, rho_i, lab);
+    if (lab != kDead)
+      d.B.bflag[i] = (uint8_t)(2u | ((cf >> 1) & 1u) | ((cf & 1u) << 2) | (bnd ? 8u : 0u));
   } else {
     drift_store<D>(d, fused, i, n, c, fi, v, v, rho_i, lab);
   }
@@ -279,6 +287,7 @@ __device__ void force_one(const DomainDev& d, bool fused, unsigned i, unsigned n
   const float p_i = P.c0sq * (rho_i - P.rho0) + P.p_bg;
   const float pb2 = boundary_pressure2(d, lab, p_i);
   float a[3] = {0.f, 0.f, 0.f}, tb[3] = {0.f, 0.f, 0.f};
+  bool near_core = false;
   for_each_near<D>(d, c, fi, [&](int wall, unsigned j, float rx, float ry, float rz) {
     const float r2 = rx * rx + ry * ry + rz * rz;
     if (r2 < P.two_h_sq && r2 > 0.f) {
@@ -288,11 +297,12 @@ __device__ void force_one(const DomainDev& d, bool fused, unsigned i, unsigned n
         const float4 v = d.vr4[j];
         vj[0] = v.x, vj[1] = v.y, vj[2] = v.z;
         rho_j = v.w;
+        if (TVF) near_core |= (d.core[j] & 1u) != 0;
       }
       force_term<TVF>(P, wall, rx, ry, rz, r2, vi, rho_i, p_i, pb2, vj, rho_j, a, tb);
     }
   });
-  finish_force<D, TVF>(d, fused, i, n, c, fi, vi, rho_i, lab, a, tb);
+  finish_force<D, TVF>(d, fused, i, n, c, fi, vi, rho_i, lab, a, tb, near_core);
 }
 
 // ---------------------------------------------------------------- neighbour lists
@@ -332,6 +342,17 @@ __device__ __forceinline__ void for_each_listed(const DomainDev& d, unsigned i, 
   }
 }
 
+// Boundary identification of reading A27 (the transport velocity's inner fluid): particle i
+// is a candidate when its position divergence psi = -sum_j V_j r_ij . grad_i W_ij falls below
+// 0.75 d, and core when it was a candidate in the previous step too (or has no previous step);
+// core[i] holds bit 0 core, bit 1 candidate for the force pass.
+__device__ __forceinline__ void identify_boundary(const DomainDev& d, unsigned i, float psi) {
+  const bool cand = psi < d.P.psi_cand;
+  const uint8_t prev = d.A.bflag[i];
+  const bool before = (prev & 2u) ? (prev & 1u) != 0 : cand;
+  d.core[i] = (uint8_t)((cand && before ? 1u : 0u) | (cand ? 2u : 0u));
+}
+
 // Density, Eq. (9), for particle i of the fluid (not in a buffer) from its list; writes
 // vr4[i] = (v_i, rho_i).
 template <int D, bool OWN>
@@ -339,13 +360,19 @@ __device__ __forceinline__ void density_fluid(const DomainDev& d, unsigned i, in
   const Phys& P = d.P;
   const float4 pi = d.pos4[i];
   const float fi[3] = {pi.x, pi.y, pi.z};
-  float s = 0.f;
+  const bool tvf = P.tvf_lambda > 0.f;
+  float s = 0.f, psi = 0.f;
   for_each_listed<D, OWN>(
       d, i, cnt, __float_as_uint(pi.w), fi,
-      [&](int, unsigned, float rx, float ry, float rz) { s += kernel_w(sqrtf(rx * rx + ry * ry + rz * rz) * P.inv_h, P); },
+      [&](int, unsigned, float rx, float ry, float rz) {
+        const float r = sqrtf(rx * rx + ry * ry + rz * rz);
+        s += kernel_w(r * P.inv_h, P);
+        if (tvf) psi -= P.vol * r * kernel_dw(r * P.inv_h, P);
+      },
       OWN ? 11 : 12);
   const float4 v = d.vel4[i];
   d.vr4[i] = make_float4(v.x, v.y, v.z, P.rho0 * (s + P.w_self) * P.inv_sum_w0);
+  if (tvf) identify_boundary(d, i, psi);
 }
 
 // Eq. (9) for fluid particle i from its list, or, for a buffer particle (the Eq. (4) rate) or
@@ -465,6 +492,7 @@ __device__ __forceinline__ void neighbours_body(const DomainDev& d, unsigned bid
     if (reuse && !full && d.A.label[i] == kDead) {
       d.nb_cnt[i] = 0u;
       d.vr4[i] = make_float4(0.f, 0.f, 0.f, d.P.rho0);
+      if (d.P.tvf_lambda > 0.f) d.core[i] = 0;
       continue;
     }
     const bool fresh = full || SPHBUF_LDG(d.s_mask + lin) != 0;
@@ -516,9 +544,14 @@ __device__ __forceinline__ void density_deferred_body(const DomainDev& d, unsign
     const float rho_i = vi4.w;
     const float p_i = P.c0sq * (rho_i - P.rho0) + P.p_bg;
     const float vi[3] = {vi4.x, vi4.y, vi4.z};
-    float s = 0.f;
+    float s = 0.f, psi = 0.f;
+    const bool tvf = P.tvf_lambda > 0.f;
     auto term = [&](int wall, unsigned j, float rx, float ry, float rz) {
       const float r2 = rx * rx + ry * ry + rz * rz;
+      if (tvf) {
+        const float r = sqrtf(r2);
+        psi -= P.vol * r * kernel_dw(r * P.inv_h, P);
+      }
       if (!buf) {
         s += kernel_w(sqrtf(r2) * P.inv_h, P);
       } else {
@@ -548,7 +581,11 @@ __device__ __forceinline__ void density_deferred_body(const DomainDev& d, unsign
           lane, G);
     }
 #pragma unroll
-    for (int o = (int)G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o, (int)G);
+    for (int o = (int)G / 2; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(0xFFFFFFFFu, s, o, (int)G);
+      psi += __shfl_xor_sync(0xFFFFFFFFu, psi, o, (int)G);
+    }
+    if (live && lane == 0 && tvf) identify_boundary(d, i, psi);
     if (live && lane == 0) {
       // (in the dual-criteria scheme the buffer particles keep their density here; their
       // continuity is integrated by the acoustic steps)
@@ -581,6 +618,7 @@ __device__ __forceinline__ void force_body(const DomainDev& d, unsigned bid, uns
     const float p_i = P.c0sq * (rho_i - P.rho0) + P.p_bg;
     const float pb2 = boundary_pressure2(d, lab, p_i);
     float a[3] = {0.f, 0.f, 0.f}, tb[3] = {0.f, 0.f, 0.f};
+    bool near_core = false;
     for_each_listed<D>(d, i, cnt, __float_as_uint(pi.w), fi, [&](int wall, unsigned j, float rx, float ry, float rz) {
       const float r2 = rx * rx + ry * ry + rz * rz;
       float vj[3] = {0.f, 0.f, 0.f};
@@ -589,12 +627,14 @@ __device__ __forceinline__ void force_body(const DomainDev& d, unsigned bid, uns
         const float4 v = SPHBUF_LDG(d.vr4 + j);
         vj[0] = v.x, vj[1] = v.y, vj[2] = v.z;
         rho_j = v.w;
+        // (kept lists reach beyond 2h: the layer test takes the pairs within 2h only)
+        if (TVF && r2 < P.two_h_sq) near_core |= (SPHBUF_LDG(d.core + j) & 1u) != 0;
       }
       force_term<TVF>(P, wall, rx, ry, rz, r2, vi, rho_i, p_i, pb2, vj, rho_j, a, tb);
     }, 13);
     int c[3];
     cell_coords(d.A.cell[i], d.g, c);
-    finish_force<D, TVF>(d, fused, i, n, c, fi, vi, rho_i, lab, a, tb);
+    finish_force<D, TVF>(d, fused, i, n, c, fi, vi, rho_i, lab, a, tb, near_core);
   }
 }
 

@@ -334,6 +334,16 @@ class Domain:
         """Neighbour lists with a skin, kept over steps (0 turns it off); before the first step."""
         self._check(self.lib.sphbuf_set_list_reuse(self.h, float(skin_over_h), int(max_steps)), "set_list_reuse")
 
+    def boundary_flags(self) -> np.ndarray:
+        """Boundary-identification flags of the last step with the transport velocity, in the
+        order of read(): bit 0 candidate, bit 1 set, bit 2 core, bit 3 boundary particle."""
+        n = self.count()
+        out = np.zeros(max(n, 1), np.uint8)
+        nn = ctypes.c_uint64()
+        self._check(self.lib.sphbuf_read_boundary_flags(self.h, _ptr(out), out.shape[0], ctypes.byref(nn)),
+                    "read_boundary_flags")
+        return out[:n]
+
     def list_builds(self) -> int:
         n = ctypes.c_uint64()
         self._check(self.lib.sphbuf_read_list_builds(self.h, ctypes.byref(n)), "read_list_builds")

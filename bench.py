@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--skin", type=float, default=0.1,
                     help="neighbour-list skin / h of the main measurement (kept lists); 0 rebuilds every step")
     ap.add_argument("--reuse-max", type=int, default=64)
+    ap.add_argument("--profile-kept", action="store_true",
+                    help="with --profile: the kept-list launch sequence")
     ap.add_argument("--profile", action="store_true",
                     help="profiling driver: the pipe at --length, 100 steps, one default step, one step with the "
                          "buffer kernel; prints the particle count and exits")
@@ -882,19 +884,38 @@ def run_reference(args):
 
 
 def run_profile(args):
-    """The launch sequence profiled for the ncu summaries: the pipe at --length (2.5 m: 2.0 M
-    particles), 100 default steps (lists rebuilt every step), one default step (k_force with
+    """The launch sequences profiled for the ncu summaries, on the pipe at --length (2.5 m:
+    2.0 M particles).
+
+    Default: 100 default steps with lists rebuilt every step, one default step (k_force with
     the fused decisions: launch 101) and one step with the decisions in the buffer kernel
-    (k_force without them: launch 102; k_buffer: launch 1)."""
+    (k_force without them: launch 102; k_buffer: launch 1).
+
+    --profile-kept: the bench's kept lists (skin --skin h) over 100 steps, then steps until one
+    keeps its lists; prints the index (from 0) of that step's k_neighbours / k_force launch
+    ("kept_launch K") for ncu's -s."""
     from paper_2406_16786_gb300 import _ffi, workloads
     from paper_2406_16786_gb300.domain import Domain
 
     case = workloads.config3(length=args.length)
     dom = Domain.from_case(case)
-    dom.step(100)
-    dom.step(1)
-    dom.step(1, _ffi.STEP_DEFAULT | _ffi.PHASE_BUFFER_KERNEL)
-    dom.sync()
+    if args.profile_kept:
+        dom.set_list_reuse(args.skin, args.reuse_max)
+        dom.step(100)
+        launches = 100
+        while True:
+            b0 = dom.list_builds()
+            dom.step(1)
+            launches += 1
+            if dom.list_builds() == b0:
+                break
+        dom.sync()
+        print("kept_launch", launches - 1, "full builds", dom.list_builds())
+    else:
+        dom.step(100)
+        dom.step(1)
+        dom.step(1, _ffi.STEP_DEFAULT | _ffi.PHASE_BUFFER_KERNEL)
+        dom.sync()
     inj, dels = dom.last_decisions()
     print("particles", dom.count(), "last step decisions", len(inj), len(dels))
     dom.close()

@@ -892,7 +892,8 @@ def run_profile(args):
     (k_force without them: launch 102; k_buffer: launch 1).
 
     --profile-kept: the bench's kept lists (skin --skin h) over 100 steps, then steps until one
-    keeps its lists; prints the index (from 0) of that step's k_neighbours / k_force launch
+    keeps its lists (its rebuild decides that the next step's search keeps them) and one more
+    step; prints the index (from 0) of the kept step's k_neighbours / k_force launch
     ("kept_launch K") for ncu's -s."""
     from paper_2406_16786_gb300 import _ffi, workloads
     from paper_2406_16786_gb300.domain import Domain
@@ -903,14 +904,16 @@ def run_profile(args):
         dom.set_list_reuse(args.skin, args.reuse_max)
         dom.step(100)
         launches = 100
+        # a step's rebuild decides (and counts) the next step's full list build
         while True:
             b0 = dom.list_builds()
             dom.step(1)
             launches += 1
             if dom.list_builds() == b0:
                 break
+        dom.step(1)
         dom.sync()
-        print("kept_launch", launches - 1, "full builds", dom.list_builds())
+        print("kept_launch", launches, "full builds", dom.list_builds())
     else:
         dom.step(100)
         dom.step(1)

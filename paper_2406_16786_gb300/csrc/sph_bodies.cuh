@@ -365,9 +365,7 @@ __device__ __forceinline__ void density_fluid(const DomainDev& d, unsigned i, in
   for_each_listed<D, OWN>(
       d, i, cnt, __float_as_uint(pi.w), fi,
       [&](int, unsigned, float rx, float ry, float rz) {
-        const float r2 = rx * rx + ry * ry + rz * rz;
-        if (r2 >= P.two_h_sq) return;  // a kept list's skin: W = 0 there
-        const float r = sqrtf(r2);
+        const float r = sqrtf(rx * rx + ry * ry + rz * rz);
         s += kernel_w(r * P.inv_h, P);
         if (tvf) psi -= P.vol * r * kernel_dw(r * P.inv_h, P);
       },
@@ -550,7 +548,6 @@ __device__ __forceinline__ void density_deferred_body(const DomainDev& d, unsign
     const bool tvf = P.tvf_lambda > 0.f;
     auto term = [&](int wall, unsigned j, float rx, float ry, float rz) {
       const float r2 = rx * rx + ry * ry + rz * rz;
-      if (r2 >= P.two_h_sq) return;  // a kept list's skin
       if (tvf) {
         const float r = sqrtf(r2);
         psi -= P.vol * r * kernel_dw(r * P.inv_h, P);
@@ -624,16 +621,14 @@ __device__ __forceinline__ void force_body(const DomainDev& d, unsigned bid, uns
     bool near_core = false;
     for_each_listed<D>(d, i, cnt, __float_as_uint(pi.w), fi, [&](int wall, unsigned j, float rx, float ry, float rz) {
       const float r2 = rx * rx + ry * ry + rz * rz;
-      // a kept list's skin (r >= 2h): every term has dW = 0 there, and the neighbour's state
-      // is not gathered
-      if (r2 >= P.two_h_sq) return;
       float vj[3] = {0.f, 0.f, 0.f};
       float rho_j = rho_i;
       if (!wall) {
         const float4 v = SPHBUF_LDG(d.vr4 + j);
         vj[0] = v.x, vj[1] = v.y, vj[2] = v.z;
         rho_j = v.w;
-        if (TVF) near_core |= (SPHBUF_LDG(d.core + j) & 1u) != 0;
+        // (kept lists reach beyond 2h: the layer test takes the pairs within 2h only)
+        if (TVF && r2 < P.two_h_sq) near_core |= (SPHBUF_LDG(d.core + j) & 1u) != 0;
       }
       force_term<TVF>(P, wall, rx, ry, rz, r2, vi, rho_i, p_i, pb2, vj, rho_j, a, tb);
     }, 13);

@@ -147,8 +147,13 @@ __host__ __device__ inline unsigned pack_cell(int cx, int cy, int cz) {
 __device__ __forceinline__ float packed_cx(unsigned pc) {
   return __int_as_float(0x4B000000 | (int)(pc & 0x7FFu)) - 8388608.f;
 }
-__device__ __forceinline__ int packed_cy(unsigned pc) { return (int)((pc >> 11) & 0x7FFu); }
-__device__ __forceinline__ int packed_cz(unsigned pc) { return (int)(pc >> 22); }
+// y and z likewise (exact; no integer-to-float conversion)
+__device__ __forceinline__ float packed_cyf(unsigned pc) {
+  return __int_as_float(0x4B000000 | (int)((pc >> 11) & 0x7FFu)) - 8388608.f;
+}
+__device__ __forceinline__ float packed_czf(unsigned pc) {
+  return __int_as_float(0x4B000000 | (int)(pc >> 22)) - 8388608.f;
+}
 
 struct Grid {
   int dim;

@@ -46,7 +46,7 @@ namespace {
     BODY<D>(sd, (unsigned)m.y, (unsigned)m.z);                                                 \
   }
 
-SPHBUF_PAIR(k_neighbours, neighbours_body, (kThreads, 5))
+SPHBUF_PAIR(k_neighbours, neighbours_body, (kThreads, 4))
 SPHBUF_PAIR(k_density_deferred, density_deferred_body, (kThreads, 4))
 template <int D, bool TVF>
 __global__ void __launch_bounds__(kThreads, 4) k_force(DomainDev d, int fused) {
@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(512, 2) k_acoustic_batch(BatchDev b, int sub) 
 #undef SPHBUF_PAIR
 
 int grid_for(const DomainDev& d, int per_sm) { return d.sm_count * per_sm; }
+
 
 }  // namespace
 

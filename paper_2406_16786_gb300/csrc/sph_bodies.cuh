@@ -75,7 +75,10 @@ template <bool TVF>
 __device__ __forceinline__ void force_term(const Phys& P, bool wall, float rx, float ry, float rz, float r2,
                                            const float vi[3], float rho_i, float p_i, float pb2, const float vj[3],
                                            float rho_j, float a[3], float tb[3]) {
-  const float r = sqrtf(r2), inv_r = 1.f / r;
+  // 1/r and r from the hardware reciprocal square root, and m / (rho_i rho_j) from the fast
+  // reciprocal: a few ulp each, far inside the FP32 pass's tolerance against FP64, where the
+  // correctly rounded sqrt and divisions cost about a sixth of the pair's instructions
+  const float inv_r = rsqrtf(r2), r = r2 * inv_r;
   float vx, vy, vz, p_j;
   if (wall) {
     // mirrored wall state: v_ij = 2 v_i, rho_j = rho_i, p_j = p_i
@@ -89,7 +92,7 @@ __device__ __forceinline__ void force_term(const Phys& P, bool wall, float rx, f
   const float dU = -(vx * rx + vy * ry + vz * rz) * inv_r;  // U_L - U_R
   const float beta = fminf(3.f * fmaxf(dU, 0.f), P.c0);
   const float pstar = 0.5f * (p_i + p_j) + 0.25f * beta * (rho_i + rho_j) * dU;
-  const float m_rr = P.mass / (rho_i * rho_j) * kernel_dw(r * P.inv_h, P);
+  const float m_rr = __fdividef(P.mass, rho_i * rho_j) * kernel_dw(r * P.inv_h, P);
   const float ce = m_rr * (pb2 - 2.f * pstar) * inv_r;  // along r_ij (e_ij = r_ij / r)
   const float cv = m_rr * 2.f * P.eta * inv_r;
   a[0] += ce * rx + cv * vx;
@@ -322,8 +325,8 @@ __device__ __forceinline__ void visit_entry(const DomainDev& d, unsigned ent, un
   const float4 p = SPHBUF_LDG((wall ? d.wpos4 : d.pos4) + j);
   const unsigned cj = __float_as_uint(p.w);
   const float rx = fi[0] - p.x - (packed_cx(cj) - packed_cx(ci)) * cs;
-  const float ry = fi[1] - (float)(packed_cy(cj) - packed_cy(ci)) * cs - p.y;
-  const float rz = (D == 3) ? fi[2] - (float)(packed_cz(cj) - packed_cz(ci)) * cs - p.z : 0.f;
+  const float ry = fi[1] - (packed_cyf(cj) - packed_cyf(ci)) * cs - p.y;
+  const float rz = (D == 3) ? fi[2] - (packed_czf(cj) - packed_czf(ci)) * cs - p.z : 0.f;
   fn(wall, j, rx, ry, rz);
 }
 
@@ -333,8 +336,11 @@ template <int D, bool OWN = false, typename Fn>
 __device__ __forceinline__ void for_each_listed(const DomainDev& d, unsigned i, int cnt, unsigned ci, const float fi[3],
                                                 Fn&& fn, unsigned site = 3) {
   const uint4* lst = reinterpret_cast<const uint4*>(d.nb + (size_t)i * d.nb_cap);
+  uint4 nq = make_uint4(0u, 0u, 0u, 0u);
+  if (cnt > 0) nq = OWN ? lst[0] : SPHBUF_LDG(lst);
   for (int e = 0; e < cnt; e += 4) {
-    const uint4 q = OWN ? lst[e >> 2] : SPHBUF_LDG(lst + (e >> 2));
+    const uint4 q = nq;
+    if (e + 4 < cnt) nq = OWN ? lst[(e >> 2) + 1] : SPHBUF_LDG(lst + (e >> 2) + 1);
     visit_entry<D>(d, q.x, ci, fi, fn, i, site);
     if (e + 1 < cnt) visit_entry<D>(d, q.y, ci, fi, fn, i, site);
     if (e + 2 < cnt) visit_entry<D>(d, q.z, ci, fi, fn, i, site);
@@ -353,23 +359,66 @@ __device__ __forceinline__ void identify_boundary(const DomainDev& d, unsigned i
   d.core[i] = (uint8_t)((cand && before ? 1u : 0u) | (cand ? 2u : 0u));
 }
 
+// The position of list entry ent (fluid slot or wall), for the pipelined walk below.
+__device__ __forceinline__ float4 entry_pos(const DomainDev& d, unsigned ent, unsigned who, unsigned site) {
+  const unsigned j = ent & 0x7FFFFFFFu;
+  const int wall = (int)(ent >> 31);
+  if (!SPHBUF_IN_BOUNDS_AT(d, wall ? j < d.W.start[d.g.ncell] : j < d.st->n, site + 100 * wall, j, who))
+    return make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFFFFFu));
+  return SPHBUF_LDG((wall ? d.wpos4 : d.pos4) + j);
+}
+
 // Density, Eq. (9), for particle i of the fluid (not in a buffer) from its list; writes
-// vr4[i] = (v_i, rho_i).
+// vr4[i] = (v_i, rho_i).  The sum runs in list order, as in every other pass.
 template <int D, bool OWN>
 __device__ __forceinline__ void density_fluid(const DomainDev& d, unsigned i, int cnt) {
   const Phys& P = d.P;
   const float4 pi = d.pos4[i];
   const float fi[3] = {pi.x, pi.y, pi.z};
+  const unsigned ci = __float_as_uint(pi.w);
   const bool tvf = P.tvf_lambda > 0.f;
+  const unsigned site = OWN ? 11 : 12;
   float s = 0.f, psi = 0.f;
-  for_each_listed<D, OWN>(
-      d, i, cnt, __float_as_uint(pi.w), fi,
-      [&](int, unsigned, float rx, float ry, float rz) {
-        const float r = sqrtf(rx * rx + ry * ry + rz * rz);
+  // software pipeline over the chunks of four entries: the positions of chunk k + 1 and the
+  // entries of chunk k + 2 are in flight while chunk k is summed
+  const uint4* lst = reinterpret_cast<const uint4*>(d.nb + (size_t)i * d.nb_cap);
+  auto ld = [&](int c) { return OWN ? lst[c] : SPHBUF_LDG(lst + c); };
+  const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+  const uint4 q = cnt > 0 ? ld(0) : zero;
+  uint4 nq = cnt > 4 ? ld(1) : zero;
+  float4 p[4];
+  {
+    const unsigned e4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) p[k] = k < cnt ? entry_pos(d, e4[k], i, site) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  const float cs = d.g.cs;
+  for (int e = 0; e < cnt; e += 4) {
+    float4 pn[4];
+    {
+      const unsigned e4[4] = {nq.x, nq.y, nq.z, nq.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        pn[k] = e + 4 + k < cnt ? entry_pos(d, e4[k], i, site) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const uint4 nnq = e + 8 < cnt ? ld((e >> 2) + 2) : zero;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (e + k < cnt) {
+        const unsigned cj = __float_as_uint(p[k].w);
+        const float rx = fi[0] - p[k].x - (packed_cx(cj) - packed_cx(ci)) * cs;
+        const float ry = fi[1] - (packed_cyf(cj) - packed_cyf(ci)) * cs - p[k].y;
+        const float rz = (D == 3) ? fi[2] - (packed_czf(cj) - packed_czf(ci)) * cs - p[k].z : 0.f;
+        const float r2 = rx * rx + ry * ry + rz * rz;
+        const float r = r2 * rsqrtf(r2);  // (listed pairs have r > 0)
         s += kernel_w(r * P.inv_h, P);
         if (tvf) psi -= P.vol * r * kernel_dw(r * P.inv_h, P);
-      },
-      OWN ? 11 : 12);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) p[k] = pn[k];
+    nq = nnq;
+  }
   const float4 v = d.vel4[i];
   d.vr4[i] = make_float4(v.x, v.y, v.z, P.rho0 * (s + P.w_self) * P.inv_sum_w0);
   if (tvf) identify_boundary(d, i, psi);
@@ -767,8 +816,8 @@ __device__ __forceinline__ void acoustic_body(const DomainDev& d, unsigned bid, 
       const float4 p = wall ? SPHBUF_LDG(d.wpos4 + j) : pc[j];
       const unsigned cj = __float_as_uint(p.w);
       const float rx = fi[0] - p.x - (packed_cx(cj) - packed_cx(ci)) * g.cs;
-      const float ry = fi[1] - (float)(packed_cy(cj) - packed_cy(ci)) * g.cs - p.y;
-      const float rz = (D == 3) ? fi[2] - (float)(packed_cz(cj) - packed_cz(ci)) * g.cs - p.z : 0.f;
+      const float ry = fi[1] - (packed_cyf(cj) - packed_cyf(ci)) * g.cs - p.y;
+      const float rz = (D == 3) ? fi[2] - (packed_czf(cj) - packed_czf(ci)) * g.cs - p.z : 0.f;
       const float r2 = rx * rx + ry * ry + rz * rz;
       float vj[3] = {0.f, 0.f, 0.f};
       float rho_j = rho_i;

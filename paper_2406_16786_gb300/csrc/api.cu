@@ -823,6 +823,7 @@ sphbuf_status sphbuf_write_particles(sphbuf_domain_t d, const int32_t* cell, con
       st.full = 1;
       st.n_inj = 0;
       st.n_del = 0;
+      for (int k = 0; k < 2; ++k) st.sched[k] = st.sched_done[k] = 0u;
       CK(cudaMemcpy(d->dev.st, &st, sizeof(StepState), cudaMemcpyHostToDevice));
       d->labels_given = true;
       d->need_rebuild = true;
@@ -838,6 +839,7 @@ sphbuf_status sphbuf_write_particles(sphbuf_domain_t d, const int32_t* cell, con
   st.n_del = 0;
   st.next_id = next_id;
   st.status = 0;
+  for (int k = 0; k < 2; ++k) st.sched[k] = st.sched_done[k] = 0u;
   CK(cudaMemcpy(d->dev.st, &st, sizeof(StepState), cudaMemcpyHostToDevice));
   d->labels_given = label != nullptr;
   d->need_rebuild = true;

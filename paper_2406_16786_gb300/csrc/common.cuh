@@ -211,6 +211,10 @@ struct StepState {
   unsigned path_bits;              // largest drift path since the last full build (float bits)
   unsigned since_full;             // steps since the last full build
   unsigned long long list_builds;  // full builds so far
+  // dynamic share-out of the neighbour (0) and force (1) passes: the next chunk to take and
+  // the blocks done; zero between launches (the last block of a launch resets them)
+  unsigned sched[2];
+  unsigned sched_done[2];
 };
 
 struct Particles {

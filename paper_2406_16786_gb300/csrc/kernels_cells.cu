@@ -280,6 +280,7 @@ __global__ void k_ingest_finish(DomainDev d, unsigned n, unsigned next_id) {
   st->n_del = 0;
   st->next_id = next_id;
   st->status = ok ? 0 : 1 /* SPHBUF_ERR_INVALID_ARG */;
+  for (int k = 0; k < 2; ++k) st->sched[k] = st->sched_done[k] = 0u;
 }
 
 __global__ void __launch_bounds__(256) k_egest_staged(DomainDev d, int* __restrict__ cell, float* __restrict__ frac,

@@ -526,23 +526,51 @@ __device__ __forceinline__ int search_list(const DomainDev& d, unsigned i, const
 // the every-step region around the buffers (where duplicates appear and parents are recycled)
 // search, through the index list, and the others keep their lists; dead slots are skipped
 // (their density copy is a harmless rho0 at rest, since listed dead slots add nothing).
+// Dynamic share-out of a pass over the particles: the blocks of the pass (nblk of them for
+// this domain) take chunks of blockDim.x particles from the domain's counter st->sched[k]
+// until none is left, so that blocks whose chunks are costly (the every-step search region of
+// kept lists, strongly compressed regions) do not hold up the end of the pass; body(i) runs
+// for i = chunk * blockDim.x + threadIdx.x (i may reach past n).  Every block takes part,
+// with n = 0 once an error is latched; the last block to finish resets the counter and the
+// done count for the pass's next launch.
+template <typename Body>
+__device__ __forceinline__ void for_each_chunk(const DomainDev& d, int k, unsigned n, unsigned nblk, Body&& body) {
+  __shared__ unsigned s_chunk;
+  const unsigned nch = (n + blockDim.x - 1) / blockDim.x;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_chunk = atomicAdd(&d.st->sched[k], 1u);
+    __syncthreads();
+    const unsigned c = s_chunk;
+    if (c >= nch) break;
+    body(c * blockDim.x + threadIdx.x);
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&d.st->sched_done[k], 1u) == nblk - 1u) {
+      atomicExch(&d.st->sched[k], 0u);
+      atomicExch(&d.st->sched_done[k], 0u);
+    }
+  }
+}
+
 template <int D>
 __device__ __forceinline__ void neighbours_body(const DomainDev& d, unsigned bid, unsigned nblk) {
   if (bid == 0 && threadIdx.x == 0) begin_step(d);
-  if (d.st->status) return;
-  const unsigned n = d.st->n;
+  const unsigned n = d.st->status ? 0u : d.st->n;
   const Grid g = d.g;
   const bool reuse = d.P.reuse != 0;
   const bool full = !reuse || d.st->full != 0;
   const float r2max = d.P.list_r2;
-  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
+  for_each_chunk(d, 0, n, nblk, [&](unsigned i) {
+    if (i >= n) return;
     const int lin = d.A.cell[i];
-    if (!SPHBUF_IN_BOUNDS(d, (lin >= 0 && lin < d.g.ncell) || d.A.label[i] == kDead, 6, i)) continue;
+    if (!SPHBUF_IN_BOUNDS(d, (lin >= 0 && lin < d.g.ncell) || d.A.label[i] == kDead, 6, i)) return;
     if (reuse && !full && d.A.label[i] == kDead) {
       d.nb_cnt[i] = 0u;
       d.vr4[i] = make_float4(0.f, 0.f, 0.f, d.P.rho0);
       if (d.P.tvf_lambda > 0.f) d.core[i] = 0;
-      continue;
+      return;
     }
     const bool fresh = full || SPHBUF_LDG(d.s_mask + lin) != 0;
     int cnt;
@@ -560,7 +588,7 @@ __device__ __forceinline__ void neighbours_body(const DomainDev& d, unsigned bid
       density_or_defer<D, true>(d, i, cnt);
     else
       density_or_defer<D, false>(d, i, cnt);
-  }
+  });
 }
 
 // The deferred particles of the density pass: Eq. (4) rate for buffer particles (the Riemann
@@ -648,15 +676,15 @@ __device__ __forceinline__ void density_deferred_body(const DomainDev& d, unsign
 // (with the transport velocity of Eq. (10) when TVF).
 template <int D, bool TVF>
 __device__ __forceinline__ void force_body(const DomainDev& d, unsigned bid, unsigned nblk, bool fused) {
-  if (d.st->status) return;
-  const unsigned n = d.st->n;
+  const unsigned n = d.st->status ? 0u : d.st->n;
   const Phys P = d.P;
   const int cap = d.nb_cap;
-  for (unsigned i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
+  for_each_chunk(d, 1, n, nblk, [&](unsigned i) {
+    if (i >= n) return;
     const int cnt = (int)d.nb_cnt[i];
     if (cnt > cap) {
       force_one<D, TVF>(d, fused, i, n);
-      continue;
+      return;
     }
     const float4 pi = d.pos4[i];
     const float fi[3] = {pi.x, pi.y, pi.z};
@@ -684,7 +712,7 @@ __device__ __forceinline__ void force_body(const DomainDev& d, unsigned bid, uns
     int c[3];
     cell_coords(d.A.cell[i], d.g, c);
     finish_force<D, TVF>(d, fused, i, n, c, fi, vi, rho_i, lab, a, tb, near_core);
-  }
+  });
 }
 
 // Kinematic steps start with a launch of their own for the step constants (begin_body): the

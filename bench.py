@@ -42,14 +42,16 @@ FP32_LANES_PER_SM = 128
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch from an ncu capture
 # of the named source revision (the 2.0 M-particle pipe, L = 2.5 m, the bench's kernels and
-# launch configuration).  The neighbour pass scales with the particle count; the buffer kernel
-# with the buffers' candidate cells, which are the same at L = 2.5 and 5.09 m.  A figure whose
-# kernel changed after its revision is not reported (None).
+# launch configuration, kept lists with skin 0.1 h).  The neighbour and force passes scale with
+# the particle count (the neighbour pass's launches are a mix of kept-list steps and full
+# builds, weighted by the measured share of full builds); the buffer kernel scales with the
+# buffers' candidate cells, which are the same at L = 2.5 and 5.09 m.  A figure whose kernel
+# changed after its revision is not reported (None).
 NCU_TRAFFIC = {
-    "k_neighbours": {"bytes_per_particle": (253.15e6 + 650.12e6) / 1965281, "source": None},
-    "k_buffer": {"bytes_per_launch": 3.489e6, "source": None},
+    "k_neighbours": {"kept_bytes_per_particle": None, "full_bytes_per_particle": None, "source": None},
+    "k_force": {"bytes_per_particle": None, "source": None},
+    "k_buffer": {"bytes_per_launch": None, "source": None},
 }
-
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -65,6 +67,8 @@ def parse():
     ap.add_argument("--skin", type=float, default=0.1,
                     help="neighbour-list skin / h of the main measurement (kept lists); 0 rebuilds every step")
     ap.add_argument("--reuse-max", type=int, default=64)
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="with --profile: the 64-domain batch, 40 steps")
     ap.add_argument("--profile-kept", action="store_true",
                     help="with --profile: the kept-list launch sequence")
     ap.add_argument("--profile", action="store_true",
@@ -138,16 +142,17 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def traffic_of(kernel, particles):
+def traffic_of(kernel, particles, full_frac=0.0):
     """DRAM bytes of one launch of `kernel` from the ncu figures above, or None when they were
     not captured from the current revision of the kernel."""
     t = NCU_TRAFFIC.get(kernel)
     if not t or not t.get("source"):
         return None
+    if "kept_bytes_per_particle" in t:
+        return particles * ((1.0 - full_frac) * t["kept_bytes_per_particle"] + full_frac * t["full_bytes_per_particle"])
     if "bytes_per_particle" in t:
         return t["bytes_per_particle"] * particles
     return t.get("bytes_per_launch")
-
 
 def measured_peaks():
     try:
@@ -580,7 +585,7 @@ def run_gpu(args):
         "phase_ms_per_step_buffer_kernel": per_sep,
         "roofline": {"bound": "alu", "kernel": kern[dom_ph]["kernel"], "achieved": kern[dom_ph]["achieved"],
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": kern[dom_ph]["frac"],
-                     "traffic": traffic_of(kern[dom_ph]["kernel"], n_mean),
+                     "traffic": traffic_of(kern[dom_ph]["kernel"], n_mean, full_frac),
                      "traffic_source": NCU_TRAFFIC.get(kern[dom_ph]["kernel"], {}).get("source"),
                      "peak_source": "FP32 lanes x 2 x max SM clock (derived; not measured)",
                      "flops_per_particle": kern[dom_ph]["flops_per_particle"], "pairs_per_particle": pairs,
@@ -621,6 +626,8 @@ def run_batched(args, stream, rank=0, world=1):
     # plain: each domain alone (graph replays), one after another
     plain = [Domain.from_case(c, stream=stream) for c in cases]
     for d in plain:
+        if args.skin > 0:
+            d.set_list_reuse(args.skin, args.reuse_max)
         d.use_graph(True)
         d.step(W)
     torch.cuda.synchronize()
@@ -636,6 +643,9 @@ def run_batched(args, stream, rank=0, world=1):
         d.close()
     # batched: the same 64 domains in one batch (grid multiplier from the autotuner)
     doms = [Domain.from_case(c, stream=stream) for c in cases]
+    for d in doms:
+        if args.skin > 0:
+            d.set_list_reuse(args.skin, args.reuse_max)
     b = Batch(doms, stream=stream)
     m, _ = b.autotune(trial_steps=2)
     b.use_graph(True)
@@ -657,6 +667,9 @@ def run_batched(args, stream, rank=0, world=1):
     # the same batch as one persistent launch per step (grid barriers between the phases), same
     # launch configuration, same number of steps
     pdoms = [Domain.from_case(c) for c in cases]
+    for d in pdoms:
+        if args.skin > 0:
+            d.set_list_reuse(args.skin, args.reuse_max)
     pb = Batch(pdoms, stream=stream)
     pb.set_config(cfg)
     pb.set_persistent(True)
@@ -674,6 +687,8 @@ def run_batched(args, stream, rank=0, world=1):
         d.close()
     nd = len(all_cases)
     return {"workload": "64 2-D star channels (1-6 arms, 10k-500k particles log-uniform, mixed BCs)",
+            "neighbour_lists": ("kept over steps, skin %g h, in all three arms" % args.skin) if args.skin > 0
+                               else "rebuilt every step",
             "domains": nd, "ranks": world, "domains_per_rank": len(mine), "particles": n_batch, "steps": K,
             "plain_domain_steps_per_s": nd * K / (t_plain / 1e3),
             "batched_domain_steps_per_s": nd * K / (t_batch / 1e3),
@@ -891,6 +906,9 @@ def run_profile(args):
     the fused decisions: launch 101) and one step with the decisions in the buffer kernel
     (k_force without them: launch 102; k_buffer: launch 1).
 
+    --profile-batch: the 64-domain batch of the batched measurement (kept lists as in the
+    bench, the batch's default launch configuration), 40 steps.
+
     --profile-kept: the bench's kept lists (skin --skin h) over 100 steps, then steps until one
     keeps its lists (its rebuild decides that the next step's search keeps them) and one more
     step; prints the index (from 0) of the kept step's k_neighbours / k_force launch
@@ -898,6 +916,22 @@ def run_profile(args):
     from paper_2406_16786_gb300 import _ffi, workloads
     from paper_2406_16786_gb300.domain import Domain
 
+    if args.profile_batch:
+        from paper_2406_16786_gb300.domain import Batch
+
+        doms = [Domain.from_case(c) for c in workloads.config5()]
+        for d in doms:
+            if args.skin > 0:
+                d.set_list_reuse(args.skin, args.reuse_max)
+        b = Batch(doms)
+        b.use_graph(True)
+        b.step(40)
+        b.sync()
+        print("batch domains", len(doms), "steps 40", "config", b.get_config())
+        b.close()
+        for d in doms:
+            d.close()
+        return
     case = workloads.config3(length=args.length)
     dom = Domain.from_case(case)
     if args.profile_kept:

@@ -909,10 +909,10 @@ def run_profile(args):
     --profile-batch: the 64-domain batch of the batched measurement (kept lists as in the
     bench, the batch's default launch configuration), 40 steps.
 
-    --profile-kept: the bench's kept lists (skin --skin h) over 100 steps, then steps until one
-    keeps its lists (its rebuild decides that the next step's search keeps them) and one more
-    step; prints the index (from 0) of the kept step's k_neighbours / k_force launch
-    ("kept_launch K") for ncu's -s."""
+    --profile-kept: the bench's kept lists (skin --skin h) over at least 100 steps, until a step's
+    rebuild keeps the lists for the next step, and that next step; prints the index (from 0) of
+    that step's k_neighbours / k_force launch ("kept_launch K") and of the last step with a full
+    list build ("full_launch F") for ncu's -s."""
     from paper_2406_16786_gb300 import _ffi, workloads
     from paper_2406_16786_gb300.domain import Domain
 
@@ -936,18 +936,19 @@ def run_profile(args):
     dom = Domain.from_case(case)
     if args.profile_kept:
         dom.set_list_reuse(args.skin, args.reuse_max)
-        dom.step(100)
-        launches = 100
         # a step's rebuild decides (and counts) the next step's full list build
+        launches, full_at = 0, 0
         while True:
             b0 = dom.list_builds()
             dom.step(1)
             launches += 1
-            if dom.list_builds() == b0:
+            if dom.list_builds() != b0:
+                full_at = launches
+            elif launches >= 100:
                 break
         dom.step(1)
         dom.sync()
-        print("kept_launch", launches, "full builds", dom.list_builds())
+        print("kept_launch", launches, "full_launch", full_at, "full builds", dom.list_builds())
     else:
         dom.step(100)
         dom.step(1)

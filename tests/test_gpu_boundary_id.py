@@ -1,6 +1,7 @@
 """Boundary identification of the transport velocity (reading A27) on the GPU against the FP64
 oracle: a 2-D block of fluid with walls on three sides and a free top (the kernel support of
-the top rows is cut), a perturbed state, lambda = 7.5, five steps.
+the top rows is cut), a perturbed state, lambda = 7.5, five steps, with neighbour lists
+rebuilt every step and kept over steps (skin 0.2 h).
 
 * Per particle (by id) the GPU's flags (candidate, core, boundary) equal the oracle's after
   every step, except where the FP32 and FP64 position divergences fall on both sides of the
@@ -54,7 +55,8 @@ def _by_id(ids, vals):
     return ids[o], vals[o]
 
 
-def test_boundary_flags_and_state_follow_the_oracle():
+@pytest.mark.parametrize("skin", [0.0, 0.2])
+def test_boundary_flags_and_state_follow_the_oracle(skin):
     from paper_2406_16786_gb300.domain import Domain
 
     c = _free_top_case()
@@ -62,6 +64,8 @@ def test_boundary_flags_and_state_follow_the_oracle():
     vel32 = c.fluid_vel.astype(np.float32)
     rho32 = c.fluid_rho.astype(np.float32)
     dom = Domain.from_case(c)
+    if skin:
+        dom.set_list_reuse(skin)
     dom.write_particles(cell, frac, vel32, rho32)
     pos = wl.decode_positions(cell, frac, c.lo, c.cs, c.grid_dims())
     sim = OB.OracleSim(c, pos=pos, vel=vel32.astype(np.float64), rho=rho32.astype(np.float64))

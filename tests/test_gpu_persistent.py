@@ -2,7 +2,8 @@
 between the phases.
 
 * It gives, bit for bit, the states of the domains stepped alone (plain launches and graph
-  replay), with the fused buffer decisions and the transport-velocity variant.
+  replay), with the fused buffer decisions and the transport-velocity variant, with lists
+  rebuilt every step and with kept lists (over several reuse cycles).
 * Its barrier waits are bounded: with a spin limit of zero every block that has to wait gives
   up at once, the step latches SPHBUF_ERR_TIMEOUT in every domain (reported by the next
   synchronising call) and the launch ends; the GPU context stays usable.
@@ -27,19 +28,26 @@ def _cases():
     return out
 
 
-@pytest.mark.parametrize("graph", [False, True])
-def test_persistent_equals_individual(graph):
+@pytest.mark.parametrize("graph,skin", [(False, 0.0), (True, 0.0), (True, 0.2)])
+def test_persistent_equals_individual(graph, skin):
     from paper_2406_16786_gb300.domain import Batch, Domain
 
+    steps = 25 if skin else 12
     alone = [Domain.from_case(c) for c in _cases()]
     for d in alone:
-        d.step(12)
+        if skin:
+            d.set_list_reuse(skin)
+        d.step(steps)
     together = [Domain.from_case(c) for c in _cases()]
+    for d in together:
+        if skin:
+            d.set_list_reuse(skin)
     b = Batch(together)
     b.set_persistent(True)
     b.use_graph(graph)
-    b.step(12)
+    b.step(steps)
     b.sync()
+    kept = 0
     for a, t in zip(alone, together):
         ra, rt = a.read(), t.read()
         for key in ra:
@@ -47,6 +55,11 @@ def test_persistent_equals_individual(graph):
         assert a.global_counters() == t.global_counters()
         (ia, da), (it, dt) = a.last_decisions(), t.last_decisions()
         assert ia == it and sorted(da) == sorted(dt)
+        if skin:
+            assert a.list_builds() == t.list_builds()
+            kept += a.list_builds() < steps
+    # (the fast shear flow of the lockstep channel outruns the skin every step)
+    assert not skin or kept >= 3
     b.close()
     for d in alone + together:
         d.close()

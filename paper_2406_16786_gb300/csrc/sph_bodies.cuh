@@ -519,13 +519,6 @@ __device__ __forceinline__ int search_list(const DomainDev& d, unsigned i, const
   return t.cnt;
 }
 
-// Neighbour-list pass, then Eq. (9) from the list for a fluid particle (deferred otherwise).
-// Lists rebuilt every step (reuse off): every particle searches the sorted cells.  Kept lists
-// (reuse on): after a full rebuild every particle searches (radius 2h + skin, drift paths
-// restart from 0); after a rebuild that kept the slots, only the particles whose cell lies in
-// the every-step region around the buffers (where duplicates appear and parents are recycled)
-// search, through the index list, and the others keep their lists; dead slots are skipped
-// (their density copy is a harmless rho0 at rest, since listed dead slots add nothing).
 // Dynamic share-out of a pass over the particles: the blocks of the pass (nblk of them for
 // this domain) take chunks of blockDim.x particles from the domain's counter st->sched[k]
 // until none is left, so that blocks whose chunks are costly (the every-step search region of
@@ -554,6 +547,13 @@ __device__ __forceinline__ void for_each_chunk(const DomainDev& d, int k, unsign
   }
 }
 
+// Neighbour-list pass, then Eq. (9) from the list for a fluid particle (deferred otherwise).
+// Lists rebuilt every step (reuse off): every particle searches the sorted cells.  Kept lists
+// (reuse on): after a full rebuild every particle searches (radius 2h + skin, drift paths
+// restart from 0); after a rebuild that kept the slots, only the particles whose cell lies in
+// the every-step region around the buffers (where duplicates appear and parents are recycled)
+// search, through the index list, and the others keep their lists; dead slots are skipped
+// (their density copy is a harmless rho0 at rest, since listed dead slots add nothing).
 template <int D>
 __device__ __forceinline__ void neighbours_body(const DomainDev& d, unsigned bid, unsigned nblk) {
   if (bid == 0 && threadIdx.x == 0) begin_step(d);

@@ -269,9 +269,13 @@ sphbuf_status sphbuf_rotation_from_normal(const double normal[3], double roll, d
  * slots, duplicates are appended), except where the lists must change: the particles in the
  * buffers' candidate cells and two rings of cells around them search their neighbours again
  * every step (through a list of the live particles sorted by (cell, id), rebuilt every step).
- * A full rebuild (sort, every list searched again) follows once twice the largest drift path
- * of any particle since the last one exceeds the skin (a pair may then have come within 2h
- * unlisted), after max_steps steps, after a kinematic step and after particles are written.
+ * A full rebuild (sort, every list searched again) follows once a pair may have come within
+ * 2h unlisted: each particle's displacement since the last full rebuild is measured relative
+ * to a reference velocity fixed for the period (the middle of the range of the previous
+ * period's drift velocities, zero included; a pair's distance changes by at most the sum of
+ * the two relative displacements, and a wall particle's is the reference velocity times the
+ * time), and the rebuild follows once twice the largest of them exceeds the skin; also after
+ * max_steps steps, after a kinematic step and after particles are written.
  * Results differ from lists rebuilt every step only by the order of the FP32 sums.  Reads
  * and counts always give the live particles sorted by (cell, id).  skin_over_h = 0 turns it
  * off (the default).  Only before the first step.  Errors: SPHBUF_ERR_INVALID_ARG (skin

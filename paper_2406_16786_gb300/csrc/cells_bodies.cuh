@@ -119,16 +119,37 @@ __device__ __forceinline__ void scan_down_occ_body(unsigned* __restrict__ cnt, c
 
 // force_full: this step's rebuild must sort (kinematic steps and the commit's rebuild);
 // otherwise, with kept neighbour lists, the first thread decides: a full rebuild once twice
-// the largest drift path since the last one exceeds the lists' skin (a pair may then have
-// come within 2h unlisted) or after reuse_max steps, else the slots keep their order.
+// the largest displacement since the last one, relative to the period's reference velocity
+// u0 (walls included, whose relative displacement is -u0 t), exceeds the lists' skin (a pair
+// may then have come within 2h unlisted) or after reuse_max steps, else the slots keep their
+// order.  At a full rebuild the next period's u0 is set from the range of this period's drift
+// velocities; any constant u0 keeps the test exact, the middle of the range makes it tightest.
 __device__ __forceinline__ void hist_body(const DomainDev& d, unsigned bid, unsigned nblk, int force_full) {
   if (d.st->status) return;
   if (bid == 0 && threadIdx.x == 0) {
     StepState* st = d.st;
     int full = 1;
     if (d.P.reuse && !force_full) {
-      const float path = __uint_as_float(st->path_bits);
+      // a pair's distance changed by at most |disp_i| + |disp_j| (both relative to u0); a
+      // wall particle's displacement relative to u0 is -u0 t
+      float u2 = 0.f;
+      for (int x = 0; x < d.g.dim; ++x) u2 += st->u0[x] * st->u0[x];
+      const float wall = d.W.start[d.g.ncell] ? sqrtf(u2) * (float)(st->since_full + 1) * d.P.dt : 0.f;
+      const float path = fmaxf(__uint_as_float(st->path_bits), wall);
       full = (2.f * path > d.P.skin || st->since_full + 1 >= (unsigned)d.P.reuse_max) ? 1 : 0;
+    }
+    if (full) {
+      // the next period's reference velocity: the middle of the range of the drift
+      // velocities of this one, zero (the walls) included
+      for (int x = 0; x < 3; ++x) {
+        float u = 0.f;
+        if (st->v_hi[x]) {
+          const float hi = fmaxf(key_to_float(st->v_hi[x]), 0.f), lo = fminf(key_to_float(~st->v_lo[x]), 0.f);
+          u = 0.5f * (hi + lo);
+        }
+        st->u0[x] = u;
+        st->v_hi[x] = st->v_lo[x] = 0u;
+      }
     }
     st->full = full;
     st->path_bits = 0u;
@@ -224,7 +245,8 @@ __device__ __forceinline__ void scatter_body(const DomainDev& d, unsigned bid, u
     const float rho = d.B.rho[i];
     d.A.rho[dst] = rho;
     d.A.id[dst] = d.B.id[i];
-    d.A.path[dst] = full ? 0.f : d.B.path[i];
+#pragma unroll
+    for (int x = 0; x < D; ++x) d.A.disp[x][dst] = full ? 0.f : d.B.disp[x][i];
     d.A.bflag[dst] = d.B.bflag[i];
     int c[3];
     cell_coords(lin, g, c);

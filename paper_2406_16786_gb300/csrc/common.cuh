@@ -147,6 +147,14 @@ __host__ __device__ inline unsigned pack_cell(int cx, int cy, int cz) {
 __device__ __forceinline__ float packed_cx(unsigned pc) {
   return __int_as_float(0x4B000000 | (int)(pc & 0x7FFu)) - 8388608.f;
 }
+// Order-preserving unsigned key of a float (and back): keys compare like the values.
+__device__ __forceinline__ unsigned float_to_key(float v) {
+  const unsigned b = __float_as_uint(v);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_to_float(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
 // y and z likewise (exact; no integer-to-float conversion)
 __device__ __forceinline__ float packed_cyf(unsigned pc) {
   return __int_as_float(0x4B000000 | (int)((pc >> 11) & 0x7FFu)) - 8388608.f;
@@ -171,8 +179,8 @@ struct Phys {
   float dt_ac;       // acoustic step of the dual-criteria scheme (dt / dual_n)
   int dual_n;        // acoustic steps per advection step; 0 = single-rate kick-drift
   // neighbour lists kept over steps (0 = rebuilt every step): lists hold the pairs within
-  // list_r2 = (2h + skin)^2 and are rebuilt when twice the largest drift since the last full
-  // build exceeds the skin, or after reuse_max steps
+  // list_r2 = (2h + skin)^2 and are rebuilt when twice the largest displacement since the last
+  // full build (relative to a reference velocity) exceeds the skin, or after reuse_max steps
   int reuse;
   float list_r2, skin;
   int reuse_max;
@@ -208,7 +216,11 @@ struct StepState {
   // slots, and the index list `order` holds the live particles sorted by (cell, id)
   int full;
   unsigned n_live;                 // live particles (n counts slots)
-  unsigned path_bits;              // largest drift path since the last full build (float bits)
+  unsigned path_bits;              // largest |disp| of this step's drift (float bits)
+  // reference velocity of the current reuse period, and the range of the drift velocities
+  // seen in it (order-preserving keys, both maximised from 0: hi = key(v), lo = ~key(v))
+  float u0[3];
+  unsigned v_hi[3], v_lo[3];
   unsigned since_full;             // steps since the last full build
   unsigned long long list_builds;  // full builds so far
   // dynamic share-out of the neighbour (0) and force (1) passes: the next chunk to take and
@@ -224,7 +236,8 @@ struct Particles {
   float* rho;
   unsigned* id;
   uint8_t* label;
-  float* path;  // drift path length since the last full neighbour-list build
+  float* disp[3];  // displacement since the last full neighbour-list build, relative to the
+                   // reference velocity StepState::u0 of that period (x < d allocated)
   // boundary identification of the transport velocity (reading A27), set by the last force
   // pass with the transport velocity: bit 0 candidate, bit 1 set (a previous step exists),
   // bit 2 core, bit 3 boundary particle

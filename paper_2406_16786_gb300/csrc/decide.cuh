@@ -34,7 +34,8 @@ __device__ __forceinline__ void write_injection(const DomainDev& d, const Decisi
   d.B.rho[dst] = e.rho;
   d.B.id[dst] = kNoSlot;
   d.B.label[dst] = 0;  // the duplicate is ordinary fluid (Algorithm 1)
-  d.B.path[dst] = 0.f;
+#pragma unroll
+  for (int x = 0; x < D; ++x) d.B.disp[x][dst] = 0.f;
   d.B.bflag[dst] = 0;
 }
 

@@ -164,7 +164,8 @@ __device__ __forceinline__ void drift_store(const DomainDev& d, bool fused, unsi
     d.B.rho[i] = d.P.rho0;
     d.B.id[i] = d.A.id[i];
     d.B.label[i] = kDead;
-    d.B.path[i] = 0.f;
+#pragma unroll
+    for (int x = 0; x < D; ++x) d.B.disp[x][i] = 0.f;
     d.B.bflag[i] = 0;
     return;
   }
@@ -201,14 +202,32 @@ __device__ __forceinline__ void drift_store(const DomainDev& d, bool fused, unsi
   d.B.label[i] = lab;
   d.B.bflag[i] = d.A.bflag[i];
   if (d.P.reuse) {
-    // drift path since the last full list build, and its largest value this step
-    float a2 = adv[0] * adv[0] + adv[1] * adv[1];
-    if (D == 3) a2 += adv[2] * adv[2];
-    const float path = d.A.path[i] + sqrtf(a2) * d.P.dt;
-    d.B.path[i] = path;
+    // displacement since the last full list build relative to the period's reference
+    // velocity, its largest length this step, and the range of the drift velocities
+    float s2 = 0.f;
+#pragma unroll
+    for (int x = 0; x < D; ++x) {
+      const float dx = d.A.disp[x][i] + (adv[x] - d.st->u0[x]) * d.P.dt;
+      d.B.disp[x][i] = dx;
+      s2 += dx * dx;
+    }
     const unsigned am = __activemask();
-    const unsigned wmax = __reduce_max_sync(am, __float_as_uint(path));
-    if ((threadIdx.x & 31) == __ffs(am) - 1) atomicMax(&d.st->path_bits, wmax);
+    const bool lead = (threadIdx.x & 31) == __ffs(am) - 1;
+    const unsigned wmax = __reduce_max_sync(am, __float_as_uint(sqrtf(s2)));
+    if (lead) atomicMax(&d.st->path_bits, wmax);
+    // (the range only centres the reference velocity, which any value keeps correct: one
+    // warp in sixteen samples it, which keeps its atomics off the step's critical path)
+    if ((((blockIdx.x * blockDim.x + threadIdx.x) >> 5) & 15u) == 0u) {
+#pragma unroll
+      for (int x = 0; x < D; ++x) {
+        const unsigned k = float_to_key(adv[x]);
+        const unsigned hi = __reduce_max_sync(am, k), lo = __reduce_max_sync(am, ~k);
+        if (lead) {
+          atomicMax(&d.st->v_hi[x], hi);
+          atomicMax(&d.st->v_lo[x], lo);
+        }
+      }
+    }
   }
 }
 
@@ -549,7 +568,7 @@ __device__ __forceinline__ void for_each_chunk(const DomainDev& d, int k, unsign
 
 // Neighbour-list pass, then Eq. (9) from the list for a fluid particle (deferred otherwise).
 // Lists rebuilt every step (reuse off): every particle searches the sorted cells.  Kept lists
-// (reuse on): after a full rebuild every particle searches (radius 2h + skin, drift paths
+// (reuse on): after a full rebuild every particle searches (radius 2h + skin, displacements
 // restart from 0); after a rebuild that kept the slots, only the particles whose cell lies in
 // the every-step region around the buffers (where duplicates appear and parents are recycled)
 // search, through the index list, and the others keep their lists; dead slots are skipped
@@ -579,7 +598,8 @@ __device__ __forceinline__ void neighbours_body(const DomainDev& d, unsigned bid
       cell_coords(lin, g, c);
       const float4 pi = d.pos4[i];
       cnt = full ? search_list<D, false>(d, i, c, pi, r2max) : search_list<D, true>(d, i, c, pi, r2max);
-      if (reuse && full) d.A.path[i] = 0.f;
+      if (reuse && full)
+        for (int x = 0; x < D; ++x) d.A.disp[x][i] = 0.f;
     } else {
       cnt = (int)d.nb_cnt[i];
     }

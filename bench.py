@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--phase-steps", type=int, default=10)
     ap.add_argument("--ab-steps", type=int, default=200)
     ap.add_argument("--ab-rounds", type=int, default=3)
-    ap.add_argument("--pair-steps", type=int, default=100)
+    ap.add_argument("--pair-steps", type=int, default=300)
     ap.add_argument("--skin", type=float, default=0.1,
                     help="neighbour-list skin / h of the main measurement (kept lists); 0 rebuilds every step")
     ap.add_argument("--reuse-max", type=int, default=64)
@@ -331,17 +331,20 @@ def fused_force_cost(dom, steps):
     phase, plain launches) alternating between the default step (decisions in the force pass's
     drift epilogue) and the step with the decisions in the buffer kernel (the same force pass
     without them); both take the same decisions, so the state follows one trajectory.  Returns
-    the mean and standard error of the force-phase difference of consecutive pairs (us)."""
+    the mean and standard error of the force-phase difference of consecutive pairs (us); the
+    pairs alternate which of the two goes first, so that an effect of the order cancels."""
     from paper_2406_16786_gb300 import _ffi
 
     dom.use_graph(False)
     dom.enable_phase_timing(True)
     diffs, ff, fs = [], [], []
-    for _ in range(steps):
-        dom.step(1, _ffi.STEP_DEFAULT)
-        tf, _ = dom.phase_times()
-        dom.step(1, _ffi.STEP_DEFAULT | _ffi.PHASE_BUFFER_KERNEL)
-        ts, _ = dom.phase_times()
+    for q in range(steps):
+        for fused in ((True, False) if q % 2 == 0 else (False, True)):
+            dom.step(1, _ffi.STEP_DEFAULT if fused else _ffi.STEP_DEFAULT | _ffi.PHASE_BUFFER_KERNEL)
+            if fused:
+                tf, _ = dom.phase_times()
+            else:
+                ts, _ = dom.phase_times()
         ff.append(tf["force"] * 1e3)
         fs.append(ts["force"] * 1e3)
         diffs.append(ff[-1] - fs[-1])
@@ -463,7 +466,7 @@ def run_gpu(args):
           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
           "fused": dict(bu_roof(fpair["us_per_step"], "force-phase time (CUDA events) of the default step minus "
                                 "that of the step whose decisions run in the buffer kernel, mean over %d "
-                                "alternating pairs (stderr in force_pairs)" % fpair["pairs"]),
+                                "alternating pairs, the order within a pair alternating (stderr in force_pairs)" % fpair["pairs"]),
                         kernel="k_force epilogue (decide_fused)", force_pairs=fpair,
                         step_ab=dict(ab, note="graph-replayed step time with the decisions fused minus the step "
                                      "without decisions, %d interleaved rounds of %d steps from the same state, "

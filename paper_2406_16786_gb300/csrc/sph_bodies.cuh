@@ -349,17 +349,17 @@ __device__ __forceinline__ void visit_entry(const DomainDev& d, unsigned ent, un
   fn(wall, j, rx, ry, rz);
 }
 
-// Calls fn for the cnt listed neighbours of particle i (16-byte loads of 4 entries).  OWN:
-// the list was written by this thread in this kernel, so it is read with coherent loads.
-template <int D, bool OWN = false, typename Fn>
+// Calls fn for the cnt listed neighbours of particle i (16-byte loads of 4 entries, the next
+// four loaded while the current four are visited).  The list was written by an earlier launch.
+template <int D, typename Fn>
 __device__ __forceinline__ void for_each_listed(const DomainDev& d, unsigned i, int cnt, unsigned ci, const float fi[3],
                                                 Fn&& fn, unsigned site = 3) {
   const uint4* lst = reinterpret_cast<const uint4*>(d.nb + (size_t)i * d.nb_cap);
   uint4 nq = make_uint4(0u, 0u, 0u, 0u);
-  if (cnt > 0) nq = OWN ? lst[0] : SPHBUF_LDG(lst);
+  if (cnt > 0) nq = SPHBUF_LDG(lst);
   for (int e = 0; e < cnt; e += 4) {
     const uint4 q = nq;
-    if (e + 4 < cnt) nq = OWN ? lst[(e >> 2) + 1] : SPHBUF_LDG(lst + (e >> 2) + 1);
+    if (e + 4 < cnt) nq = SPHBUF_LDG(lst + (e >> 2) + 1);
     visit_entry<D>(d, q.x, ci, fi, fn, i, site);
     if (e + 1 < cnt) visit_entry<D>(d, q.y, ci, fi, fn, i, site);
     if (e + 2 < cnt) visit_entry<D>(d, q.z, ci, fi, fn, i, site);

@@ -557,10 +557,20 @@ def run_gpu(args):
 
     dom.close()
     batched = None if args.no_batched else run_batched(args, stream, rank, world)
-    tjunction = None if args.no_tjunction else run_restricted_vs_full(args, stream)
-    rotating = None if args.no_rotating else run_rotating(args, stream)
-    pipe_8m = None if args.no_pipe8 else run_pipe_8m(args, stream)
-    dual = None if args.no_dual else run_dual(args, stream)
+    # the side measurements (no collectives): a failure is recorded in its key and does not
+    # take the main measurement's line with it
+    def side(skip, fn):
+        if skip:
+            return None
+        try:
+            return fn(args, stream)
+        except Exception as e:  # noqa: BLE001 - recorded in the line
+            return {"error": "%s: %s" % (type(e).__name__, e)}
+
+    tjunction = side(args.no_tjunction, run_restricted_vs_full)
+    rotating = side(args.no_rotating, run_rotating)
+    pipe_8m = side(args.no_pipe8, run_pipe_8m)
+    dual = side(args.no_dual, run_dual)
 
     cpu = None
     cpu_bu = None

@@ -6,7 +6,10 @@ configuration (graph replays of the whole step).
 * One physics step: sampled particles against the FP64 oracle evaluated one by one from the
   same input (neighbours of the sample found with a k-d tree), with the one-step tolerances
   of tests/test_gpu_physics.py; count invariant and sortedness on all particles.
+* Kept neighbour lists: a step that keeps its lists equals the same state stepped with
+  lists built again, up to the order of the FP32 sums.
 """
+import numpy as np
 import pytest
 
 from paper_2406_16786_gb300 import workloads as wl
@@ -27,3 +30,47 @@ def test_full_size_kinematic_steps_bit_exact(case):
 
 def test_full_size_physics_step_sampled(case):
     assert sampled.physics_step_sampled(case) > 1000
+
+
+def test_full_size_kept_lists_equal_a_fresh_build():
+    """The bench's kept neighbour lists (skin 0.1 h) at full size: after a few reuse periods,
+    a step that keeps its lists gives the particles, cells, labels and decisions of the same
+    state stepped by a fresh domain that builds every list again, with fields that differ only
+    by the order of the FP32 sums.  (The inlet pressure is held constant, 25 Pa, so that both
+    domains see the same p_b at their different step counts.)"""
+    from paper_2406_16786_gb300.domain import Domain
+
+    c = wl.config3(length=5.09)
+    for b in c.buffers:
+        if b.p_amp:
+            b.p_b, b.p_amp = 25.0, 0.0
+    a = Domain.from_case(c)
+    a.set_list_reuse(0.1)
+    a.use_graph(True)
+    a.step(120)  # (crossings begin after ~80 steps: the buffer lattices start 0.5 dp off the faces)
+    # step on until a rebuild keeps the lists for the next step
+    while True:
+        b0 = a.list_builds()
+        a.step(1)
+        if a.list_builds() == b0:
+            break
+    s = a.read()
+    nid = a.global_counters()["next_id"]
+    fresh = Domain.from_case(c)
+    fresh.write_particles(s["cell"], s["frac"], s["vel"], s["rho"], ids=s["id"], labels=s["label"], next_id=nid)
+    a.step(1)
+    fresh.step(1)
+    ra, rf = a.read(), fresh.read()
+    assert np.array_equal(ra["id"], rf["id"])
+    assert np.array_equal(ra["cell"], rf["cell"])
+    assert np.array_equal(ra["label"], rf["label"])
+    (ia, da), (i_f, df) = a.last_decisions(), fresh.last_decisions()
+    assert [x[:2] for x in ia] == [x[:2] for x in i_f] and sorted(da) == sorted(df)
+    assert len(ia) + len(da) > 0
+    assert np.max(np.abs(ra["frac"].astype(np.float64) - rf["frac"])) < 1e-6 * c.cs
+    v_a, v_f = ra["vel"].astype(np.float64), rf["vel"].astype(np.float64)
+    assert np.linalg.norm(v_a - v_f) / np.linalg.norm(v_f) < 1e-5
+    r_a, r_f = ra["rho"].astype(np.float64), rf["rho"].astype(np.float64)
+    assert np.max(np.abs(r_a - r_f)) / c.rho0 < 1e-6
+    a.close()
+    fresh.close()

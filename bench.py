@@ -87,7 +87,7 @@ def parse():
     ap.add_argument("--no-pipe8", action="store_true")
     ap.add_argument("--no-dual", action="store_true")
     ap.add_argument("--no-tjunction", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=150.0,
                     help="seconds the reference arm's warm-up + timed steps may take (sizes its sample)")

@@ -641,13 +641,13 @@ sphbuf_status sphbuf_create_domain(const sphbuf_domain_desc* desc, void* cuda_st
     A(dalloc(d, &p->rho, C));
     A(dalloc(d, &p->id, C));
     A(dalloc(d, &p->label, C));
-    for (int x = 0; x < 3; ++x) {
-      p->disp[x] = nullptr;
-      if (x < D) A(dalloc(d, &p->disp[x], C));
-    }
     A(dalloc(d, &p->bflag, C));
   }
   A(dalloc(d, &v.order, C));
+  for (int x = 0; x < 3; ++x) {
+    v.disp[x] = nullptr;
+    if (x < D) A(dalloc(d, &v.disp[x], C));
+  }
   A(dalloc(d, &v.core, C));
   A(dalloc(d, &v.vr4, C));
   A(dalloc(d, &v.deferred, C));

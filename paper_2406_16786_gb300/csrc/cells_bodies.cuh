@@ -245,8 +245,6 @@ __device__ __forceinline__ void scatter_body(const DomainDev& d, unsigned bid, u
     const float rho = d.B.rho[i];
     d.A.rho[dst] = rho;
     d.A.id[dst] = d.B.id[i];
-#pragma unroll
-    for (int x = 0; x < D; ++x) d.A.disp[x][dst] = full ? 0.f : d.B.disp[x][i];
     d.A.bflag[dst] = d.B.bflag[i];
     int c[3];
     cell_coords(lin, g, c);

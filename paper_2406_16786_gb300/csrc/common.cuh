@@ -236,8 +236,6 @@ struct Particles {
   float* rho;
   unsigned* id;
   uint8_t* label;
-  float* disp[3];  // displacement since the last full neighbour-list build, relative to the
-                   // reference velocity StepState::u0 of that period (x < d allocated)
   // boundary identification of the transport velocity (reading A27), set by the last force
   // pass with the transport velocity: bit 0 candidate, bit 1 set (a previous step exists),
   // bit 2 core, bit 3 boundary particle

@@ -35,7 +35,7 @@ __device__ __forceinline__ void write_injection(const DomainDev& d, const Decisi
   d.B.id[dst] = kNoSlot;
   d.B.label[dst] = 0;  // the duplicate is ordinary fluid (Algorithm 1)
 #pragma unroll
-  for (int x = 0; x < D; ++x) d.B.disp[x][dst] = 0.f;
+  for (int x = 0; x < D; ++x) d.disp[x][dst] = 0.f;
   d.B.bflag[dst] = 0;
 }
 

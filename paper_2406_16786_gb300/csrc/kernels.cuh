@@ -46,6 +46,11 @@ struct DomainDev {
   const uint8_t* s_mask;      // per cell: 1 where kept lists are rebuilt every step (candidate
                               //   cells and two rings of cells around them)
   unsigned* order;            // live particles' slots sorted by (cell, id) (kept lists)
+  float* disp[3];             // per slot (kept lists): displacement since the last full list
+                              //   build relative to the period's reference velocity
+                              //   StepState::u0 (x < d allocated); only the slot's own drift
+                              //   reads and writes it, so it stays in place between full
+                              //   builds and is reset at each
   uint8_t* core;              // per slot, from the density pass with the transport velocity:
                               //   bit 0 core boundary particle, bit 1 candidate (reading A27)
   StepState* st;

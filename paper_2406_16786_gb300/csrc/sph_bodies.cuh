@@ -165,7 +165,7 @@ __device__ __forceinline__ void drift_store(const DomainDev& d, bool fused, unsi
     d.B.id[i] = d.A.id[i];
     d.B.label[i] = kDead;
 #pragma unroll
-    for (int x = 0; x < D; ++x) d.B.disp[x][i] = 0.f;
+    for (int x = 0; x < D; ++x) d.disp[x][i] = 0.f;
     d.B.bflag[i] = 0;
     return;
   }
@@ -207,8 +207,8 @@ __device__ __forceinline__ void drift_store(const DomainDev& d, bool fused, unsi
     float s2 = 0.f;
 #pragma unroll
     for (int x = 0; x < D; ++x) {
-      const float dx = d.A.disp[x][i] + (adv[x] - d.st->u0[x]) * d.P.dt;
-      d.B.disp[x][i] = dx;
+      const float dx = d.disp[x][i] + (adv[x] - d.st->u0[x]) * d.P.dt;
+      d.disp[x][i] = dx;
       s2 += dx * dx;
     }
     const unsigned am = __activemask();
@@ -599,7 +599,7 @@ __device__ __forceinline__ void neighbours_body(const DomainDev& d, unsigned bid
       const float4 pi = d.pos4[i];
       cnt = full ? search_list<D, false>(d, i, c, pi, r2max) : search_list<D, true>(d, i, c, pi, r2max);
       if (reuse && full)
-        for (int x = 0; x < D; ++x) d.A.disp[x][i] = 0.f;
+        for (int x = 0; x < D; ++x) d.disp[x][i] = 0.f;
     } else {
       cnt = (int)d.nb_cnt[i];
     }

@@ -142,13 +142,18 @@ __device__ __forceinline__ void hist_body(const DomainDev& d, unsigned bid, unsi
       // the next period's reference velocity: the middle of the range of the drift
       // velocities of this one, zero (the walls) included
       for (int x = 0; x < 3; ++x) {
+        unsigned khi = 0u, klo = 0u;
+        for (int q = 0; q < kRangeCopies; ++q) {
+          khi = max(khi, st->v_hi[q][x]);
+          klo = max(klo, st->v_lo[q][x]);
+          st->v_hi[q][x] = st->v_lo[q][x] = 0u;
+        }
         float u = 0.f;
-        if (st->v_hi[x]) {
-          const float hi = fmaxf(key_to_float(st->v_hi[x]), 0.f), lo = fminf(key_to_float(~st->v_lo[x]), 0.f);
+        if (khi) {
+          const float hi = fmaxf(key_to_float(khi), 0.f), lo = fminf(key_to_float(~klo), 0.f);
           u = 0.5f * (hi + lo);
         }
         st->u0[x] = u;
-        st->v_hi[x] = st->v_lo[x] = 0u;
       }
     }
     st->full = full;

@@ -25,6 +25,7 @@
 namespace sphbuf {
 
 constexpr int kMaxBuffers = 32;
+constexpr int kRangeCopies = 64;  // copies of the drift-velocity range (StepState::v_hi, v_lo)
 constexpr uint8_t kDead = 255;
 constexpr unsigned kNoSlot = 0xFFFFFFFFu;
 constexpr int kScanItems = 16;      // cells per thread in the scan kernels
@@ -220,7 +221,7 @@ struct StepState {
   // reference velocity of the current reuse period, and the range of the drift velocities
   // seen in it (order-preserving keys, both maximised from 0: hi = key(v), lo = ~key(v))
   float u0[3];
-  unsigned v_hi[3], v_lo[3];
+  unsigned v_hi[kRangeCopies][3], v_lo[kRangeCopies][3];  // copies that spread the atomics
   unsigned since_full;             // steps since the last full build
   unsigned long long list_builds;  // full builds so far
   // dynamic share-out of the neighbour (0) and force (1) passes: the next chunk to take and

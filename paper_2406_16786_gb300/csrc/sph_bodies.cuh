@@ -215,17 +215,17 @@ __device__ __forceinline__ void drift_store(const DomainDev& d, bool fused, unsi
     const bool lead = (threadIdx.x & 31) == __ffs(am) - 1;
     const unsigned wmax = __reduce_max_sync(am, __float_as_uint(sqrtf(s2)));
     if (lead) atomicMax(&d.st->path_bits, wmax);
-    // (the range only centres the reference velocity, which any value keeps correct: one
-    // warp in sixteen samples it, which keeps its atomics off the step's critical path)
-    if ((((blockIdx.x * blockDim.x + threadIdx.x) >> 5) & 15u) == 0u) {
+    // the range over every particle (so that u0, and with it the step on which lists are
+    // built again, depends on the state alone, not on which warp took which particles); each
+    // warp adds to one of kRangeCopies copies, which keeps the atomics off one address
+    const unsigned copy = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) % (unsigned)kRangeCopies;
 #pragma unroll
-      for (int x = 0; x < D; ++x) {
-        const unsigned k = float_to_key(adv[x]);
-        const unsigned hi = __reduce_max_sync(am, k), lo = __reduce_max_sync(am, ~k);
-        if (lead) {
-          atomicMax(&d.st->v_hi[x], hi);
-          atomicMax(&d.st->v_lo[x], lo);
-        }
+    for (int x = 0; x < D; ++x) {
+      const unsigned k = float_to_key(adv[x]);
+      const unsigned hi = __reduce_max_sync(am, k), lo = __reduce_max_sync(am, ~k);
+      if (lead) {
+        atomicMax(&d.st->v_hi[copy][x], hi);
+        atomicMax(&d.st->v_lo[copy][x], lo);
       }
     }
   }

@@ -48,9 +48,12 @@ FP32_LANES_PER_SM = 128
 # buffers' candidate cells, which are the same at L = 2.5 and 5.09 m.  A figure whose kernel
 # changed after its revision is not reported (None).
 NCU_TRAFFIC = {
-    "k_neighbours": {"kept_bytes_per_particle": None, "full_bytes_per_particle": None, "source": None},
-    "k_force": {"bytes_per_particle": None, "source": None},
-    "k_buffer": {"bytes_per_launch": None, "source": None},
+    "k_neighbours": {"kept_bytes_per_particle": (746.45e6 + 87.98e6) / 1965281,
+                     "full_bytes_per_particle": (177.17e6 + 667.30e6) / 1965281,
+                     "source": "ncu, kernels of commit 48e37d8, 2.0 M pipe (kept-list step; full build)"},
+    "k_force": {"bytes_per_particle": (872.15e6 + 90.46e6) / 1965281,
+                "source": "ncu, kernels of commit 48e37d8, 2.0 M pipe (kept-list step)"},
+    "k_buffer": {"bytes_per_launch": 3.49e6, "source": "ncu, kernels of commit 48e37d8, 2.0 M pipe"},
 }
 
 

@@ -263,7 +263,9 @@ sphbuf_status sphbuf_read_boundary_pressure(sphbuf_domain_t d, int buffer_id, do
  * a roll about X': R <- Rx(roll) R.  n need not be unit length. */
 sphbuf_status sphbuf_rotation_from_normal(const double normal[3], double roll, double out_R[9]);
 
-/* Kept neighbour lists (a Verlet skin): with skin_over_h > 0 the lists hold the pairs within
+/* Kept neighbour lists (a Verlet skin; the paper has no counterpart: its neighbour search is a
+ * cell-linked list, Sec. 3.1, and the results here differ from it only by the order of the
+ * FP32 sums): with skin_over_h > 0 the lists hold the pairs within
  * 2h + skin (skin = skin_over_h h, at most h) and are kept over steps.  A step whose rebuild
  * keeps the lists also keeps the particles' slots (no sort; deleted particles stay as dead
  * slots, duplicates are appended), except where the lists must change: the particles in the
